@@ -1,0 +1,178 @@
+/*
+ * fh.h -- C ABI of the GB300 FFT/CG homogenization library (libfh.so).
+ *
+ * The library solves the trigonometric-collocation Lippmann-Schwinger system
+ * of Zeman et al., "Accelerating a FFT-based solver for numerical
+ * homogenization of periodic media by conjugate gradients":
+ *
+ *     (I + B) e = e0,   B = F^-1 Gamma0 F dL          (Eq. linear_system, Eq. mtrx_B)
+ *
+ * for the periodic field e on an odd grid N = (N_0, ..., N_{d-1}) under a
+ * prescribed macroscopic field E (Eq. problem_def_2), with
+ *   dL(x)     = L(x) - L0                              (Eq. current_decomp)
+ *   Gamma0(k) = xi (x) xi / (xi . L0 . xi), Gamma0(0)=0, xi_a = k_a / Y_a  (Section 2.1)
+ * and returns the effective tensor L_eff[:, b] = <L e^(b)> (nodal mean).
+ *
+ * Conventions for every call:
+ *  - Status codes only; nothing aborts or throws across the ABI.  On error
+ *    fh_last_error(ctx) returns a message.
+ *  - Fields are component-major ("SoA") [d][N_0]...[N_{d-1}], C-order, the
+ *    last axis contiguous; node i sits at pixel coordinate i.
+ *  - Pointers documented as "device" must be CUDA device (or managed)
+ *    memory owned by the caller; "host" pointers are ordinary host memory.
+ *    The library never frees caller memory and keeps no caller pointer
+ *    after a call returns.
+ *  - The context owns every internal device buffer (spectra, Krylov vectors,
+ *    scalars); it is allocated in fh_create and freed in fh_destroy.
+ *  - All device work is enqueued on the CUDA stream given to fh_create.
+ *    fh_apply does not synchronise.  fh_solve synchronises on the stream
+ *    only to read its small status word between iteration chunks, and
+ *    before returning.
+ *  - One context must not be used from two host threads at once.
+ */
+#ifndef FH_H_
+#define FH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fh_ctx fh_ctx;
+
+typedef enum {
+  FH_OK = 0,
+  FH_ERR_ARG = 1,            /* invalid argument (null pointer, bad d/N/tol ...) */
+  FH_ERR_EVEN_N = 2,         /* an axis length is even; only odd N is supported
+                                (Section 3 footnote: odd grids avoid the Nyquist mode) */
+  FH_ERR_NOT_SPD = 3,        /* a phase tensor or L0 is not symmetric positive definite */
+  FH_ERR_OOM = 4,            /* device allocation failed */
+  FH_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+  FH_ERR_NOT_CONVERGED = 6,  /* iteration cap reached before the tolerance */
+  FH_ERR_BREAKDOWN = 7,      /* (A p, p) <= 0, a zero BiCG denominator, or a non-finite scalar */
+  FH_ERR_TIMEOUT = 8,        /* a bounded device wait expired */
+  FH_ERR_UNSUPPORTED = 9     /* size/precision without a compiled FFT plan */
+} fh_status;
+
+typedef enum {
+  FH_CG = 0,           /* conjugate gradients, Saad Alg. 6.18 (Section 2.3) */
+  FH_BICG = 1,         /* biconjugate gradients, Saad Alg. 7.3, shadow r0* = r0 (Section 3) */
+  FH_FIXED_POINT = 2   /* Moulinec-Suquet Neumann iteration, Eq. (orig_fft) */
+} fh_method;
+
+typedef enum {
+  FH_FP64 = 0,         /* every vector and FFT in float64 */
+  FH_FP32 = 1,         /* float32 vectors and FFTs, float64 scalars (no refinement) */
+  FH_FP32_REFINED = 2  /* float32 inner solves on A d = r, float64 outer residual
+                          r = e0 - A x and float64 x += d until the float64 residual
+                          meets the tolerance */
+} fh_precision;
+
+/* Per-solve report.  history/history_cap are inputs (a host buffer for the
+ * relative recursive residual of every inner iteration; may be NULL/0). */
+typedef struct {
+  int iters;              /* inner iterations over all refinement steps */
+  int outer_iters;        /* float64 refinement steps (0 unless FH_FP32_REFINED) */
+  int matvecs;            /* applications of A or A^T */
+  int status;             /* fh_status of this solve */
+  double rel_res_true;    /* ||e0 - A e||_2 / ||e0||_2 recomputed at exit (float64 for
+                             FH_FP64 and FH_FP32_REFINED, float32 pipeline for FH_FP32) */
+  double rel_res;         /* last recursive relative residual of the inner solver */
+  double eta_r;           /* Eq. (errR_def) as printed: ||L0 (e_{m+1} - e_m)|| / ||e0|| */
+  double eta_e;           /* Eq. (errE_def) of the returned field (float64) */
+  double* history;        /* in: host buffer or NULL */
+  int history_cap;        /* in: its capacity */
+  int history_len;        /* out: entries written */
+} fh_info;
+
+/* fh_create -- build a solver context for one microstructure.
+ *
+ * Problem statement of Section 2.1 / 2.2: cell Y = prod (-Y_a, Y_a), grid N,
+ * phase image, per-phase conductivity tensors L, reference medium L0.
+ *
+ *  out        host; receives the context (NULL on failure).
+ *  d          2 or 3.
+ *  N          host, d ints, each odd and >= 3; supported lengths are those
+ *             that factor into 3, 5 and 7.
+ *  Y          host, d half side lengths (> 0), or NULL for all ones.
+ *  phase      |N| bytes in C order, phase id per node (< nphase); a host
+ *             pointer if phase_on_device == 0, else a device pointer.
+ *             Copied into the context.
+ *  nphase     1..256.
+ *  L          host, nphase*d*d float64, row-major tensor per phase, each SPD.
+ *  L0         host, d*d float64 SPD, or NULL for Eq. (opt_ref):
+ *             (lambda_min + lambda_max)/2 I over all phase eigenvalues.
+ *  precision  an fh_precision; decides which buffers are allocated
+ *             (FH_FP32_REFINED allocates both float32 and float64 paths).
+ *  stream     cudaStream_t (as void*), or NULL for the legacy default stream.
+ *
+ * Errors: FH_ERR_ARG, FH_ERR_EVEN_N, FH_ERR_NOT_SPD, FH_ERR_UNSUPPORTED,
+ * FH_ERR_OOM, FH_ERR_CUDA.  On error nothing is leaked. */
+fh_status fh_create(fh_ctx** out, int d, const int* N, const double* Y,
+                    const uint8_t* phase, int phase_on_device, int nphase,
+                    const double* L, const double* L0, int precision, void* stream);
+
+/* fh_set_phase -- replace the phase image (same grid, same phase table).
+ * phase: |N| bytes, host (phase_on_device == 0) or device.  Enqueued on the
+ * context stream; a host source is copied synchronously. */
+fh_status fh_set_phase(fh_ctx* ctx, const uint8_t* phase, int phase_on_device);
+
+/* fh_apply -- one matrix-free product (Eq. linear_system, Eq. mtrx_B):
+ *   transpose == 0:  e_out = (I + B) e_in   = e_in + F^-1 Gamma0 F (dL e_in)
+ *   transpose != 0:  e_out = (I + B^T) e_in = e_in + dL F^-1 Gamma0 F e_in
+ *  e_in, e_out  device, d*|N| elements [d][N...]; dtype FH_FP64 (double) or
+ *               FH_FP32 (float).  e_in == e_out is allowed.
+ *  dtype        FH_FP64 needs a context created with FH_FP64 or
+ *               FH_FP32_REFINED; FH_FP32 needs FH_FP32 or FH_FP32_REFINED.
+ * Asynchronous on the context stream.  Errors: FH_ERR_ARG, FH_ERR_CUDA. */
+fh_status fh_apply(fh_ctx* ctx, const void* e_in, void* e_out, int transpose, int dtype);
+
+/* fh_solve -- solve (I + B) e = e0 with e0 = E at every node.
+ *  E          host, d float64 (the macroscopic field of Eq. problem_def_2).
+ *  tol        > 0: stop when ||e0 - A e||_2 / ||e0||_2 <= tol.  The inner
+ *             solver tests its recursive residual; FH_FP64 and FH_FP32_REFINED
+ *             confirm with a float64 true residual before returning FH_OK.
+ *  method     an fh_method.
+ *  max_iter   cap on inner iterations (all refinement steps together).
+ *  e_init     device float64 [d][N...] initial field, or NULL for e = E.
+ *  e_out      device float64 [d][N...] for the solution, or NULL.
+ *  Leff_col   host, d float64 for <L e> (column of L_eff for unit E), or NULL.
+ *  info       host, or NULL.
+ * Returns FH_OK, FH_ERR_NOT_CONVERGED (e_out still holds the last iterate),
+ * FH_ERR_BREAKDOWN, FH_ERR_ARG or FH_ERR_CUDA. */
+fh_status fh_solve(fh_ctx* ctx, const double* E, double tol, int method, int max_iter,
+                   const double* e_init, double* e_out, double* Leff_col, fh_info* info);
+
+/* fh_solve_all -- d solves with E = e_1 ... e_d; Leff receives the full
+ * d x d effective tensor, row-major (column b from load b).  infos: host
+ * array of d fh_info, or NULL.  Returns the first non-OK status. */
+fh_status fh_solve_all(fh_ctx* ctx, double tol, int method, int max_iter,
+                       double* Leff, fh_info* infos);
+
+/* fh_effective_column -- col[a] = mean over nodes of (L(x) e(x))_a, float64.
+ *  e: device float64 [d][N...]; col: host, d doubles.  Synchronises. */
+fh_status fh_effective_column(fh_ctx* ctx, const double* e, double* col);
+
+/* fh_eta_e -- equilibrium norm of Eq. (errE_def) for field e (device float64):
+ *   eta_e^2 = sum_k |xi . j^(k)|^2 / |j^(0)|^2,  j = L e.  Synchronises. */
+fh_status fh_eta_e(fh_ctx* ctx, const double* e, double* eta);
+
+/* fh_destroy -- free the context and every buffer it owns.  NULL is a no-op. */
+void fh_destroy(fh_ctx* ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* fh_status_string(int status);
+
+/* Last error message recorded on ctx (static or context storage, never NULL). */
+const char* fh_last_error(const fh_ctx* ctx);
+
+/* Library version string. */
+const char* fh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FH_H_ */
