@@ -85,6 +85,7 @@ typedef struct {
   double* history;        /* in: host buffer or NULL */
   int history_cap;        /* in: its capacity */
   int history_len;        /* out: entries written */
+  long long launches;     /* out: CUDA kernels this call launched (graph replays included) */
 } fh_info;
 
 /* fh_create -- build a solver context for one microstructure.
@@ -158,6 +159,21 @@ fh_status fh_effective_column(fh_ctx* ctx, const double* e, double* col);
 /* fh_eta_e -- equilibrium norm of Eq. (errE_def) for field e (device float64):
  *   eta_e^2 = sum_k |xi . j^(k)|^2 / |j^(0)|^2,  j = L e.  Synchronises. */
 fh_status fh_eta_e(fh_ctx* ctx, const double* e, double* eta);
+
+/* fh_profile -- measurement hook (no counterpart in the paper; used to state
+ * achieved bandwidth against the HBM roofline).  Times `reps` back-to-back
+ * launches of one piece of the CG iteration on the context stream with CUDA
+ * events after 3 warm-up launches, and writes the average milliseconds per
+ * launch to *ms.  The context's Krylov vectors are overwritten (zeroed); any
+ * solve state is lost.
+ *  dtype  FH_FP64 or FH_FP32 (pipeline to time)
+ *  what   0 row-forward pass (p = r + beta p, dL p, forward line FFTs)
+ *         1 column passes with the Green projection
+ *         2 row-inverse pass (inverse line FFTs, A p = p + y, (p, A p))
+ *         3 CG vector update (x += alpha p, r -= alpha A p, (r, r))
+ *         5 one full operator application (all passes of fh_apply)
+ * Synchronises.  Errors: FH_ERR_ARG, FH_ERR_CUDA. */
+fh_status fh_profile(fh_ctx* ctx, int dtype, int what, int reps, double* ms);
 
 /* fh_destroy -- free the context and every buffer it owns.  NULL is a no-op. */
 void fh_destroy(fh_ctx* ctx);

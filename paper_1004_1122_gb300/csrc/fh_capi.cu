@@ -1,0 +1,655 @@
+// fh_capi.cu -- the C ABI of include/fh.h: context creation and validation,
+// the matrix-free product, and the solve drivers (float64, float32, and
+// float32 inner solves with float64 refinement).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fh.h"
+#include "fh_pipeline.cuh"
+
+using fh::Pipeline;
+using fh::Problem;
+using fh::SolveResult;
+
+struct fh_ctx {
+  Problem pb;
+  int precision = FH_FP64;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  uint8_t* d_phase = nullptr;
+  Pipeline<float>* p32 = nullptr;
+  Pipeline<double>* p64 = nullptr;
+  double* d_x64 = nullptr;   // float64 solution (refinement iterate / output staging)
+  double* d_r64 = nullptr;   // float64 residual
+  long long own_launches = 0;  // kernels launched directly by this file
+  std::string err;
+};
+
+namespace {
+
+const char* kStatusNames[] = {"FH_OK",          "FH_ERR_ARG",           "FH_ERR_EVEN_N",
+                              "FH_ERR_NOT_SPD", "FH_ERR_OOM",           "FH_ERR_CUDA",
+                              "FH_ERR_NOT_CONVERGED", "FH_ERR_BREAKDOWN", "FH_ERR_TIMEOUT",
+                              "FH_ERR_UNSUPPORTED"};
+
+fh_status fail(fh_ctx* c, fh_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+// Cholesky test of a symmetric matrix (row-major, n x n).
+bool is_spd(const double* A, int n) {
+  double scale = 0.0;
+  for (int i = 0; i < n * n; ++i) scale = std::fmax(scale, std::fabs(A[i]));
+  if (!(scale > 0.0) || !std::isfinite(scale)) return false;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(A[i * n + j] - A[j * n + i]) > 1e-12 * scale) return false;
+  std::vector<double> Lc(n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double s = A[j * n + j];
+    for (int k = 0; k < j; ++k) s -= Lc[j * n + k] * Lc[j * n + k];
+    if (!(s > 1e-14 * scale)) return false;
+    Lc[j * n + j] = std::sqrt(s);
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; ++k) t -= Lc[i * n + k] * Lc[j * n + k];
+      Lc[i * n + j] = t / Lc[j * n + j];
+    }
+  }
+  return true;
+}
+
+// Symmetric eigenvalue extremes by Jacobi rotations (n <= 3).
+void sym_eig_range(const double* A, int n, double& lo, double& hi) {
+  double a[9];
+  for (int i = 0; i < n * n; ++i) a[i] = A[i];
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += a[i * n + j] * a[i * n + j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = a[k * n + p], akq = a[k * n + q];
+          a[k * n + p] = c * akp - s * akq;
+          a[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = a[p * n + k], aqk = a[q * n + k];
+          a[p * n + k] = c * apk - s * aqk;
+          a[q * n + k] = s * apk + c * aqk;
+        }
+      }
+  }
+  lo = hi = a[0];
+  for (int i = 1; i < n; ++i) {
+    lo = std::fmin(lo, a[i * n + i]);
+    hi = std::fmax(hi, a[i * n + i]);
+  }
+}
+
+template <typename T>
+__global__ void k_convert_vec(const double* in, T* out, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = T(in[i]);
+}
+template <typename T>
+__global__ void k_widen_vec(const T* in, double* out, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+__global__ void k_to_float(const double* in, float* out, float* zero1, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    out[i] = (float)in[i];
+    zero1[i] = 0.0f;
+  }
+}
+__global__ void k_add_float(double* x, const float* d, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+__global__ void k_fill_vec(double* x, long long nodes, int d, double e0, double e1, double e2) {
+  const long long len = nodes * d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / nodes;
+    x[i] = c == 0 ? e0 : (c == 1 ? e1 : e2);
+  }
+}
+
+int vec_grid(long long len) {
+  long long g = (len + 255) / 256;
+  return (int)(g < 1184 ? (g < 1 ? 1 : g) : 1184);
+}
+
+fh_status from_rc(fh_ctx* c, int rc, const std::string& err) {
+  if (rc == 0) return FH_OK;
+  c->err = err;
+  return (fh_status)rc;
+}
+
+fh_status cuda_fail(fh_ctx* c, cudaError_t e, const char* what) {
+  c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return FH_ERR_CUDA;
+}
+
+int to_status(int done) {
+  switch (done) {
+    case fh::kConverged: return FH_OK;
+    case fh::kBreakdown: return FH_ERR_BREAKDOWN;
+    default: return FH_ERR_NOT_CONVERGED;
+  }
+}
+
+bool l0_isotropic(const Problem& pb, double& l0) {
+  const int d = pb.d;
+  l0 = pb.L0[0];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (std::fabs(pb.L0[i * d + j] - (i == j ? l0 : 0.0)) > 1e-15 * std::fabs(l0)) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fh_version(void) { return "fh 0.1.0 (sm_103a)"; }
+
+const char* fh_status_string(int s) {
+  if (s < 0 || s > 9) return "FH_UNKNOWN";
+  return kStatusNames[s];
+}
+
+const char* fh_last_error(const fh_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+void fh_destroy(fh_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  if (c->p32) {
+    c->p32->release();
+    delete c->p32;
+  }
+  if (c->p64) {
+    c->p64->release();
+    delete c->p64;
+  }
+  if (c->d_phase) cudaFree(c->d_phase);
+  if (c->d_x64) cudaFree(c->d_x64);
+  if (c->d_r64) cudaFree(c->d_r64);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+fh_status fh_create(fh_ctx** out, int d, const int* N, const double* Y, const uint8_t* phase,
+                    int phase_on_device, int nphase, const double* L, const double* L0,
+                    int precision, void* stream) {
+  if (!out) return FH_ERR_ARG;
+  *out = nullptr;
+  if (d != 2 && d != 3) return FH_ERR_ARG;
+  if (!N || !phase || !L || nphase < 1 || nphase > 256) return FH_ERR_ARG;
+  if (precision < FH_FP64 || precision > FH_FP32_REFINED) return FH_ERR_ARG;
+  for (int a = 0; a < d; ++a) {
+    if (N[a] < 3) return FH_ERR_ARG;
+    if (N[a] % 2 == 0) return FH_ERR_EVEN_N;
+    if (Y && !(Y[a] > 0.0 && std::isfinite(Y[a]))) return FH_ERR_ARG;
+  }
+  fh_ctx* c = new (std::nothrow) fh_ctx();
+  if (!c) return FH_ERR_OOM;
+  Problem& pb = c->pb;
+  pb.d = d;
+  pb.nodes = 1;
+  for (int a = 0; a < d; ++a) {
+    pb.N[a] = N[a];
+    pb.Y[a] = Y ? Y[a] : 1.0;
+    pb.nodes *= N[a];
+  }
+  pb.nphase = nphase;
+  pb.L.assign(L, L + (size_t)nphase * d * d);
+  for (int p = 0; p < nphase; ++p) {
+    if (!is_spd(&pb.L[(size_t)p * d * d], d)) {
+      fh_destroy(c);
+      return FH_ERR_NOT_SPD;
+    }
+  }
+  if (L0) {
+    pb.L0.assign(L0, L0 + d * d);
+    if (!is_spd(pb.L0.data(), d)) {
+      fh_destroy(c);
+      return FH_ERR_NOT_SPD;
+    }
+  } else {
+    // Eq. (opt_ref): (lambda_min + lambda_max) / 2 I over every phase eigenvalue
+    double lo = 1e300, hi = -1e300;
+    for (int p = 0; p < nphase; ++p) {
+      double a, b;
+      sym_eig_range(&pb.L[(size_t)p * d * d], d, a, b);
+      lo = std::fmin(lo, a);
+      hi = std::fmax(hi, b);
+    }
+    pb.L0.assign(d * d, 0.0);
+    for (int i = 0; i < d; ++i) pb.L0[i * d + i] = 0.5 * (lo + hi);
+  }
+  pb.dL.resize(pb.L.size());
+  for (int p = 0; p < nphase; ++p)
+    for (int i = 0; i < d * d; ++i) pb.dL[(size_t)p * d * d + i] = pb.L[(size_t)p * d * d + i] - pb.L0[i];
+  c->precision = precision;
+
+  cudaError_t e;
+  if (stream) {
+    c->st = (cudaStream_t)stream;
+  } else {
+    if ((e = cudaStreamCreate(&c->st)) != cudaSuccess) {
+      fh_destroy(c);
+      return FH_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if ((e = cudaMalloc(&c->d_phase, pb.nodes)) != cudaSuccess) {
+    fh_destroy(c);
+    return FH_ERR_OOM;
+  }
+  pb.d_phase = c->d_phase;
+  fh_status s = fh_set_phase(c, phase, phase_on_device);
+  if (s != FH_OK) {
+    fh_destroy(c);
+    return s;
+  }
+  std::string err;
+  int rc = 0;
+  if (precision == FH_FP64 || precision == FH_FP32_REFINED) {
+    c->p64 = new (std::nothrow) Pipeline<double>();
+    if (!c->p64) rc = FH_ERR_OOM;
+    if (!rc) rc = c->p64->init(pb, 1, precision == FH_FP64, c->st, err);
+  }
+  if (!rc && (precision == FH_FP32 || precision == FH_FP32_REFINED)) {
+    c->p32 = new (std::nothrow) Pipeline<float>();
+    if (!c->p32) rc = FH_ERR_OOM;
+    if (!rc) rc = c->p32->init(pb, 1, true, c->st, err);
+  }
+  const size_t vbytes = (size_t)d * pb.nodes * sizeof(double);
+  if (!rc && cudaMalloc(&c->d_x64, vbytes) != cudaSuccess) rc = FH_ERR_OOM;
+  if (!rc && cudaMalloc(&c->d_r64, vbytes) != cudaSuccess) rc = FH_ERR_OOM;
+  if (rc) {
+    fh_destroy(c);
+    return (fh_status)rc;
+  }
+  *out = c;
+  return FH_OK;
+}
+
+fh_status fh_set_phase(fh_ctx* c, const uint8_t* phase, int phase_on_device) {
+  if (!c || !phase) return FH_ERR_ARG;
+  const size_t n = (size_t)c->pb.nodes;
+  std::vector<uint8_t> h(n);
+  cudaError_t e;
+  if (phase_on_device) {
+    e = cudaMemcpyAsync(h.data(), phase, n, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  } else {
+    std::memcpy(h.data(), phase, n);
+    e = cudaSuccess;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "phase copy");
+  for (size_t i = 0; i < n; ++i)
+    if (h[i] >= c->pb.nphase) return fail(c, FH_ERR_ARG, "phase id out of range");
+  e = cudaMemcpyAsync(c->d_phase, h.data(), n, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "phase upload");
+  return FH_OK;
+}
+
+fh_status fh_apply(fh_ctx* c, const void* in, void* out, int transpose, int dtype) {
+  if (!c || !in || !out) return FH_ERR_ARG;
+  cudaError_t e;
+  if (dtype == FH_FP64) {
+    if (!c->p64) return fail(c, FH_ERR_ARG, "context has no float64 pipeline");
+    e = c->p64->apply(static_cast<const double*>(in), static_cast<double*>(out), transpose != 0);
+  } else if (dtype == FH_FP32) {
+    if (!c->p32) return fail(c, FH_ERR_ARG, "context has no float32 pipeline");
+    e = c->p32->apply(static_cast<const float*>(in), static_cast<float*>(out), transpose != 0);
+  } else {
+    return fail(c, FH_ERR_ARG, "dtype must be FH_FP64 or FH_FP32");
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "fh_apply");
+  return FH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+fh_status finish_info(fh_ctx* c, Pipeline<T>* P, fh_info* info, int hist_len) {
+  if (info && info->history && info->history_cap > 0 && P->hist && hist_len > 0) {
+    const int n = hist_len < info->history_cap ? hist_len : info->history_cap;
+    cudaError_t e = cudaMemcpyAsync(info->history, P->hist, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "history copy");
+    info->history_len = n;
+  }
+  return FH_OK;
+}
+
+template <typename T>
+int ensure_hist(Pipeline<T>* P, fh_info* info, std::string& err) {
+  if (!info || !info->history || info->history_cap <= 0) {
+    P->hist = nullptr;
+    P->hist_cap = 0;
+    return 0;
+  }
+  if (P->hist_cap < info->history_cap || P->hist == nullptr) {
+    double* h = nullptr;
+    if (cudaMalloc(&h, info->history_cap * sizeof(double)) != cudaSuccess) {
+      err = "history allocation";
+      return FH_ERR_OOM;
+    }
+    P->allocs.push_back(h);
+    P->hist = h;
+  }
+  P->hist_cap = info->history_cap;
+  return 0;
+}
+
+// Direct solve in one precision (FH_FP64 or FH_FP32): the Krylov loop runs in
+// P; x0 = E or e_init.  Restarts from the current iterate if the true residual
+// (same precision) misses the tolerance while the recursive one met it.
+template <typename T>
+fh_status solve_direct(fh_ctx* c, Pipeline<T>* P, const double* E, double tol, int method,
+                       int max_iter, const double* e_init, fh_info* info, double& rel_true,
+                       double& eta_r) {
+  std::string err;
+  const long long len = (long long)c->pb.d * c->pb.nodes;
+  double Ev[fh::kMaxLoads][fh::kMaxD] = {};
+  for (int a = 0; a < c->pb.d; ++a) Ev[0][a] = E[a];
+  int rc = ensure_hist(P, info, err);
+  if (rc) return from_rc(c, rc, err);
+  int x0 = fh::kX0Const;
+  if (e_init) {
+    ++c->own_launches;
+    k_convert_vec<T><<<vec_grid(len), 256, 0, c->st>>>(e_init, P->x[0], len);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "initial field");
+    x0 = fh::kX0Keep;
+  }
+  int total = 0, status = fh::kCap;
+  SolveResult res;
+  const double e2 = [&] {
+    double s = 0.0;
+    for (int a = 0; a < c->pb.d; ++a) s += E[a] * E[a];
+    return s * (double)c->pb.nodes;
+  }();
+  rel_true = NAN;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    const int budget = max_iter - total;
+    rc = P->solve(method, Ev, false, x0, nullptr, tol, budget > 0 ? budget : 0, &res, err);
+    if (rc) return from_rc(c, rc, err);
+    total += res.iters;
+    status = res.status;
+    // true residual of the iterate (into the ap buffer as scratch)
+    double rr;
+    const T* xin[fh::kMaxLoads] = {P->x[0]};
+    T* rout[fh::kMaxLoads] = {P->ap[0]};
+    rc = P->residual(xin, rout, false, Ev, &rr, err);
+    if (rc) return from_rc(c, rc, err);
+    rel_true = std::sqrt(rr / (e2 > 0 ? e2 : 1.0));
+    if (status != fh::kConverged || rel_true <= tol || total >= max_iter) break;
+    x0 = fh::kX0Keep;  // restart CG from the current iterate
+  }
+  if (status == fh::kConverged && !(rel_true <= tol)) status = fh::kCap;
+  if (info) {
+    info->iters = total;
+    info->outer_iters = 0;
+    info->rel_res = res.rel;
+  }
+  // eta_r (Eq. errR_def as printed)
+  eta_r = NAN;
+  if (method == fh::kFixed) {
+    double l0;
+    if (l0_isotropic(c->pb, l0)) eta_r = l0 * res.rel;
+  } else {
+    double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < c->pb.d; ++i)
+      for (int j = 0; j < c->pb.d; ++j) M[i * 3 + j] = c->pb.L0[i * c->pb.d + j];
+    double n2;
+    rc = P->matnorm2(P->p[0], M, &n2, err);
+    if (rc) return from_rc(c, rc, err);
+    eta_r = std::fabs(res.alpha) * std::sqrt(n2 / (e2 > 0 ? e2 : 1.0));
+  }
+  fh_status fs = finish_info(c, P, info, res.iters + 1);
+  if (fs != FH_OK) return fs;
+  return (fh_status)to_status(status);
+}
+
+}  // namespace
+
+extern "C" {
+
+fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_iter,
+                   const double* e_init, double* e_out, double* Leff_col, fh_info* info) {
+  if (!c || !E) return FH_ERR_ARG;
+  if (!(tol > 0.0) || max_iter < 0) return fail(c, FH_ERR_ARG, "tol must be > 0, max_iter >= 0");
+  if (method < FH_CG || method > FH_FIXED_POINT) return fail(c, FH_ERR_ARG, "unknown method");
+  for (int a = 0; a < c->pb.d; ++a)
+    if (!std::isfinite(E[a])) return fail(c, FH_ERR_ARG, "E not finite");
+  const int d = c->pb.d;
+  const long long len = (long long)d * c->pb.nodes;
+  const size_t vbytes = (size_t)len * sizeof(double);
+  if (info) {
+    info->iters = info->outer_iters = info->matvecs = 0;
+    info->history_len = 0;
+    info->launches = 0;
+    info->rel_res_true = info->rel_res = info->eta_r = info->eta_e = NAN;
+  }
+  const long long launches0 = c->own_launches + (c->p32 ? c->p32->launches : 0) +
+                              (c->p64 ? c->p64->launches : 0);
+  std::string err;
+  int rc;
+  cudaError_t e;
+  fh_status st = FH_OK;
+  double rel_true = NAN, eta_r = NAN;
+  const double* xfinal = nullptr;  // float64 device field of the result
+
+  if (c->precision == FH_FP64) {
+    st = solve_direct<double>(c, c->p64, E, tol, method, max_iter, e_init, info, rel_true, eta_r);
+    if (st == FH_ERR_CUDA || st == FH_ERR_OOM || st == FH_ERR_ARG || st == FH_ERR_TIMEOUT) return st;
+    xfinal = c->p64->x[0];
+  } else if (c->precision == FH_FP32) {
+    st = solve_direct<float>(c, c->p32, E, tol, method, max_iter, e_init, info, rel_true, eta_r);
+    if (st == FH_ERR_CUDA || st == FH_ERR_OOM || st == FH_ERR_ARG || st == FH_ERR_TIMEOUT) return st;
+    ++c->own_launches;
+    k_widen_vec<float><<<vec_grid(len), 256, 0, c->st>>>(c->p32->x[0], c->d_x64, len);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "widen");
+    xfinal = c->d_x64;
+  } else {
+    // FP32 inner solves on A d = r with a float64 outer residual r = e0 - A x
+    Pipeline<float>* P = c->p32;
+    Pipeline<double>* Q = c->p64;
+    rc = ensure_hist(P, info, err);
+    if (rc) return from_rc(c, rc, err);
+    double Ev[fh::kMaxLoads][fh::kMaxD] = {};
+    for (int a = 0; a < d; ++a) Ev[0][a] = E[a];
+    double e2 = 0.0;
+    for (int a = 0; a < d; ++a) e2 += E[a] * E[a];
+    e2 *= (double)c->pb.nodes;
+    if (e2 <= 0.0) e2 = 1.0;
+    if (e_init) {
+      e = cudaMemcpyAsync(c->d_x64, e_init, vbytes, cudaMemcpyDeviceToDevice, c->st);
+    } else {
+      ++c->own_launches;
+      k_fill_vec<<<vec_grid(len), 256, 0, c->st>>>(c->d_x64, c->pb.nodes, d, E[0], E[1], d > 2 ? E[2] : 0.0);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "initial field");
+    int total = 0, outer = 0, status = fh::kCap, hist_len = 0;
+    double prev_rel = INFINITY;
+    SolveResult res;
+    double last_alpha = 0.0, last_inner_b = 0.0;
+    for (;;) {
+      double rr;
+      const double* xin[fh::kMaxLoads] = {c->d_x64};
+      double* rout[fh::kMaxLoads] = {c->d_r64};
+      rc = Q->residual(xin, rout, false, Ev, &rr, err);
+      if (rc) return from_rc(c, rc, err);
+      rel_true = std::sqrt(rr / e2);
+      if (!std::isfinite(rel_true)) { status = fh::kBreakdown; break; }
+      if (rel_true <= tol) { status = fh::kConverged; break; }
+      if (total >= max_iter) { status = fh::kCap; break; }
+      if (outer > 0 && !(rel_true < 0.9 * prev_rel)) {
+        // the float64 residual stopped improving: float32 accuracy exhausted
+        status = res.status == fh::kBreakdown ? fh::kBreakdown : fh::kCap;
+        break;
+      }
+      prev_rel = rel_true;
+      // inner tolerance relative to the current residual: aim a little past
+      // the target, never below what float32 can resolve
+      double eta = 0.3 * tol / rel_true;
+      if (eta < 2e-6) eta = 2e-6;
+      if (eta > 0.1) eta = 0.1;
+      ++c->own_launches;
+      k_to_float<<<vec_grid(len), 256, 0, c->st>>>(c->d_r64, P->rhs[0], P->x[0], len);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "refine init");
+      rc = P->solve(method, Ev, true, method == fh::kFixed ? fh::kX0Rhs : fh::kX0Zero, nullptr, eta,
+                    max_iter - total, &res, err);
+      if (rc) return from_rc(c, rc, err);
+      total += res.iters;
+      hist_len = res.iters + 1;
+      last_alpha = res.alpha;
+      last_inner_b = rr;
+      ++c->own_launches;
+      k_add_float<<<vec_grid(len), 256, 0, c->st>>>(c->d_x64, P->x[0], len);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "refine add");
+      ++outer;
+      if (res.status == fh::kBreakdown && res.iters == 0) { status = fh::kBreakdown; break; }
+    }
+    (void)last_inner_b;
+    if (info) {
+      info->iters = total;
+      info->outer_iters = outer;
+      info->rel_res = res.rel;
+    }
+    eta_r = NAN;
+    if (method == fh::kFixed) {
+      double l0;
+      if (l0_isotropic(c->pb, l0)) eta_r = l0 * rel_true;
+    } else if (outer > 0) {
+      double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) M[i * 3 + j] = c->pb.L0[i * d + j];
+      double n2;
+      rc = P->matnorm2(P->p[0], M, &n2, err);
+      if (rc) return from_rc(c, rc, err);
+      eta_r = std::fabs(last_alpha) * std::sqrt(n2 / e2);
+    }
+    fh_status fs = finish_info(c, P, info, hist_len);
+    if (fs != FH_OK) return fs;
+    st = (fh_status)to_status(status);
+    xfinal = c->d_x64;
+  }
+
+  if (e_out) {
+    e = cudaMemcpyAsync(e_out, xfinal, vbytes, cudaMemcpyDeviceToDevice, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "output copy");
+  }
+  if (Leff_col) {
+    fh_status s2 = fh_effective_column(c, xfinal, Leff_col);
+    if (s2 != FH_OK) return s2;
+  }
+  if (info) {
+    info->rel_res_true = rel_true;
+    info->eta_r = eta_r;
+    info->status = st;
+    double eta;
+    if (fh_eta_e(c, xfinal, &eta) == FH_OK) info->eta_e = eta;
+    info->matvecs = info->iters * (method == FH_BICG ? 2 : 1) + 1 + info->outer_iters;
+    info->launches = c->own_launches + (c->p32 ? c->p32->launches : 0) +
+                     (c->p64 ? c->p64->launches : 0) - launches0;
+  }
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(c, e, "fh_solve");
+  return st;
+}
+
+fh_status fh_solve_all(fh_ctx* c, double tol, int method, int max_iter, double* Leff,
+                       fh_info* infos) {
+  if (!c || !Leff) return FH_ERR_ARG;
+  const int d = c->pb.d;
+  fh_status first = FH_OK;
+  for (int b = 0; b < d; ++b) {
+    double E[3] = {0, 0, 0};
+    E[b] = 1.0;
+    double col[3];
+    fh_status s = fh_solve(c, E, tol, method, max_iter, nullptr, nullptr, col, infos ? &infos[b] : nullptr);
+    if (s == FH_ERR_CUDA || s == FH_ERR_OOM || s == FH_ERR_ARG || s == FH_ERR_TIMEOUT) return s;
+    if (first == FH_OK && s != FH_OK) first = s;
+    for (int a = 0; a < d; ++a) Leff[a * d + b] = col[a];
+  }
+  return first;
+}
+
+fh_status fh_profile(fh_ctx* c, int dtype, int what, int reps, double* ms) {
+  if (!c || !ms || reps < 1) return FH_ERR_ARG;
+  std::string err;
+  int rc;
+  if (dtype == FH_FP64 && c->p64 && c->p64->x[0]) {
+    rc = c->p64->profile(what, reps, ms, err);
+  } else if (dtype == FH_FP32 && c->p32) {
+    rc = c->p32->profile(what, reps, ms, err);
+  } else {
+    return fail(c, FH_ERR_ARG, "no Krylov pipeline of that precision in this context");
+  }
+  return from_rc(c, rc, err);
+}
+
+fh_status fh_effective_column(fh_ctx* c, const double* e, double* col) {
+  if (!c || !e || !col) return FH_ERR_ARG;
+  std::string err;
+  int rc;
+  if (c->p64) {
+    rc = c->p64->current_mean(e, col, err);
+  } else {
+    const long long len = (long long)c->pb.d * c->pb.nodes;
+    ++c->own_launches;
+    k_convert_vec<float><<<vec_grid(len), 256, 0, c->st>>>(e, c->p32->ap[0], len);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "convert");
+    rc = c->p32->current_mean(c->p32->ap[0], col, err);
+  }
+  return from_rc(c, rc, err);
+}
+
+fh_status fh_eta_e(fh_ctx* c, const double* e, double* eta) {
+  if (!c || !e || !eta) return FH_ERR_ARG;
+  std::string err;
+  int rc;
+  if (c->p64) {
+    rc = c->p64->eta_e(e, eta, err);
+  } else {
+    const long long len = (long long)c->pb.d * c->pb.nodes;
+    ++c->own_launches;
+    k_convert_vec<float><<<vec_grid(len), 256, 0, c->st>>>(e, c->p32->ap[0], len);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "convert");
+    rc = c->p32->eta_e(c->p32->ap[0], eta, err);
+  }
+  return from_rc(c, rc, err);
+}
+
+}  // extern "C"

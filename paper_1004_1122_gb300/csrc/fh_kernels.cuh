@@ -1,0 +1,872 @@
+// fh_kernels.cuh -- the fused memory passes of the collocation operator
+//   A e = e + F^-1 [ Gamma0(k) . F(dL . e) ]         (Eq. linear_system, Eq. mtrx_B)
+// and the Krylov vector work around it (Section 2.3, Section 3).
+//
+// One application of B on a d-dimensional grid is 2d-1 passes over HBM:
+//
+//   row_fwd   lines along the contiguous last axis: gather dL[phase] (d x d),
+//             tau = dL e (optionally fused with the CG direction update
+//             p = r + beta p), pack two real channels per complex sequence,
+//             forward FFT, unpack to the half spectrum k_last in [0, (n+1)/2)
+//             and store it in the tiled spectrum layout below.
+//   col(mid)  3-D only: forward FFT along axis 1 on contiguous tiles.
+//   col(last) forward FFT along axis 0, Green projection
+//             y^(k) = xi (xi . tau^(k)) / (xi . L0 . xi) / |N|, zero at k = 0
+//             (Section 2.1), inverse FFT along axis 0.
+//   col(mid)  3-D only: inverse FFT along axis 1.
+//   row_inv   inverse FFT of each line (rebuilding the Hermitian spectrum of
+//             two real channels at once), then a fused epilogue: e + y,
+//             e + dL y (transpose), A p with (p, A p), the fixed-point update
+//             e <- e0 - y, or the residual e0 - e - y, with float64 dot
+//             partials per CTA.
+//
+// Spectrum layout (complex, element type T):
+//   S[((t * nlines + line) * C + c) * M + m]
+// line = i0 * n1 + i1 is the index of a line along the last axis (2-D: n1 = 1),
+// k_last = t * C + c is the half-spectrum frequency (tiles of C, padded),
+// m in [0, M) is the real channel (load l = m / d, component a = m % d).
+// For a fixed tile t, the Green pass reads the whole axis-0 column of C
+// frequencies x M channels as one contiguous block (2-D) or as contiguous
+// chunks of G * C * M (3-D), and the row passes touch contiguous runs of
+// lines_per_cta * C * M elements.
+#pragma once
+
+#include "fh_fft.cuh"
+
+namespace fh {
+
+constexpr int kMaxLoads = 3;
+constexpr int kMaxD = 3;
+constexpr int kMaxChannels = kMaxLoads * kMaxD;
+constexpr int kRedThreads = 256;
+constexpr int kRowMaxThreads = 512;   // row passes: <= 128 registers per thread
+constexpr int kColMaxThreads = 768;   // column passes: <= 85 registers per thread
+
+// ----------------------------------------------------------------------------
+// device scalars of one Krylov solve (one per load)
+// ----------------------------------------------------------------------------
+struct Scal {
+  double rr;       // (r, r)
+  double rho;      // BiCG (r, r*)
+  double den;      // (A p, p) or (A p, p*)
+  double alpha;
+  double beta;
+  double b2;       // ||rhs||^2, denominator of the relative residual
+  double tol2;     // tol^2
+  double rel;      // last relative residual
+  double rel_true; // last true residual (set by residual kernels)
+  int iter;
+  int max_iter;
+  int done;        // 0 running, 1 converged, 2 breakdown, 3 iteration cap
+  int hist_cap;
+  double* hist;    // device history array or nullptr
+  double E[3];     // constant right-hand side (macroscopic field) when no rhs field
+};
+
+enum : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kCap = 3 };
+
+struct Mat3 {
+  double v[9];
+};
+
+// ----------------------------------------------------------------------------
+// launch descriptors (plain structs passed by value)
+// ----------------------------------------------------------------------------
+struct Geom {
+  int d;
+  int n[3];
+  int nlast, H, C, Tt;
+  int nlines;     // |N| / nlast
+  int n1;         // 3-D: n[1]; 2-D: 1
+  long long nodes;
+  int M;          // channels = d * nloads
+  int nloads;
+  double invY[3];
+  double L0[9];
+  double inv_nodes;
+};
+
+template <typename T> struct RowArgs {
+  Geom g;
+  FFTPlan plan;
+  int lpc;        // lines per CTA
+  int tpl;        // threads per sequence
+  int nseq;       // complex sequences per CTA
+  const cplx<T>* tw;
+  cplx<T>* S;
+  const uint8_t* phase;
+  const T* tab;   // per-phase d x d table (dL, or L for the equilibrium norm), T
+  int nphase;
+  // per-load vectors (meaning depends on the mode)
+  const T* in[kMaxLoads];
+  T* out[kMaxLoads];
+  const T* aux[kMaxLoads];
+  T* aux2[kMaxLoads];
+  const T* rhs[kMaxLoads];   // field right-hand side or nullptr for constant scal[l].E
+  Scal* scal;               // nloads entries
+  double* part;             // partials [nloads][gridDim.x]
+};
+
+struct ColArgsBase {
+  Geom g;
+  FFTPlan plan;
+  int Q;          // columns per CTA
+  int tpc;        // threads per column
+  int G;          // 3-D: lines along axis 1 grouped per CTA in the last pass
+  long long stride_i;
+  int nb_inner;
+  long long base_outer, base_inner;
+  int axis;       // FFT axis of this pass (0 = Green axis, 1 = middle axis)
+};
+
+template <typename T> struct ColArgs {
+  ColArgsBase b;
+  const cplx<T>* tw;
+  cplx<T>* S;
+  Scal* scal;
+  double* part;
+};
+
+// ----------------------------------------------------------------------------
+// small helpers
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ bool all_done(const Scal* s, int nloads) {
+  if (s == nullptr) return false;
+  for (int l = 0; l < nloads; ++l)
+    if (s[l].done == kRunning) return false;
+  return true;
+}
+
+__device__ __forceinline__ int signed_freq(int j, int n) { return j <= (n - 1) / 2 ? j : j - n; }
+
+// Dot-product accumulator.  float64 work accumulates directly; float32 work
+// sums short runs (at most kRun terms) in float32 and folds each run into a
+// float64 total, so the per-element cost stays on the float32 pipe (float64
+// throughput is ~60x lower on this part) while the total is float64.
+template <typename T> struct DotAcc {
+  double total = 0.0;
+  __device__ __forceinline__ void add(T x) { total += (double)x; }
+  __device__ __forceinline__ double get() const { return total; }
+};
+template <> struct DotAcc<float> {
+  static constexpr int kRun = 32;
+  double total = 0.0;
+  float run = 0.0f;
+  int cnt = 0;
+  __device__ __forceinline__ void add(float x) {
+    run += x;
+    if (++cnt == kRun) { total += (double)run; run = 0.0f; cnt = 0; }
+  }
+  __device__ __forceinline__ double get() const { return total + (double)run; }
+};
+
+// Block-wide float64 sum of up to kMaxLoads values; thread 0 writes
+// part[l * gridDim.x + blockIdx.x].
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], int nv, double* part,
+                                                   int nblocks, int blk) {
+  __shared__ double red[32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double x = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp][i] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double x = lane < nw ? red[lane][i] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0 && i < nv) part[(long long)i * nblocks + blk] = x;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// row forward pass
+// ----------------------------------------------------------------------------
+enum : int {
+  kProApply = 0,     // tau = tab . in
+  kProPlain = 1,     // tau = in
+  kProDir = 2,       // p = r + beta p (in = r, out = p); tau = tab . p
+  kProDirPlain = 3   // p = r + beta p; tau = p
+};
+
+template <typename T, int D, int NL, int PRO>
+__global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  T* stab = reinterpret_cast<T*>(sm + (size_t)a.nseq * a.plan.n);
+  const Geom& g = a.g;
+  if (all_done(a.scal, NL)) return;
+  const int n = a.plan.n;
+  constexpr int d = D, M = D * NL;
+  const int line0 = blockIdx.x * a.lpc;
+
+  constexpr bool kUseTab = (PRO == kProApply || PRO == kProDir);
+  constexpr bool kDir = (PRO == kProDir || PRO == kProDirPlain);
+  bool lact[NL];
+  T lbeta[NL];
+  const T* pin[NL];
+  T* pout[NL];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    lact[l] = !kDir || a.scal[l].done == kRunning;
+    lbeta[l] = kDir ? T(a.scal[l].beta) : T(0);
+    pin[l] = a.in[l];
+    pout[l] = a.out[l];
+  }
+  if (kUseTab) {
+    for (int i = threadIdx.x; i < a.nphase * d * d; i += blockDim.x) stab[i] = a.tab[i];
+  }
+  __syncthreads();
+
+  // 1. gather + polarisation into the packed sequences
+  for (int idx = threadIdx.x; idx < a.lpc * n; idx += blockDim.x) {
+    const int ll = idx / n, i = idx - ll * n;
+    const int line = line0 + ll;
+    const bool valid = line < g.nlines;
+    const long long off = (long long)line * n + i;
+    int ph = 0;
+    if (kUseTab && valid) ph = a.phase[off];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      T v[D];
+      const bool active = valid && lact[l];
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        T x = T(0);
+        if (valid) {
+          if (kDir) {
+            const T r = pin[l][c * g.nodes + off];
+            const T p = pout[l][c * g.nodes + off];
+            x = r + lbeta[l] * p;
+            if (active) pout[l][c * g.nodes + off] = x;
+          } else {
+            x = pin[l][c * g.nodes + off];
+          }
+        }
+        v[c] = x;
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        T t = v[c];
+        if (kUseTab) {
+          t = T(0);
+          const T* row = stab + (ph * D + c) * D;
+#pragma unroll
+          for (int b2 = 0; b2 < D; ++b2) t += row[b2] * v[b2];
+        }
+        const int gch = ll * M + l * D + c;
+        T* dst = reinterpret_cast<T*>(&sm[(size_t)(gch >> 1) * n + i]);
+        dst[gch & 1] = t;
+      }
+    }
+  }
+  // zero the imaginary half of a trailing unpaired channel
+  if ((a.lpc * M) & 1) {
+    const int s = a.nseq - 1;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sm[(size_t)s * n + i].y = T(0);
+  }
+  __syncthreads();
+
+  // 2. forward FFT of every sequence
+  {
+    const int s = threadIdx.x / a.tpl;
+    const int u = s < a.nseq ? threadIdx.x - s * a.tpl : n;  // idle threads never touch smem
+    run_fft<false, T>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
+  }
+
+  // 3. unpack two real spectra per sequence and store the half spectrum
+  const int CM = g.C * M;
+  const int per_t = a.lpc * CM;
+  for (int idx = threadIdx.x; idx < g.Tt * per_t; idx += blockDim.x) {
+    const int t = idx / per_t;
+    int rem = idx - t * per_t;
+    const int ll = rem / CM;
+    rem -= ll * CM;
+    const int c = rem / M, m = rem - c * M;
+    const int line = line0 + ll;
+    if (line >= g.nlines) continue;
+    const int kx = t * g.C + c;
+    C val;
+    val.x = T(0);
+    val.y = T(0);
+    if (kx < g.H) {
+      const int gch = ll * M + m;
+      const C* seq = sm + (size_t)(gch >> 1) * n;
+      const C z1 = seq[kx];
+      const C z2 = seq[kx == 0 ? 0 : n - kx];
+      if ((gch & 1) == 0) {
+        val.x = T(0.5) * (z1.x + z2.x);
+        val.y = T(0.5) * (z1.y - z2.y);
+      } else {
+        val.x = T(0.5) * (z1.y + z2.y);
+        val.y = T(0.5) * (z2.x - z1.x);
+      }
+    }
+    a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m] = val;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// column passes
+// ----------------------------------------------------------------------------
+enum : int { kColFwd = 0, kColInv = 1, kColGreen = 2, kColEta = 3 };
+
+template <typename T, int D, int CM_>
+__global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const ColArgsBase& b = a.b;
+  const Geom& g = b.g;
+  if (all_done(a.scal, g.nloads)) return;
+  constexpr int d = D;
+  const int n = b.plan.n, Q = b.Q;
+  const int blk_outer = blockIdx.x / b.nb_inner;
+  const int blk_inner = blockIdx.x - blk_outer * b.nb_inner;
+  const long long base = blk_outer * b.base_outer + blk_inner * b.base_inner;
+  // columns that fall outside the grid (partial G group in 3-D) are zero
+  int qvalid = Q;
+  if (b.axis == 0 && D == 3) {
+    const int lines_left = g.n1 - blk_inner * b.G;
+    const int gv = lines_left < b.G ? lines_left : b.G;
+    qvalid = gv * g.C * g.M;
+  }
+
+  for (int idx = threadIdx.x; idx < n * Q; idx += blockDim.x) {
+    const int i = idx / Q, q = idx - i * Q;
+    C v;
+    v.x = T(0);
+    v.y = T(0);
+    if (q < qvalid) v = a.S[base + i * b.stride_i + q];
+    sm[idx] = v;
+  }
+  __syncthreads();
+
+  const int q = threadIdx.x % Q;
+  const int u0 = threadIdx.x / Q;
+  const int u = u0 < b.tpc ? u0 : n;
+  if (CM_ == kColFwd || CM_ == kColGreen || CM_ == kColEta)
+    run_fft<false, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+  else
+    run_fft<true, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+
+  if (CM_ == kColGreen || CM_ == kColEta) {
+    const int M = g.M;
+    const int t = blk_outer;
+    const int ngrp = Q / D;  // groups of D components sharing one frequency
+    T invY[D], L0[D * D];
+#pragma unroll
+    for (int p = 0; p < D; ++p) invY[p] = T(g.invY[p]);
+#pragma unroll
+    for (int p = 0; p < D; ++p)
+#pragma unroll
+      for (int r = 0; r < D; ++r) L0[p * D + r] = T(g.L0[p * 3 + r]);
+    const T inv_nodes = T(g.inv_nodes);
+    double acc[2] = {0.0, 0.0};
+    for (int idx = threadIdx.x; idx < n * ngrp; idx += blockDim.x) {
+      const int i = idx / ngrp, grp = idx - i * ngrp;
+      const int q0 = grp * D;
+      const int gl = q0 / (g.C * M);
+      const int c = (q0 / M) % g.C;
+      const int kl = t * g.C + c;
+      const int k0 = signed_freq(i, n);
+      const int k1 = D == 2 ? kl : signed_freq(blk_inner * b.G + gl, g.n[1]);
+      T xi[D];
+      xi[0] = T(k0) * invY[0];
+      xi[1] = T(k1) * invY[1];
+      if (D == 3) xi[D - 1] = T(kl) * invY[D - 1];
+      C* cell = sm + (size_t)i * Q + q0;
+      const bool pad = kl >= g.H;
+      if (CM_ == kColGreen) {
+        T den = T(0);
+#pragma unroll
+        for (int p = 0; p < D; ++p) {
+          T row = T(0);
+#pragma unroll
+          for (int r = 0; r < D; ++r) row += L0[p * D + r] * xi[r];
+          den += xi[p] * row;
+        }
+        T sre = T(0), sim = T(0);
+#pragma unroll
+        for (int p = 0; p < D; ++p) {
+          sre += xi[p] * cell[p].x;
+          sim += xi[p] * cell[p].y;
+        }
+        const bool zero = pad || (k0 == 0 && k1 == 0 && kl == 0);
+        const T f = zero ? T(0) : inv_nodes / den;
+#pragma unroll
+        for (int p = 0; p < D; ++p) {
+          cell[p].x = xi[p] * sre * f;
+          cell[p].y = xi[p] * sim * f;
+        }
+      } else {
+        if (!pad) {
+          double dre = 0.0, dim = 0.0;
+#pragma unroll
+          for (int p = 0; p < D; ++p) {
+            dre += (double)xi[p] * (double)cell[p].x;
+            dim += (double)xi[p] * (double)cell[p].y;
+          }
+          const double w = kl == 0 ? 1.0 : 2.0;  // half spectrum: k and -k
+          acc[0] += w * (dre * dre + dim * dim);
+          if (k0 == 0 && k1 == 0 && kl == 0) {
+#pragma unroll
+            for (int p = 0; p < D; ++p)
+              acc[1] += (double)cell[p].x * cell[p].x + (double)cell[p].y * cell[p].y;
+          }
+        }
+      }
+    }
+    if (CM_ == kColEta) {
+      block_reduce_store<2>(acc, 2, a.part, gridDim.x, blockIdx.x);
+      return;
+    }
+    __syncthreads();
+    run_fft<true, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+  }
+
+  for (int idx = threadIdx.x; idx < n * Q; idx += blockDim.x) {
+    const int i = idx / Q, qq = idx - i * Q;
+    if (qq < qvalid) a.S[base + i * b.stride_i + qq] = sm[idx];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// row inverse pass with fused epilogues
+// ----------------------------------------------------------------------------
+enum : int {
+  kEpiApply = 0,    // out = in + y
+  kEpiApplyT = 1,   // out = in + tab . y
+  kEpiDir = 2,      // out = in + y (A p), dot (in, out)
+  kEpiDirShadow = 3,// out = in + y (A p), dot (out, aux)  [BiCG: (A p, p*)]
+  kEpiFixed = 4,    // out = rhs - y, dot |out - in|^2     [FFTH]
+  kEpiResid = 5     // out = rhs - in - y, dot |out|^2     [residual]
+};
+
+template <typename T, int D, int NL, int EPI>
+__global__ void __launch_bounds__(kRowMaxThreads) k_row_inv(RowArgs<T> a) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  T* stab = reinterpret_cast<T*>(sm + (size_t)a.nseq * a.plan.n);
+  const Geom& g = a.g;
+  if (all_done(a.scal, NL)) return;
+  const int n = a.plan.n;
+  constexpr int d = D, M = D * NL;
+  const int line0 = blockIdx.x * a.lpc;
+  const int nch = a.lpc * M;
+
+  if (EPI == kEpiApplyT) {
+    for (int i = threadIdx.x; i < a.nphase * D * D; i += blockDim.x) stab[i] = a.tab[i];
+  }
+
+  // 1. rebuild the full spectrum of each packed sequence from the half spectra
+  const int per_t = a.nseq * g.C;
+  for (int idx = threadIdx.x; idx < g.Tt * per_t; idx += blockDim.x) {
+    const int t = idx / per_t;
+    const int rem = idx - t * per_t;
+    const int s = rem / g.C, c = rem - s * g.C;
+    const int kx = t * g.C + c;
+    if (kx >= g.H) continue;
+    C y0, y1;
+    y0.x = y0.y = y1.x = y1.y = T(0);
+    const int g0 = 2 * s, g1 = 2 * s + 1;
+    {
+      const int ll = g0 / M, m = g0 - ll * M;
+      const int line = line0 + ll;
+      if (line < g.nlines) y0 = a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m];
+    }
+    if (g1 < nch) {
+      const int ll = g1 / M, m = g1 - ll * M;
+      const int line = line0 + ll;
+      if (line < g.nlines) y1 = a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m];
+    }
+    C* seq = sm + (size_t)s * n;
+    if (kx == 0) {
+      C w;
+      w.x = y0.x;
+      w.y = y1.x;
+      seq[0] = w;
+    } else {
+      C w, wm;
+      w.x = y0.x - y1.y;
+      w.y = y0.y + y1.x;
+      wm.x = y0.x + y1.y;
+      wm.y = y1.x - y0.y;
+      seq[kx] = w;
+      seq[n - kx] = wm;
+    }
+  }
+  __syncthreads();
+
+  // 2. inverse FFT
+  {
+    const int s = threadIdx.x / a.tpl;
+    const int u = s < a.nseq ? threadIdx.x - s * a.tpl : n;
+    run_fft<true, T>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
+  }
+
+  // 3. epilogue
+  constexpr bool kDot = (EPI == kEpiDir || EPI == kEpiDirShadow || EPI == kEpiFixed || EPI == kEpiResid);
+  DotAcc<T> acc[NL];
+  bool lact[NL];
+  const T* pin[NL];
+  T* pout[NL];
+  const T* paux[NL];
+  const T* prhs[NL];
+  T Ec[NL][D];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    lact[l] = !kDot || a.scal == nullptr || a.scal[l].done == kRunning;
+    pin[l] = a.in[l];
+    pout[l] = a.out[l];
+    paux[l] = a.aux[l];
+    prhs[l] = a.rhs[l];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      Ec[l][c] = (a.scal != nullptr && (EPI == kEpiFixed || EPI == kEpiResid)) ? T(a.scal[l].E[c]) : T(0);
+  }
+  for (int idx = threadIdx.x; idx < a.lpc * n; idx += blockDim.x) {
+    const int ll = idx / n, i = idx - ll * n;
+    const int line = line0 + ll;
+    if (line >= g.nlines) continue;
+    const long long off = (long long)line * n + i;
+    int ph = 0;
+    if (EPI == kEpiApplyT) ph = a.phase[off];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      if (!lact[l]) continue;
+      T y[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const int gch = ll * M + l * D + c;
+        const T* src = reinterpret_cast<const T*>(&sm[(size_t)(gch >> 1) * n + i]);
+        y[c] = src[gch & 1];
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const long long o = c * g.nodes + off;
+        if (EPI == kEpiApply) {
+          pout[l][o] = pin[l][o] + y[c];
+        } else if (EPI == kEpiApplyT) {
+          const T* row = stab + (ph * D + c) * D;
+          T t = T(0);
+#pragma unroll
+          for (int b2 = 0; b2 < D; ++b2) t += row[b2] * y[b2];
+          pout[l][o] = pin[l][o] + t;
+        } else if (EPI == kEpiDir) {
+          const T p = pin[l][o];
+          const T ap = p + y[c];
+          pout[l][o] = ap;
+          acc[l].add(p * ap);
+        } else if (EPI == kEpiDirShadow) {
+          const T p = pin[l][o];
+          const T ap = p + y[c];
+          pout[l][o] = ap;
+          acc[l].add(ap * paux[l][o]);
+        } else if (EPI == kEpiFixed) {
+          const T e = pin[l][o];
+          const T rhs = prhs[l] ? prhs[l][o] : Ec[l][c];
+          const T en = rhs - y[c];
+          pout[l][o] = en;
+          const T df = en - e;
+          acc[l].add(df * df);
+        } else {  // kEpiResid
+          const T e = pin[l][o];
+          const T rhs = prhs[l] ? prhs[l][o] : Ec[l][c];
+          const T r = rhs - e - y[c];
+          pout[l][o] = r;
+          acc[l].add(r * r);
+        }
+      }
+    }
+  }
+  if (kDot) {
+    double tot[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) tot[l] = acc[l].get();
+    block_reduce_store<NL>(tot, NL, a.part, gridDim.x, blockIdx.x);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// vector kernels (grid-stride, float64 dot partials)
+// ----------------------------------------------------------------------------
+struct VecArgsBase {
+  long long len;   // elements per load vector (d * |N|)
+  int nloads;
+};
+
+template <typename T> struct VecArgs {
+  VecArgsBase b;
+  T* x[kMaxLoads];
+  T* r[kMaxLoads];
+  const T* p[kMaxLoads];
+  const T* ap[kMaxLoads];
+  T* rs[kMaxLoads];        // BiCG shadow residual
+  const T* atps[kMaxLoads];// BiCG A^T p*
+  Scal* scal;
+  double* part;            // [2][nloads][grid]
+};
+
+// CG: x += alpha p; r -= alpha A p; partial (r, r)
+template <typename T, int NL>
+__global__ void k_cg_update(VecArgs<T> a) {
+  if (all_done(a.scal, NL)) return;
+  double acc[NL];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    acc[l] = 0.0;
+    if (a.scal[l].done != kRunning) continue;
+    const T al = T(a.scal[l].alpha);
+    T* x = a.x[l];
+    T* r = a.r[l];
+    const T* p = a.p[l];
+    const T* ap = a.ap[l];
+    DotAcc<T> dot;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.b.len;
+         i += (long long)gridDim.x * blockDim.x) {
+      x[i] += al * p[i];
+      const T rn = r[i] - al * ap[i];
+      r[i] = rn;
+      dot.add(rn * rn);
+    }
+    acc[l] = dot.get();
+  }
+  block_reduce_store<NL>(acc, NL, a.part, gridDim.x, blockIdx.x);
+}
+
+// BiCG: x += alpha p; r -= alpha A p; r* -= alpha A^T p*; partials (r, r*), (r, r)
+// partial layout: (r, r*) of load l at slot l, (r, r) at slot kMaxLoads + l.
+template <typename T, int NL>
+__global__ void k_bicg_update(VecArgs<T> a) {
+  if (all_done(a.scal, NL)) return;
+  double acc[2 * kMaxLoads];
+#pragma unroll
+  for (int i = 0; i < 2 * kMaxLoads; ++i) acc[i] = 0.0;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    if (a.scal[l].done != kRunning) continue;
+    const T al = T(a.scal[l].alpha);
+    T* x = a.x[l];
+    T* r = a.r[l];
+    T* rs = a.rs[l];
+    const T* p = a.p[l];
+    const T* ap = a.ap[l];
+    const T* atps = a.atps[l];
+    DotAcc<T> d1, d2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.b.len;
+         i += (long long)gridDim.x * blockDim.x) {
+      x[i] += al * p[i];
+      const T rn = r[i] - al * ap[i];
+      const T sn = rs[i] - al * atps[i];
+      r[i] = rn;
+      rs[i] = sn;
+      d1.add(rn * sn);
+      d2.add(rn * rn);
+    }
+    acc[l] = d1.get();
+    acc[kMaxLoads + l] = d2.get();
+  }
+  block_reduce_store<2 * kMaxLoads>(acc, 2 * kMaxLoads, a.part, gridDim.x, blockIdx.x);
+}
+
+// ----------------------------------------------------------------------------
+// scalar control kernels: one CTA of kRedThreads threads
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double reduce_parts(const double* part, int np) {
+  __shared__ double red[kRedThreads];
+  double x = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) x += part[i];
+  red[threadIdx.x] = x;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ bool finite_d(double x) { return x == x && x - x == 0.0; }
+
+__device__ __forceinline__ void record_hist(Scal& s) {
+  if (s.hist != nullptr && s.iter < s.hist_cap) s.hist[s.iter] = s.rel;
+}
+
+// After the initial residual (kEpiResid partials or a copied rhs):
+// rr = sum, rel = sqrt(rr / b2), beta = 0, iter = 0.
+static __global__ void k_scal_start(Scal* scal, const double* part, int np, int nloads, int bicg) {
+  for (int l = 0; l < nloads; ++l) {
+    const double rr = reduce_parts(part + (long long)l * np, np);
+    if (threadIdx.x == 0) {
+      Scal& s = scal[l];
+      s.rr = rr;
+      s.rho = rr;  // r0* = r0
+      s.beta = 0.0;
+      s.alpha = 0.0;
+      s.iter = 0;
+      s.rel = sqrt(rr / s.b2);
+      s.rel_true = s.rel;
+      record_hist(s);
+      if (!finite_d(rr)) s.done = kBreakdown;
+      else if (rr <= s.tol2 * s.b2) s.done = kConverged;
+      else if (s.max_iter <= 0) s.done = kCap;
+      else s.done = kRunning;
+    }
+  }
+  (void)bicg;
+}
+
+// alpha = (r, r) / (A p, p) for CG; alpha = (r, r*) / (A p, p*) for BiCG
+static __global__ void k_scal_alpha(Scal* scal, const double* part, int np, int nloads, int bicg) {
+  for (int l = 0; l < nloads; ++l) {
+    const double den = reduce_parts(part + (long long)l * np, np);
+    if (threadIdx.x == 0) {
+      Scal& s = scal[l];
+      if (s.done != kRunning) continue;
+      s.den = den;
+      const double num = bicg ? s.rho : s.rr;
+      if (!finite_d(den) || (!bicg && den <= 0.0) || den == 0.0) {
+        s.done = kBreakdown;
+      } else {
+        s.alpha = num / den;
+      }
+    }
+  }
+}
+
+// CG: beta = (r+, r+) / (r, r); convergence on the recursive residual.
+// BiCG: beta = (r+, r*+) / (r, r*); convergence on (r+, r+).
+static __global__ void k_scal_beta(Scal* scal, const double* part, int np, int nloads, int bicg) {
+  for (int l = 0; l < nloads; ++l) {
+    double rho_new = 0.0, rr_new;
+    if (bicg) {
+      rho_new = reduce_parts(part + (long long)l * np, np);
+      rr_new = reduce_parts(part + (long long)(kMaxLoads + l) * np, np);
+    } else {
+      rr_new = reduce_parts(part + (long long)l * np, np);
+    }
+    if (threadIdx.x == 0) {
+      Scal& s = scal[l];
+      if (s.done != kRunning) continue;
+      s.iter += 1;
+      s.rel = sqrt(rr_new / s.b2);
+      record_hist(s);
+      if (!finite_d(rr_new)) { s.done = kBreakdown; continue; }
+      if (rr_new <= s.tol2 * s.b2) { s.rr = rr_new; s.done = kConverged; continue; }
+      if (s.iter >= s.max_iter) { s.rr = rr_new; s.done = kCap; continue; }
+      if (bicg) {
+        if (!finite_d(rho_new) || rho_new == 0.0) { s.done = kBreakdown; continue; }
+        s.beta = rho_new / s.rho;
+        s.rho = rho_new;
+        s.rr = rr_new;
+      } else {
+        s.beta = rr_new / s.rr;
+        s.rr = rr_new;
+      }
+    }
+  }
+}
+
+// Fixed point: the epilogue produced ||e_new - e||^2 = ||r(e)||^2.
+static __global__ void k_scal_fixed(Scal* scal, const double* part, int np, int nloads) {
+  for (int l = 0; l < nloads; ++l) {
+    const double rr = reduce_parts(part + (long long)l * np, np);
+    if (threadIdx.x == 0) {
+      Scal& s = scal[l];
+      if (s.done != kRunning) continue;
+      s.rr = rr;
+      s.rel = sqrt(rr / s.b2);
+      record_hist(s);
+      if (!finite_d(rr)) { s.done = kBreakdown; continue; }
+      s.iter += 1;
+      if (rr <= s.tol2 * s.b2) { s.done = kConverged; continue; }
+      if (s.iter >= s.max_iter) { s.done = kCap; continue; }
+    }
+  }
+}
+
+// Reduce one partial array into out[l] (plain sum per load); used for the
+// true residual, norms, the effective tensor and the equilibrium norm.
+static __global__ void k_reduce_to(const double* part, int np, int nv, double* out) {
+  for (int v = 0; v < nv; ++v) {
+    const double x = reduce_parts(part + (long long)v * np, np);
+    if (threadIdx.x == 0) out[v] = x;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// misc elementwise kernels
+// ----------------------------------------------------------------------------
+// x[c * nodes + i] = E[c]
+template <typename T>
+__global__ void k_fill_const(T* x, long long nodes, int d, double E0, double E1, double E2) {
+  const double E[3] = {E0, E1, E2};
+  const long long len = nodes * d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = T(E[i / nodes]);
+}
+
+// partial sums of (Tab[phase] e)_c over nodes, c < D (effective tensor column)
+template <typename T, int D>
+__global__ void k_current_sum(const T* e, const uint8_t* phase, const double* tab, long long nodes,
+                              double* part) {
+  double acc[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) acc[c] = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ph = phase[i];
+    double v[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) v[c] = (double)e[c * nodes + i];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int b2 = 0; b2 < D; ++b2) s += tab[(ph * D + c) * D + b2] * v[b2];
+      acc[c] += s;
+    }
+  }
+  block_reduce_store<D>(acc, D, part, gridDim.x, blockIdx.x);
+}
+
+// partial sums of |M e|^2 with a constant D x D matrix (norms, eta_r numerator)
+template <typename T, int D>
+__global__ void k_matnorm2(const T* e, long long nodes, Mat3 m, double* part) {
+  T Mx[D * D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) Mx[i * D + j] = T(m.v[i * 3 + j]);
+  DotAcc<T> dot;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+       i += (long long)gridDim.x * blockDim.x) {
+    T v[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) v[c] = e[c * nodes + i];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T s = T(0);
+#pragma unroll
+      for (int b2 = 0; b2 < D; ++b2) s += Mx[c * D + b2] * v[b2];
+      dot.add(s * s);
+    }
+  }
+  double acc[1] = {dot.get()};
+  block_reduce_store<1>(acc, 1, part, gridDim.x, blockIdx.x);
+}
+
+}  // namespace fh

@@ -1,0 +1,45 @@
+// fh_launch.cuh -- per (precision, dimension, load count) launch table.
+// The pass kernels are templates over D (2 or 3) and NL (loads per launch);
+// each combination is compiled in its own translation unit and reached
+// through a table of host function pointers.
+#pragma once
+
+#include "fh_kernels.cuh"
+
+namespace fh {
+
+struct Launch {
+  int grid = 0, block = 0;
+  size_t smem = 0;
+};
+
+template <typename T>
+struct LaunchTable {
+  int D = 0, NL = 0;
+  cudaError_t (*set_smem)(size_t row_smem, size_t col0_smem, size_t col1_smem) = nullptr;
+  cudaError_t (*row_fwd)(int pro, const Launch&, const RowArgs<T>&, cudaStream_t) = nullptr;
+  cudaError_t (*row_inv)(int epi, const Launch&, const RowArgs<T>&, cudaStream_t) = nullptr;
+  cudaError_t (*col)(int mode, const Launch&, const ColArgs<T>&, cudaStream_t) = nullptr;
+  cudaError_t (*cg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
+  cudaError_t (*bicg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
+  cudaError_t (*current_sum)(const Launch&, const T*, const uint8_t*, const double*, long long,
+                             double*, cudaStream_t) = nullptr;
+  cudaError_t (*matnorm2)(const Launch&, const T*, long long, const Mat3&, double*,
+                          cudaStream_t) = nullptr;
+};
+
+// Supported (D, NL): (2, 1), (2, 2), (3, 1), (3, 3).
+LaunchTable<float> launch_table_f32_d2(int nl);
+LaunchTable<float> launch_table_f32_d3(int nl);
+LaunchTable<double> launch_table_f64_d2(int nl);
+LaunchTable<double> launch_table_f64_d3(int nl);
+
+template <typename T> LaunchTable<T> launch_table(int d, int nl);
+template <> inline LaunchTable<float> launch_table<float>(int d, int nl) {
+  return d == 2 ? launch_table_f32_d2(nl) : launch_table_f32_d3(nl);
+}
+template <> inline LaunchTable<double> launch_table<double>(int d, int nl) {
+  return d == 2 ? launch_table_f64_d2(nl) : launch_table_f64_d3(nl);
+}
+
+}  // namespace fh

@@ -1,0 +1,117 @@
+// fh_launch_impl.cuh -- launcher templates behind LaunchTable; included by the
+// four fh_launch_*.cu translation units only.
+#pragma once
+
+#include "fh_launch.cuh"
+
+namespace fh {
+
+// Raise the dynamic shared-memory limit of a kernel to everything the device
+// allows (minus its static shared memory), so contexts of different sizes in
+// one process never lower each other's limit.  `bytes` is the size this
+// context needs; it must fit.
+template <typename K>
+static cudaError_t opt_in_smem(K kernel, size_t bytes) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const size_t cap = (size_t)optin - fa.sharedSizeBytes;
+  if (bytes > cap) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+}
+
+template <typename T, int D, int NL>
+struct Launchers {
+  static cudaError_t set_smem(size_t rs, size_t c0, size_t c1) {
+    cudaError_t e;
+#define FH_SM(K, B) \
+  if ((e = opt_in_smem(K, B)) != cudaSuccess) return e;
+    FH_SM((k_row_fwd<T, D, NL, kProApply>), rs)
+    FH_SM((k_row_fwd<T, D, NL, kProPlain>), rs)
+    FH_SM((k_row_fwd<T, D, NL, kProDir>), rs)
+    FH_SM((k_row_fwd<T, D, NL, kProDirPlain>), rs)
+    FH_SM((k_row_inv<T, D, NL, kEpiApply>), rs)
+    FH_SM((k_row_inv<T, D, NL, kEpiApplyT>), rs)
+    FH_SM((k_row_inv<T, D, NL, kEpiDir>), rs)
+    FH_SM((k_row_inv<T, D, NL, kEpiDirShadow>), rs)
+    FH_SM((k_row_inv<T, D, NL, kEpiFixed>), rs)
+    FH_SM((k_row_inv<T, D, NL, kEpiResid>), rs)
+    FH_SM((k_col<T, D, kColGreen>), c0)
+    FH_SM((k_col<T, D, kColEta>), c0)
+    FH_SM((k_col<T, D, kColFwd>), c1)
+    FH_SM((k_col<T, D, kColInv>), c1)
+#undef FH_SM
+    return cudaSuccess;
+  }
+  static cudaError_t row_fwd(int pro, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
+    switch (pro) {
+      case kProApply: k_row_fwd<T, D, NL, kProApply><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kProPlain: k_row_fwd<T, D, NL, kProPlain><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kProDir: k_row_fwd<T, D, NL, kProDir><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kProDirPlain: k_row_fwd<T, D, NL, kProDirPlain><<<L.grid, L.block, L.smem, st>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  static cudaError_t row_inv(int epi, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
+    switch (epi) {
+      case kEpiApply: k_row_inv<T, D, NL, kEpiApply><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kEpiApplyT: k_row_inv<T, D, NL, kEpiApplyT><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kEpiDir: k_row_inv<T, D, NL, kEpiDir><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kEpiDirShadow: k_row_inv<T, D, NL, kEpiDirShadow><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kEpiFixed: k_row_inv<T, D, NL, kEpiFixed><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kEpiResid: k_row_inv<T, D, NL, kEpiResid><<<L.grid, L.block, L.smem, st>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  static cudaError_t col(int mode, const Launch& L, const ColArgs<T>& a, cudaStream_t st) {
+    switch (mode) {
+      case kColFwd: k_col<T, D, kColFwd><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kColInv: k_col<T, D, kColInv><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kColGreen: k_col<T, D, kColGreen><<<L.grid, L.block, L.smem, st>>>(a); break;
+      case kColEta: k_col<T, D, kColEta><<<L.grid, L.block, L.smem, st>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  static cudaError_t cg_update(const Launch& L, const VecArgs<T>& v, cudaStream_t st) {
+    k_cg_update<T, NL><<<L.grid, L.block, 0, st>>>(v);
+    return cudaGetLastError();
+  }
+  static cudaError_t bicg_update(const Launch& L, const VecArgs<T>& v, cudaStream_t st) {
+    k_bicg_update<T, NL><<<L.grid, L.block, 0, st>>>(v);
+    return cudaGetLastError();
+  }
+  static cudaError_t current_sum(const Launch& L, const T* e, const uint8_t* ph, const double* tab,
+                                 long long nodes, double* part, cudaStream_t st) {
+    k_current_sum<T, D><<<L.grid, L.block, 0, st>>>(e, ph, tab, nodes, part);
+    return cudaGetLastError();
+  }
+  static cudaError_t matnorm2(const Launch& L, const T* e, long long nodes, const Mat3& m,
+                              double* part, cudaStream_t st) {
+    k_matnorm2<T, D><<<L.grid, L.block, 0, st>>>(e, nodes, m, part);
+    return cudaGetLastError();
+  }
+  static LaunchTable<T> table() {
+    LaunchTable<T> t;
+    t.D = D;
+    t.NL = NL;
+    t.set_smem = &set_smem;
+    t.row_fwd = &row_fwd;
+    t.row_inv = &row_inv;
+    t.col = &col;
+    t.cg_update = &cg_update;
+    t.bicg_update = &bicg_update;
+    t.current_sum = &current_sum;
+    t.matnorm2 = &matnorm2;
+    return t;
+  }
+};
+
+}  // namespace fh

@@ -1,0 +1,142 @@
+// fh_pipeline.cuh -- per-precision pass pipeline: plans, tilings, device
+// buffers, kernel launches, and the Krylov solvers driven from the host in
+// graph-captured chunks of iterations.
+//
+// Pipeline<T> is explicitly instantiated for float and double in
+// fh_pipeline_f32.cu / fh_pipeline_f64.cu.
+#pragma once
+
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fh_launch.cuh"
+#include "fh_plan.h"
+
+namespace fh {
+
+// Host copy of one problem (Section 2.1 / 2.2 inputs) shared by both pipelines.
+struct Problem {
+  int d = 2;
+  int N[3] = {1, 1, 1};
+  double Y[3] = {1.0, 1.0, 1.0};
+  long long nodes = 0;
+  int nphase = 0;
+  std::vector<double> L;    // nphase * d * d
+  std::vector<double> L0;   // d * d
+  std::vector<double> dL;   // nphase * d * d, L - L0
+  const uint8_t* d_phase = nullptr;  // device, owned by the context
+};
+
+// Krylov methods (mirror fh_method)
+enum : int { kCG = 0, kBiCG = 1, kFixed = 2 };
+
+// How the solve starts.
+enum : int {
+  kX0Const = 0,   // x = E (cold start, e^0)
+  kX0Field = 1,   // x = given field (same precision, device)
+  kX0Zero = 2,    // x = 0 (inner refinement solve on A d = r)
+  kX0Rhs = 3,     // x = rhs field (inner fixed point starts at e^0 = rhs)
+  kX0Keep = 4     // x already holds the start (restart from the current iterate)
+};
+
+struct SolveResult {
+  int status = 0;      // kConverged / kBreakdown / kCap
+  int iters = 0;
+  double rel = 0.0;    // last recursive relative residual
+  double alpha = 0.0;
+};
+
+template <typename T>
+struct Pipeline {
+  using C = cplx<T>;
+  Geom g{};
+  FFTPlan prow{}, pcol0{}, pcol1{};
+  int lpc = 0, tpl = 0, nseq = 0;
+  Launch row{}, col0{}, col1{};
+  ColArgsBase cb0{}, cb1{};
+  C* tw_last = nullptr;
+  C* tw0 = nullptr;
+  C* tw1 = nullptr;
+  C* S = nullptr;
+  T* dtab = nullptr;   // dL per phase
+  T* ltab = nullptr;   // L per phase
+  double* ltab64 = nullptr;
+  const uint8_t* phase = nullptr;
+  int nphase = 0;
+  Scal* scal = nullptr;      // [nloads] Krylov scalars
+  Scal* scal_aux = nullptr;  // [nloads] scratch scalars for residual / norms
+  Scal* h_scal = nullptr;    // pinned host mirror
+  double* part = nullptr;
+  double* h_red = nullptr;   // pinned host mirror of small reductions
+  double* d_red = nullptr;
+  int part_stride = 0;       // max grid over all partial producers
+  int nloads = 1;
+  long long vlen = 0;        // d * nodes
+  T* x[kMaxLoads] = {};
+  T* r[kMaxLoads] = {};
+  T* p[kMaxLoads] = {};
+  T* ap[kMaxLoads] = {};
+  T* rs[kMaxLoads] = {};
+  T* ps[kMaxLoads] = {};
+  T* atps[kMaxLoads] = {};
+  T* rhs[kMaxLoads] = {};
+  double* hist = nullptr;
+  int hist_cap = 0;
+  cudaStream_t st = nullptr;
+  std::vector<void*> allocs;
+  std::map<int, cudaGraphExec_t> graphs;  // key: method * 1024 + chunk
+  Launch vec{};
+  LaunchTable<T> lt{};
+  int sms = 0;
+  bool rhs_active_ = false;
+  long long launches = 0;                    // kernels enqueued (graph replays included)
+  std::map<int, long long> graph_kernels;    // kernels per captured chunk
+
+  int init(const Problem& pb, int nloads_, bool krylov, cudaStream_t stream, std::string& err);
+  void release();
+  void set_phase(const uint8_t* d_phase) { phase = d_phase; }
+
+  // ---- one application of the operator passes --------------------------
+  RowArgs<T> row_args() const;
+  cudaError_t launch_row_fwd(int pro, const RowArgs<T>& a);
+  cudaError_t launch_row_inv(int epi, const RowArgs<T>& a);
+  cudaError_t launch_green(int mode, Scal* sc, double* pt);
+  cudaError_t passes(int pro, int epi, const RowArgs<T>& af, const RowArgs<T>& ai, Scal* sc);
+
+  // e_out = (I + B) e_in  or (I + B^T) e_in, single load, no scalars
+  cudaError_t apply(const T* in, T* out, bool transpose);
+
+  // ---- Krylov solve ------------------------------------------------------
+  // Solves A x = rhs for every load.  rhs is the constant E[l] when
+  // rhs_field is false, else the field in this->rhs[l].  x0 per kX0*.
+  int solve(int method, const double (*E)[kMaxD], bool rhs_field, int x0, const T* const* x_init,
+            double tol, int max_iter, SolveResult* res, std::string& err);
+  cudaError_t enqueue_iter(int method);
+  cudaError_t enqueue_chunk(int method, int K);
+  int chunk_size(int method) const;
+
+  // ---- reductions ---------------------------------------------------------
+  // out[l] = ||x_l||^2 (sum over the vector), synchronous
+  int norm2(T* const* v, double* out, std::string& err);
+  // ||rhs - A x||^2 per load into out (synchronous), residual field into r
+  int residual(const T* const* xin, T* const* rout, bool rhs_field, const double (*E)[kMaxD],
+               double* out, std::string& err);
+  // column of <tab e> (tab = L) in float64
+  int current_mean(const T* e, double* col, std::string& err);
+  int eta_e(const T* e, double* eta, std::string& err);
+  int matnorm2(const T* e, const double* M, double* out, std::string& err);
+
+  // ---- measurement --------------------------------------------------------
+  // Average device time (ms, CUDA events on the pipeline stream) of `reps`
+  // back-to-back launches of one piece of the CG iteration:
+  // 0 row_fwd (direction update + dL + FFT), 1 column passes (Green),
+  // 2 row_inv (inverse FFT + A p + dot), 3 CG vector update, 5 operator apply.
+  int profile(int what, int reps, double* ms, std::string& err);
+};
+
+extern template struct Pipeline<float>;
+extern template struct Pipeline<double>;
+
+}  // namespace fh

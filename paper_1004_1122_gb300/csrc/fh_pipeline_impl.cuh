@@ -1,0 +1,724 @@
+// fh_pipeline_impl.cuh -- member definitions of Pipeline<T>; included only by
+// the two explicit-instantiation translation units.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+
+#include "fh_pipeline.cuh"
+
+namespace fh {
+
+#define FH_CK(call)                               \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return e_;             \
+  } while (0)
+
+#define FH_CKS(call)                                                          \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      err = std::string(#call) + ": " + cudaGetErrorString(e_);               \
+      return 5; /* FH_ERR_CUDA */                                             \
+    }                                                                         \
+  } while (0)
+
+static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+template <typename T>
+static int dev_alloc(std::vector<void*>& allocs, T** ptr, size_t count, std::string& err) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return 4;  // FH_ERR_OOM
+  }
+  allocs.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t stream,
+                      std::string& err) {
+  st = stream;
+  nloads = nloads_;
+  const bool f64 = sizeof(T) == 8;
+  const size_t esz = sizeof(C);
+  int dev = 0;
+  FH_CKS(cudaGetDevice(&dev));
+  FH_CKS(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int optin = 0;
+  FH_CKS(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+
+  const int d = pb.d;
+  g.d = d;
+  for (int a = 0; a < 3; ++a) g.n[a] = a < d ? pb.N[a] : 1;
+  g.nlast = pb.N[d - 1];
+  g.H = (g.nlast + 1) / 2;
+  g.nodes = pb.nodes;
+  g.nlines = (int)(pb.nodes / g.nlast);
+  g.n1 = d == 3 ? pb.N[1] : 1;
+  g.M = d * nloads;
+  g.nloads = nloads;
+  for (int a = 0; a < 3; ++a) g.invY[a] = a < d ? 1.0 / pb.Y[a] : 0.0;
+  for (int i = 0; i < 9; ++i) g.L0[i] = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) g.L0[i * 3 + j] = pb.L0[i * d + j];
+  g.inv_nodes = 1.0 / (double)pb.nodes;
+  vlen = (long long)d * pb.nodes;
+  phase = pb.d_phase;
+  nphase = pb.nphase;
+  lt = launch_table<T>(d, nloads);
+  if (lt.row_fwd == nullptr) {
+    err = "unsupported number of loads per launch for this dimension";
+    return 9;
+  }
+
+  // FFT plans
+  int tpc0 = 0, tpc1 = 0;
+  if (!make_fft_plan(g.nlast, f64, kRowMaxThreads, prow, tpl) || !make_fft_plan(pb.N[0], f64, kColMaxThreads, pcol0, tpc0) ||
+      (d == 3 && !make_fft_plan(pb.N[1], f64, kColMaxThreads, pcol1, tpc1))) {
+    err = "no FFT plan for this grid (axis lengths must factor into 3, 5 and 7)";
+    return 9;  // FH_ERR_UNSUPPORTED
+  }
+  const int M = g.M;
+  const size_t smem_green = std::min<size_t>(150 * 1024, (size_t)optin - 4096);
+  // tile width C of the half spectrum
+  int Cc = 0;
+  for (int cand : {16, 8, 4, 2, 1}) {
+    const int Tt = (g.H + cand - 1) / cand;
+    const double pad = double(Tt * cand - g.H) / g.H;
+    if (cand > 1 && pad > 0.15) continue;
+    if (d == 2) {
+      if ((size_t)pb.N[0] * cand * M * esz > smem_green) continue;
+      if (round_up(cand * M * tpc0, 32) > kColMaxThreads) continue;
+    } else {
+      if ((size_t)pb.N[1] * cand * M * esz > smem_green) continue;
+      if (round_up(cand * M * tpc1, 32) > kColMaxThreads) continue;
+      if ((size_t)pb.N[0] * cand * M * esz > smem_green) continue;
+      if (round_up(cand * M * tpc0, 32) > kColMaxThreads) continue;
+    }
+    Cc = cand;
+    break;
+  }
+  if (Cc == 0) {
+    err = "grid too large for the column tiling";
+    return 9;
+  }
+  g.C = Cc;
+  g.Tt = (g.H + Cc - 1) / Cc;
+  const long long CM = (long long)Cc * M;
+
+  // row passes
+  {
+    const int per_line_thr = std::max(1, tpl * M / 2);
+    int l = std::max(1, 256 / per_line_thr);
+    const int cap = std::max(1, (g.nlines + 2 * sms - 1) / (2 * sms));
+    l = std::min(l, cap);
+    while (l > 1 && ((size_t)((l * M + 1) / 2) * g.nlast * esz > 96 * 1024)) --l;
+    if ((l * M) % 2 && l > 1) --l;
+    lpc = l;
+    nseq = (lpc * M + 1) / 2;
+    while (lpc > 1 && round_up(((lpc * M + 1) / 2) * tpl, 32) > kRowMaxThreads) --lpc;
+    nseq = (lpc * M + 1) / 2;
+    row.block = round_up(nseq * tpl, 32);
+    row.grid = (g.nlines + lpc - 1) / lpc;
+    row.smem = (size_t)nseq * g.nlast * esz + (size_t)std::max(1, nphase) * d * d * sizeof(T);
+    if (row.block > kRowMaxThreads || row.smem > (size_t)optin) {
+      err = "row pass does not fit one CTA";
+      return 9;
+    }
+  }
+  // Green pass along axis 0
+  {
+    int G = 1;
+    if (d == 3) {
+      for (int cand = g.n1; cand >= 1; --cand) {
+        if (g.n1 % cand) continue;
+        if ((size_t)pb.N[0] * cand * CM * esz > std::min<size_t>(100 * 1024, smem_green)) continue;
+        if (round_up((int)(cand * CM) * tpc0, 32) > kColMaxThreads) continue;
+        G = cand;
+        break;
+      }
+    }
+    cb0.g = g;
+    cb0.plan = pcol0;
+    cb0.Q = (int)(G * CM);
+    cb0.tpc = tpc0;
+    cb0.G = G;
+    cb0.axis = 0;
+    cb0.base_outer = (long long)g.nlines * CM;
+    if (d == 2) {
+      cb0.stride_i = CM;
+      cb0.nb_inner = 1;
+      cb0.base_inner = 0;
+    } else {
+      cb0.stride_i = (long long)g.n1 * CM;
+      cb0.nb_inner = (g.n1 + G - 1) / G;
+      cb0.base_inner = G * CM;
+    }
+    col0.block = round_up(cb0.Q * tpc0, 32);
+    col0.grid = g.Tt * cb0.nb_inner;
+    col0.smem = (size_t)pb.N[0] * cb0.Q * esz;
+  }
+  if (d == 3) {
+    cb1.g = g;
+    cb1.plan = pcol1;
+    cb1.Q = (int)CM;
+    cb1.tpc = tpc1;
+    cb1.G = 1;
+    cb1.axis = 1;
+    cb1.stride_i = CM;
+    cb1.nb_inner = pb.N[0];
+    cb1.base_outer = (long long)g.nlines * CM;
+    cb1.base_inner = (long long)g.n1 * CM;
+    col1.block = round_up(cb1.Q * tpc1, 32);
+    col1.grid = g.Tt * pb.N[0];
+    col1.smem = (size_t)pb.N[1] * cb1.Q * esz;
+  }
+  vec.block = 256;
+  vec.grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 4, (vlen + 255) / 256));
+  part_stride = std::max(std::max(row.grid, col0.grid), vec.grid);
+
+  FH_CKS(lt.set_smem(row.smem, col0.smem, d == 3 ? col1.smem : 0));
+
+  // device buffers
+  int rc;
+  const size_t spec = (size_t)g.Tt * g.C * g.nlines * M;
+  if ((rc = dev_alloc(allocs, &S, spec, err))) return rc;
+  auto upload_tw = [&](int n, C** dst) -> int {
+    std::vector<double> re, im;
+    twiddles(n, re, im);
+    std::vector<C> h(n);
+    for (int m = 0; m < n; ++m) {
+      h[m].x = T(re[m]);
+      h[m].y = T(im[m]);
+    }
+    int r2 = dev_alloc(allocs, dst, n, err);
+    if (r2) return r2;
+    FH_CKS(cudaMemcpy(*dst, h.data(), n * sizeof(C), cudaMemcpyHostToDevice));
+    return 0;
+  };
+  if ((rc = upload_tw(g.nlast, &tw_last))) return rc;
+  if ((rc = upload_tw(pb.N[0], &tw0))) return rc;
+  if (d == 3 && (rc = upload_tw(pb.N[1], &tw1))) return rc;
+  {
+    const int nt = std::max(1, nphase) * d * d;
+    std::vector<T> hd(nt), hl(nt);
+    for (int i = 0; i < nphase * d * d; ++i) {
+      hd[i] = T(pb.dL[i]);
+      hl[i] = T(pb.L[i]);
+    }
+    if ((rc = dev_alloc(allocs, &dtab, nt, err))) return rc;
+    if ((rc = dev_alloc(allocs, &ltab, nt, err))) return rc;
+    if ((rc = dev_alloc(allocs, &ltab64, nt, err))) return rc;
+    FH_CKS(cudaMemcpy(dtab, hd.data(), nt * sizeof(T), cudaMemcpyHostToDevice));
+    FH_CKS(cudaMemcpy(ltab, hl.data(), nt * sizeof(T), cudaMemcpyHostToDevice));
+    FH_CKS(cudaMemcpy(ltab64, pb.L.data(), nphase * d * d * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if ((rc = dev_alloc(allocs, &scal, kMaxLoads, err))) return rc;
+  if ((rc = dev_alloc(allocs, &scal_aux, kMaxLoads, err))) return rc;
+  if ((rc = dev_alloc(allocs, &part, (size_t)2 * kMaxLoads * part_stride, err))) return rc;
+  if ((rc = dev_alloc(allocs, &d_red, 16, err))) return rc;
+  FH_CKS(cudaMallocHost(&h_scal, 2 * kMaxLoads * sizeof(Scal)));
+  FH_CKS(cudaMallocHost(&h_red, 16 * sizeof(double)));
+  std::memset(h_scal, 0, 2 * kMaxLoads * sizeof(Scal));
+  if (krylov) {
+    for (int l = 0; l < nloads; ++l) {
+      if ((rc = dev_alloc(allocs, &x[l], vlen, err))) return rc;
+      if ((rc = dev_alloc(allocs, &r[l], vlen, err))) return rc;
+      if ((rc = dev_alloc(allocs, &p[l], vlen, err))) return rc;
+      if ((rc = dev_alloc(allocs, &ap[l], vlen, err))) return rc;
+      if ((rc = dev_alloc(allocs, &rhs[l], vlen, err))) return rc;
+    }
+  }
+  return 0;
+}
+
+template <typename T>
+void Pipeline<T>::release() {
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  graphs.clear();
+  for (void* q : allocs) cudaFree(q);
+  allocs.clear();
+  if (h_scal) cudaFreeHost(h_scal);
+  if (h_red) cudaFreeHost(h_red);
+  h_scal = nullptr;
+  h_red = nullptr;
+}
+
+template <typename T>
+RowArgs<T> Pipeline<T>::row_args() const {
+  RowArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = g;
+  a.plan = prow;
+  a.lpc = lpc;
+  a.tpl = tpl;
+  a.nseq = nseq;
+  a.tw = tw_last;
+  a.S = S;
+  a.phase = phase;
+  a.tab = dtab;
+  a.nphase = nphase;
+  a.part = part;
+  return a;
+}
+
+template <typename T>
+cudaError_t Pipeline<T>::launch_row_fwd(int pro, const RowArgs<T>& a) {
+  ++launches;
+  return lt.row_fwd(pro, row, a, st);
+}
+
+template <typename T>
+cudaError_t Pipeline<T>::launch_row_inv(int epi, const RowArgs<T>& a) {
+  ++launches;
+  return lt.row_inv(epi, row, a, st);
+}
+
+template <typename T>
+cudaError_t Pipeline<T>::launch_green(int mode, Scal* sc, double* pt) {
+  ColArgs<T> m;
+  m.b = cb1;
+  m.tw = tw1;
+  m.S = S;
+  m.scal = sc;
+  m.part = pt;
+  ColArgs<T> a;
+  a.b = cb0;
+  a.tw = tw0;
+  a.S = S;
+  a.scal = sc;
+  a.part = pt;
+  if (g.d == 3) {
+    ++launches;
+    FH_CK(lt.col(kColFwd, col1, m, st));
+  }
+  ++launches;
+  if (mode == kColEta) return lt.col(kColEta, col0, a, st);
+  FH_CK(lt.col(kColGreen, col0, a, st));
+  if (g.d == 3) {
+    ++launches;
+    FH_CK(lt.col(kColInv, col1, m, st));
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Pipeline<T>::passes(int pro, int epi, const RowArgs<T>& af, const RowArgs<T>& ai,
+                                Scal* sc) {
+  FH_CK(launch_row_fwd(pro, af));
+  FH_CK(launch_green(kColGreen, sc, nullptr));
+  FH_CK(launch_row_inv(epi, ai));
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Pipeline<T>::apply(const T* in, T* out, bool transpose) {
+  RowArgs<T> a = row_args();
+  for (int l = 0; l < kMaxLoads; ++l) {
+    a.in[l] = in;
+    a.out[l] = out;
+  }
+  a.scal = nullptr;
+  if (nloads != 1) return cudaErrorInvalidValue;
+  return passes(transpose ? kProPlain : kProApply, transpose ? kEpiApplyT : kEpiApply, a, a, nullptr);
+}
+
+template <typename T>
+int Pipeline<T>::chunk_size(int method) const {
+  int K = g.nodes >= 1000000 ? 8 : (g.nodes >= 100000 ? 16 : 32);
+  if (method == kFixed) K *= 4;
+  return K;
+}
+
+template <typename T>
+cudaError_t Pipeline<T>::enqueue_iter(int method) {
+  RowArgs<T> a = row_args();
+  a.scal = scal;
+  if (method == kCG) {
+    RowArgs<T> f = a, i = a;
+    for (int l = 0; l < nloads; ++l) {
+      f.in[l] = r[l];
+      f.out[l] = p[l];
+      i.in[l] = p[l];
+      i.out[l] = ap[l];
+    }
+    FH_CK(passes(kProDir, kEpiDir, f, i, scal));
+    ++launches;
+    k_scal_alpha<<<1, kRedThreads, 0, st>>>(scal, part, row.grid, nloads, 0);
+    FH_CK(cudaGetLastError());
+    VecArgs<T> v;
+    std::memset(&v, 0, sizeof(v));
+    v.b.len = vlen;
+    v.b.nloads = nloads;
+    for (int l = 0; l < nloads; ++l) {
+      v.x[l] = x[l];
+      v.r[l] = r[l];
+      v.p[l] = p[l];
+      v.ap[l] = ap[l];
+    }
+    v.scal = scal;
+    v.part = part;
+    ++launches;
+    FH_CK(lt.cg_update(vec, v, st));
+    ++launches;
+    k_scal_beta<<<1, kRedThreads, 0, st>>>(scal, part, vec.grid, nloads, 0);
+    return cudaGetLastError();
+  }
+  if (method == kBiCG) {
+    // A^T p* with p* = r* + beta p*
+    RowArgs<T> ft = a, it = a, f = a, i = a;
+    for (int l = 0; l < nloads; ++l) {
+      ft.in[l] = rs[l];
+      ft.out[l] = ps[l];
+      it.in[l] = ps[l];
+      it.out[l] = atps[l];
+      f.in[l] = r[l];
+      f.out[l] = p[l];
+      i.in[l] = p[l];
+      i.out[l] = ap[l];
+      i.aux[l] = ps[l];
+    }
+    FH_CK(passes(kProDirPlain, kEpiApplyT, ft, it, scal));
+    FH_CK(passes(kProDir, kEpiDirShadow, f, i, scal));
+    ++launches;
+    k_scal_alpha<<<1, kRedThreads, 0, st>>>(scal, part, row.grid, nloads, 1);
+    FH_CK(cudaGetLastError());
+    VecArgs<T> v;
+    std::memset(&v, 0, sizeof(v));
+    v.b.len = vlen;
+    v.b.nloads = nloads;
+    for (int l = 0; l < nloads; ++l) {
+      v.x[l] = x[l];
+      v.r[l] = r[l];
+      v.p[l] = p[l];
+      v.ap[l] = ap[l];
+      v.rs[l] = rs[l];
+      v.atps[l] = atps[l];
+    }
+    v.scal = scal;
+    v.part = part;
+    ++launches;
+    FH_CK(lt.bicg_update(vec, v, st));
+    ++launches;
+    k_scal_beta<<<1, kRedThreads, 0, st>>>(scal, part, vec.grid, nloads, 1);
+    return cudaGetLastError();
+  }
+  // fixed point: e <- rhs - B e
+  RowArgs<T> f = a, i = a;
+  for (int l = 0; l < nloads; ++l) {
+    f.in[l] = x[l];
+    i.in[l] = x[l];
+    i.out[l] = x[l];
+    i.rhs[l] = rhs_active_ ? rhs[l] : nullptr;
+  }
+  FH_CK(passes(kProApply, kEpiFixed, f, i, scal));
+  ++launches;
+  k_scal_fixed<<<1, kRedThreads, 0, st>>>(scal, part, row.grid, nloads);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Pipeline<T>::enqueue_chunk(int method, int K) {
+  const int key = (method * 2 + (rhs_active_ ? 1 : 0)) * 4096 + K;
+  auto it = graphs.find(key);
+  if (it == graphs.end()) {
+    cudaGraph_t graph;
+    const long long before = launches;
+    FH_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < K && e == cudaSuccess; ++k) e = enqueue_iter(method);
+    cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+    graph_kernels[key] = launches - before;
+    launches = before;
+    if (e != cudaSuccess) return e;
+    if (e2 != cudaSuccess) return e2;
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    FH_CK(e);
+    it = graphs.emplace(key, exec).first;
+  }
+  launches += graph_kernels[key];
+  return cudaGraphLaunch(it->second, st);
+}
+
+template <typename T>
+int Pipeline<T>::norm2(T* const* v, double* out, std::string& err) {
+  const Mat3 I = {{1, 0, 0, 0, 1, 0, 0, 0, 1}};
+  for (int l = 0; l < nloads; ++l) { ++launches; FH_CKS(lt.matnorm2(vec, v[l], g.nodes, I, part + (long long)l * vec.grid, st)); }
+  ++launches;
+  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, vec.grid, nloads, d_red);
+  FH_CKS(cudaGetLastError());
+  FH_CKS(cudaMemcpyAsync(h_red, d_red, nloads * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FH_CKS(cudaStreamSynchronize(st));
+  for (int l = 0; l < nloads; ++l) out[l] = h_red[l];
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::matnorm2(const T* e, const double* Mx, double* out, std::string& err) {
+  Mat3 m;
+  for (int i = 0; i < 9; ++i) m.v[i] = Mx[i];
+  ++launches;
+  FH_CKS(lt.matnorm2(vec, e, g.nodes, m, part, st));
+  ++launches;
+  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, vec.grid, 1, d_red);
+  FH_CKS(cudaGetLastError());
+  FH_CKS(cudaMemcpyAsync(h_red, d_red, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FH_CKS(cudaStreamSynchronize(st));
+  *out = h_red[0];
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::residual(const T* const* xin, T* const* rout, bool rhs_field,
+                          const double (*E)[kMaxD], double* out, std::string& err) {
+  for (int l = 0; l < nloads; ++l) {
+    Scal& s = h_scal[kMaxLoads + l];
+    std::memset(&s, 0, sizeof(Scal));
+    s.done = kRunning;
+    s.b2 = 1.0;
+    for (int c = 0; c < kMaxD; ++c) s.E[c] = c < g.d ? E[l][c] : 0.0;
+  }
+  FH_CKS(cudaMemcpyAsync(scal_aux, h_scal + kMaxLoads, nloads * sizeof(Scal), cudaMemcpyHostToDevice, st));
+  RowArgs<T> a = row_args();
+  a.scal = scal_aux;
+  for (int l = 0; l < nloads; ++l) {
+    a.in[l] = xin[l];
+    a.out[l] = rout[l];
+    a.rhs[l] = rhs_field ? rhs[l] : nullptr;
+  }
+  FH_CKS(passes(kProApply, kEpiResid, a, a, scal_aux));
+  ++launches;
+  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, row.grid, nloads, d_red);
+  FH_CKS(cudaGetLastError());
+  FH_CKS(cudaMemcpyAsync(h_red, d_red, nloads * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FH_CKS(cudaStreamSynchronize(st));
+  for (int l = 0; l < nloads; ++l) out[l] = h_red[l];
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::current_mean(const T* e, double* col, std::string& err) {
+  ++launches;
+  FH_CKS(lt.current_sum(vec, e, phase, ltab64, g.nodes, part, st));
+  ++launches;
+  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, vec.grid, g.d, d_red);
+  FH_CKS(cudaGetLastError());
+  FH_CKS(cudaMemcpyAsync(h_red, d_red, g.d * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FH_CKS(cudaStreamSynchronize(st));
+  for (int c = 0; c < g.d; ++c) col[c] = h_red[c] / (double)g.nodes;
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::eta_e(const T* e, double* eta, std::string& err) {
+  if (nloads != 1) {
+    err = "eta_e needs a single-load pipeline";
+    return 1;
+  }
+  RowArgs<T> a = row_args();
+  a.tab = ltab;  // j = L e
+  for (int l = 0; l < kMaxLoads; ++l) a.in[l] = e;
+  FH_CKS(launch_row_fwd(kProApply, a));
+  FH_CKS(launch_green(kColEta, nullptr, part));
+  ++launches;
+  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, col0.grid, 2, d_red);
+  FH_CKS(cudaGetLastError());
+  FH_CKS(cudaMemcpyAsync(h_red, d_red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FH_CKS(cudaStreamSynchronize(st));
+  *eta = h_red[1] > 0.0 ? std::sqrt(h_red[0] / h_red[1]) : 0.0;
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int x0,
+                       const T* const* x_init, double tol, int max_iter, SolveResult* res,
+                       std::string& err) {
+  int rc;
+  if (method == kBiCG && rs[0] == nullptr) {
+    for (int l = 0; l < nloads; ++l) {
+      if ((rc = dev_alloc(allocs, &rs[l], vlen, err))) return rc;
+      if ((rc = dev_alloc(allocs, &ps[l], vlen, err))) return rc;
+      if ((rc = dev_alloc(allocs, &atps[l], vlen, err))) return rc;
+    }
+  }
+  rhs_active_ = rhs_field;
+  double b2[kMaxLoads];
+  if (rhs_field) {
+    if ((rc = norm2(rhs, b2, err))) return rc;
+  } else {
+    for (int l = 0; l < nloads; ++l) {
+      double e2 = 0.0;
+      for (int c = 0; c < g.d; ++c) e2 += E[l][c] * E[l][c];
+      b2[l] = e2 * (double)g.nodes;
+    }
+  }
+  for (int l = 0; l < nloads; ++l) {
+    Scal& s = h_scal[l];
+    std::memset(&s, 0, sizeof(Scal));
+    s.b2 = b2[l] > 0.0 ? b2[l] : 1.0;
+    s.tol2 = tol * tol;
+    s.max_iter = max_iter;
+    s.done = kRunning;
+    s.hist = hist;
+    s.hist_cap = hist_cap;
+    for (int c = 0; c < kMaxD; ++c) s.E[c] = (!rhs_field && c < g.d) ? E[l][c] : 0.0;
+  }
+  FH_CKS(cudaMemcpyAsync(scal, h_scal, nloads * sizeof(Scal), cudaMemcpyHostToDevice, st));
+  const size_t vbytes = (size_t)vlen * sizeof(T);
+  for (int l = 0; l < nloads; ++l) {
+    switch (x0) {
+      case kX0Const:
+        ++launches;
+        k_fill_const<T><<<vec.grid, vec.block, 0, st>>>(x[l], g.nodes, g.d, E[l][0], E[l][1],
+                                                        g.d > 2 ? E[l][2] : 0.0);
+        FH_CKS(cudaGetLastError());
+        break;
+      case kX0Field:
+        FH_CKS(cudaMemcpyAsync(x[l], x_init[l], vbytes, cudaMemcpyDeviceToDevice, st));
+        break;
+      case kX0Zero:
+        FH_CKS(cudaMemsetAsync(x[l], 0, vbytes, st));
+        break;
+      case kX0Keep:
+        break;
+      default:
+        FH_CKS(cudaMemcpyAsync(x[l], rhs[l], vbytes, cudaMemcpyDeviceToDevice, st));
+        break;
+    }
+  }
+  if (method != kFixed) {
+    if (x0 == kX0Zero) {
+      const Mat3 I = {{1, 0, 0, 0, 1, 0, 0, 0, 1}};
+      for (int l = 0; l < nloads; ++l) {
+        FH_CKS(cudaMemcpyAsync(r[l], rhs[l], vbytes, cudaMemcpyDeviceToDevice, st));
+        ++launches;
+        FH_CKS(lt.matnorm2(vec, r[l], g.nodes, I, part + (long long)l * vec.grid, st));
+      }
+      ++launches;
+      k_scal_start<<<1, kRedThreads, 0, st>>>(scal, part, vec.grid, nloads, method == kBiCG);
+    } else {
+      RowArgs<T> a = row_args();
+      a.scal = scal;
+      for (int l = 0; l < nloads; ++l) {
+        a.in[l] = x[l];
+        a.out[l] = r[l];
+        a.rhs[l] = rhs_field ? rhs[l] : nullptr;
+      }
+      FH_CKS(passes(kProApply, kEpiResid, a, a, scal));
+      ++launches;
+      k_scal_start<<<1, kRedThreads, 0, st>>>(scal, part, row.grid, nloads, method == kBiCG);
+    }
+    FH_CKS(cudaGetLastError());
+    for (int l = 0; l < nloads; ++l) {
+      FH_CKS(cudaMemsetAsync(p[l], 0, vbytes, st));
+      if (method == kBiCG) {
+        FH_CKS(cudaMemcpyAsync(rs[l], r[l], vbytes, cudaMemcpyDeviceToDevice, st));
+        FH_CKS(cudaMemsetAsync(ps[l], 0, vbytes, st));
+      }
+    }
+  }
+  const int K = chunk_size(method);
+  long long guard = 0;
+  const long long guard_max = (long long)max_iter / K + 4;
+  while (true) {
+    FH_CKS(enqueue_chunk(method, K));
+    FH_CKS(cudaMemcpyAsync(h_scal, scal, nloads * sizeof(Scal), cudaMemcpyDeviceToHost, st));
+    FH_CKS(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int l = 0; l < nloads; ++l) all = all && h_scal[l].done != kRunning;
+    if (all) break;
+    if (++guard > guard_max) {
+      err = "iteration guard exceeded without a device status";
+      return 8;  // FH_ERR_TIMEOUT
+    }
+  }
+  for (int l = 0; l < nloads; ++l) {
+    res[l].status = h_scal[l].done;
+    res[l].iters = h_scal[l].iter;
+    res[l].rel = h_scal[l].rel;
+    res[l].alpha = h_scal[l].alpha;
+  }
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::profile(int what, int reps, double* ms, std::string& err) {
+  if (x[0] == nullptr) {
+    err = "profiling needs a context with Krylov buffers";
+    return 1;
+  }
+  for (int l = 0; l < nloads; ++l) {
+    Scal& s = h_scal[l];
+    std::memset(&s, 0, sizeof(Scal));
+    s.done = kRunning;
+    s.alpha = 1e-3;
+    s.beta = 0.5;
+    s.b2 = 1.0;
+    s.max_iter = 1 << 30;
+  }
+  FH_CKS(cudaMemcpyAsync(scal, h_scal, nloads * sizeof(Scal), cudaMemcpyHostToDevice, st));
+  const size_t vbytes = (size_t)vlen * sizeof(T);
+  for (int l = 0; l < nloads; ++l) {
+    FH_CKS(cudaMemsetAsync(x[l], 0, vbytes, st));
+    FH_CKS(cudaMemsetAsync(r[l], 0, vbytes, st));
+    FH_CKS(cudaMemsetAsync(p[l], 0, vbytes, st));
+    FH_CKS(cudaMemsetAsync(ap[l], 0, vbytes, st));
+  }
+  RowArgs<T> a = row_args();
+  a.scal = scal;
+  RowArgs<T> f = a, i = a, app = a;
+  for (int l = 0; l < nloads; ++l) {
+    f.in[l] = r[l];
+    f.out[l] = p[l];
+    i.in[l] = p[l];
+    i.out[l] = ap[l];
+    app.in[l] = x[l];
+    app.out[l] = ap[l];
+  }
+  app.scal = nullptr;
+  VecArgs<T> v;
+  std::memset(&v, 0, sizeof(v));
+  v.b.len = vlen;
+  v.b.nloads = nloads;
+  for (int l = 0; l < nloads; ++l) {
+    v.x[l] = x[l];
+    v.r[l] = r[l];
+    v.p[l] = p[l];
+    v.ap[l] = ap[l];
+  }
+  v.scal = scal;
+  v.part = part;
+  auto one = [&]() -> cudaError_t {
+    switch (what) {
+      case 0: return launch_row_fwd(kProDir, f);
+      case 1: return launch_green(kColGreen, scal, nullptr);
+      case 2: return launch_row_inv(kEpiDir, i);
+      case 3: ++launches; return lt.cg_update(vec, v, st);
+      case 5: return passes(kProApply, kEpiApply, app, app, nullptr);
+      default: return cudaErrorInvalidValue;
+    }
+  };
+  for (int w = 0; w < 3; ++w) FH_CKS(one());
+  cudaEvent_t e0, e1;
+  FH_CKS(cudaEventCreate(&e0));
+  FH_CKS(cudaEventCreate(&e1));
+  FH_CKS(cudaEventRecord(e0, st));
+  for (int k = 0; k < reps; ++k) FH_CKS(one());
+  FH_CKS(cudaEventRecord(e1, st));
+  FH_CKS(cudaEventSynchronize(e1));
+  float t = 0.f;
+  FH_CKS(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = (double)t / reps;
+  return 0;
+}
+
+}  // namespace fh

@@ -1,0 +1,267 @@
+"""ctypes binding of libfh.so (C ABI in include/fh.h).
+
+Argument marshalling only: every step of the operator and the solvers runs in
+the CUDA library.  PyTorch provides device memory and the CUDA stream.  If the
+library is missing the import of a Solver fails loudly; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libfh.so")
+
+FH_OK = 0
+STATUS = {
+    0: "FH_OK", 1: "FH_ERR_ARG", 2: "FH_ERR_EVEN_N", 3: "FH_ERR_NOT_SPD", 4: "FH_ERR_OOM",
+    5: "FH_ERR_CUDA", 6: "FH_ERR_NOT_CONVERGED", 7: "FH_ERR_BREAKDOWN", 8: "FH_ERR_TIMEOUT",
+    9: "FH_ERR_UNSUPPORTED",
+}
+METHODS = {"cg": 0, "bicg": 1, "fixed_point": 2, "ffth": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_refined": 2}
+DT_FP64, DT_FP32 = 0, 1
+
+# Names declared in include/fh.h (checked by the ABI test).
+EXPORTS = (
+    "fh_create", "fh_set_phase", "fh_apply", "fh_solve", "fh_solve_all", "fh_effective_column",
+    "fh_eta_e", "fh_profile", "fh_destroy", "fh_status_string", "fh_last_error", "fh_version",
+)
+
+
+class FhInfo(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("outer_iters", ctypes.c_int),
+        ("matvecs", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("rel_res_true", ctypes.c_double),
+        ("rel_res", ctypes.c_double),
+        ("eta_r", ctypes.c_double),
+        ("eta_e", ctypes.c_double),
+        ("history", ctypes.POINTER(ctypes.c_double)),
+        ("history_cap", ctypes.c_int),
+        ("history_len", ctypes.c_int),
+        ("launches", ctypes.c_longlong),
+    ]
+
+
+class FhError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfh.so and declare the prototypes.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(
+            f"{path} not found: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    pI = ctypes.POINTER(ctypes.c_int)
+    pD = ctypes.POINTER(ctypes.c_double)
+    lib.fh_create.argtypes = [ctypes.POINTER(P), I, pI, pD, P, I, I, pD, pD, I, P]
+    lib.fh_create.restype = I
+    lib.fh_set_phase.argtypes = [P, P, I]
+    lib.fh_set_phase.restype = I
+    lib.fh_apply.argtypes = [P, P, P, I, I]
+    lib.fh_apply.restype = I
+    lib.fh_solve.argtypes = [P, pD, D, I, I, P, P, pD, ctypes.POINTER(FhInfo)]
+    lib.fh_solve.restype = I
+    lib.fh_solve_all.argtypes = [P, D, I, I, pD, ctypes.POINTER(FhInfo)]
+    lib.fh_solve_all.restype = I
+    lib.fh_effective_column.argtypes = [P, P, pD]
+    lib.fh_effective_column.restype = I
+    lib.fh_eta_e.argtypes = [P, P, pD]
+    lib.fh_eta_e.restype = I
+    lib.fh_profile.argtypes = [P, I, I, I, pD]
+    lib.fh_profile.restype = I
+    lib.fh_destroy.argtypes = [P]
+    lib.fh_destroy.restype = V
+    lib.fh_status_string.argtypes = [I]
+    lib.fh_status_string.restype = ctypes.c_char_p
+    lib.fh_last_error.argtypes = [P]
+    lib.fh_last_error.restype = ctypes.c_char_p
+    lib.fh_version.argtypes = []
+    lib.fh_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _dptr(a) -> ctypes.c_double:
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _info_dict(info: FhInfo, hist: Optional[np.ndarray]) -> dict:
+    out = {
+        "status": STATUS.get(info.status, info.status),
+        "iters": info.iters,
+        "outer_iters": info.outer_iters,
+        "matvecs": info.matvecs,
+        "rel_res_true": info.rel_res_true,
+        "rel_res": info.rel_res,
+        "eta_r": info.eta_r,
+        "eta_e": info.eta_e,
+        "launches": info.launches,
+    }
+    if hist is not None:
+        out["history"] = hist[: info.history_len].copy()
+    return out
+
+
+class Solver:
+    """One microstructure on one grid (fh_create ... fh_destroy).
+
+    phase      uint8 image of shape N (numpy on the host, or a CUDA torch tensor)
+    L          per-phase tensors, shape (nphase, d, d), float64
+    L0         reference conductivity (d, d) or None for Eq. (opt_ref)
+    Y          cell half sizes (d,) or None
+    precision  "fp64", "fp32" or "fp32_refined"
+    """
+
+    def __init__(self, phase, L, L0=None, Y=None, precision: str = "fp64", stream=None):
+        import torch
+
+        self._torch = torch
+        self.lib = load_library()
+        if torch.is_tensor(phase):
+            on_dev = phase.is_cuda
+            N = tuple(phase.shape)
+            ph_ptr = phase.data_ptr()
+            self._phase_ref = phase
+        else:
+            ph = np.ascontiguousarray(phase, dtype=np.uint8)
+            on_dev = False
+            N = ph.shape
+            ph_ptr = ph.ctypes.data
+            self._phase_ref = ph
+        self.N = tuple(int(n) for n in N)
+        self.d = len(self.N)
+        Lh = np.ascontiguousarray(L, dtype=np.float64)
+        self.nphase = Lh.shape[0]
+        L0h = None if L0 is None else np.ascontiguousarray(L0, dtype=np.float64)
+        Yh = None if Y is None else np.ascontiguousarray(Y, dtype=np.float64)
+        Nh = (ctypes.c_int * self.d)(*self.N)
+        self.precision = precision
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        ctx = ctypes.c_void_p()
+        rc = self.lib.fh_create(ctypes.byref(ctx), self.d, Nh,
+                                None if Yh is None else _dptr(Yh),
+                                ctypes.c_void_p(ph_ptr), int(on_dev), self.nphase, _dptr(Lh),
+                                None if L0h is None else _dptr(L0h), PRECISIONS[precision],
+                                ctypes.c_void_p(stream.cuda_stream))
+        if rc != FH_OK:
+            raise FhError(rc, "fh_create failed")
+        self.ctx = ctx
+
+    # -- lifecycle --------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.fh_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc: int, what: str):
+        if rc != FH_OK:
+            raise FhError(rc, f"{what}: {self.lib.fh_last_error(self.ctx).decode()}")
+
+    # -- calls ------------------------------------------------------------
+    def set_phase(self, phase):
+        torch = self._torch
+        if torch.is_tensor(phase):
+            rc = self.lib.fh_set_phase(self.ctx, ctypes.c_void_p(phase.data_ptr()), int(phase.is_cuda))
+        else:
+            ph = np.ascontiguousarray(phase, dtype=np.uint8)
+            rc = self.lib.fh_set_phase(self.ctx, ctypes.c_void_p(ph.ctypes.data), 0)
+        self._check(rc, "fh_set_phase")
+
+    def apply(self, e, out=None, transpose: bool = False):
+        """(I + B) e or (I + B^T) e for a CUDA tensor e of shape (d, *N)."""
+        torch = self._torch
+        assert e.is_cuda and e.is_contiguous() and tuple(e.shape) == (self.d,) + self.N
+        dt = DT_FP64 if e.dtype == torch.float64 else DT_FP32
+        if out is None:
+            out = torch.empty_like(e)
+        rc = self.lib.fh_apply(self.ctx, ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                               int(transpose), dt)
+        self._check(rc, "fh_apply")
+        return out
+
+    def solve(self, E: Sequence[float], tol: float = 1e-8, method: str = "cg", max_iter: int = 10000,
+              e_init=None, out=None, history: int = 0, want_field: bool = True, check: bool = False):
+        """Solve for the load E.  Returns (field or None, L_eff column, info dict)."""
+        torch = self._torch
+        Eh = np.ascontiguousarray(E, dtype=np.float64)
+        if want_field and out is None:
+            out = torch.empty((self.d,) + self.N, dtype=torch.float64, device=self.dev)
+        col = np.zeros(self.d)
+        info = FhInfo()
+        hist = None
+        if history > 0:
+            hist = np.zeros(history)
+            info.history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            info.history_cap = history
+        rc = self.lib.fh_solve(self.ctx, _dptr(Eh), float(tol), METHODS[method], int(max_iter),
+                               None if e_init is None else ctypes.c_void_p(e_init.data_ptr()),
+                               None if out is None else ctypes.c_void_p(out.data_ptr()),
+                               _dptr(col), ctypes.byref(info))
+        if check:
+            self._check(rc, "fh_solve")
+        elif rc not in (FH_OK, 6, 7):
+            self._check(rc, "fh_solve")
+        return out, col, _info_dict(info, hist)
+
+    def solve_all(self, tol: float = 1e-8, method: str = "cg", max_iter: int = 10000):
+        Leff = np.zeros((self.d, self.d))
+        infos = (FhInfo * self.d)()
+        rc = self.lib.fh_solve_all(self.ctx, float(tol), METHODS[method], int(max_iter), _dptr(Leff), infos)
+        if rc not in (FH_OK, 6, 7):
+            self._check(rc, "fh_solve_all")
+        return Leff, [_info_dict(infos[i], None) for i in range(self.d)]
+
+    def profile(self, what: int, reps: int = 20, dtype: str = "fp32") -> float:
+        """Average ms per launch of one piece of the CG iteration (fh_profile)."""
+        v = np.zeros(1)
+        self._check(self.lib.fh_profile(self.ctx, DT_FP64 if dtype == "fp64" else DT_FP32, int(what),
+                                        int(reps), _dptr(v)), "fh_profile")
+        return float(v[0])
+
+    def effective_column(self, e) -> np.ndarray:
+        col = np.zeros(self.d)
+        self._check(self.lib.fh_effective_column(self.ctx, ctypes.c_void_p(e.data_ptr()), _dptr(col)),
+                    "fh_effective_column")
+        return col
+
+    def eta_e(self, e) -> float:
+        v = np.zeros(1)
+        self._check(self.lib.fh_eta_e(self.ctx, ctypes.c_void_p(e.data_ptr()), _dptr(v)), "fh_eta_e")
+        return float(v[0])
+
+
+def version() -> str:
+    return load_library().fh_version().decode()

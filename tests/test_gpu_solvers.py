@@ -1,0 +1,221 @@
+"""Parity of fh_solve (CUDA) with the oracle's solvers.
+
+Bars (spec accuracy targets): float64 path <= 1e-10 relative error of the
+field and of L_eff against the oracle's tight solution; float32 + float64
+refinement <= 1e-6.  Comparisons are made at tolerances where the iteration
+error is below those bars (the field error is at most kappa times the
+relative residual, kappa <= contrast).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_1122_gb300 import microstructure as micro
+
+from gpu_util import cuda_or_skip
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _c1():
+    phase = micro.centred_disk(81, 0.3)
+    L = micro.isotropic_table([1.0, 10.0], 2)
+    return phase, L, oracle.reference_medium(L)
+
+
+def test_c1_fp64_cg_matches_oracle_iterates():
+    """C1: 81^2 centred disk, vf 0.3, L = 1 / 10, L0 = 5.5 I, E = (1, 0), FP64 CG to 1e-8.
+    Same algorithm, same start: the iteration counts agree and the residual
+    histories agree to round-off."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase, L, L0 = _c1()
+    xo, io = oracle.cg(phase, L, L0, [1.0, 0.0], tol=1e-8)
+    with fh.Solver(phase, L, precision="fp64") as s:
+        x, col, info = s.solve([1.0, 0.0], tol=1e-8, method="cg", history=512)
+    assert info["status"] == "FH_OK"
+    assert info["iters"] == io["iters"]
+    h = info["history"]
+    assert np.allclose(h, io["history"][: len(h)], rtol=1e-9, atol=1e-15)
+    assert _rel_l2(x.cpu().numpy(), xo) < 1e-10
+    assert info["rel_res_true"] <= 1e-8
+
+
+@pytest.mark.parametrize("method", ["cg", "bicg", "fixed_point"])
+def test_fp64_methods_reach_oracle_solution(method):
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = micro.rsa_disks(135, 0.35, 6, 14, seed=micro.config_seed(2, 7))
+    L = micro.isotropic_table([1.0, 20.0], 2)
+    L0 = oracle.reference_medium(L)
+    xo, io = oracle.cg(phase, L, L0, [0.0, 1.0], tol=1e-13)
+    with fh.Solver(phase, L, precision="fp64") as s:
+        x, col, info = s.solve([0.0, 1.0], tol=1e-12, method=method, max_iter=20000)
+    assert info["status"] == "FH_OK", info
+    assert _rel_l2(x.cpu().numpy(), xo) < 1e-10
+    Lo = oracle.effective_tensor([xo], phase, L)[:, 0]
+    assert np.max(np.abs(col - Lo)) / np.max(np.abs(Lo)) < 1e-10
+
+
+@pytest.mark.parametrize("method", ["cg", "bicg", "fixed_point"])
+def test_fp32_refined_meets_1e6(method):
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = micro.rsa_disks(243, 0.4, 8, 20, seed=micro.config_seed(2, 3))
+    rho = 100.0
+    L = micro.isotropic_table([1.0, rho], 2)
+    L0 = oracle.reference_medium(L)
+    xo, _ = oracle.cg(phase, L, L0, [1.0, 0.0], tol=1e-13)
+    with fh.Solver(phase, L, precision="fp32_refined") as s:
+        x, col, info = s.solve([1.0, 0.0], tol=1e-10, method=method, max_iter=50000)
+    assert info["status"] == "FH_OK", info
+    assert info["outer_iters"] >= 1
+    assert _rel_l2(x.cpu().numpy(), xo) < 1e-6
+    Lo = oracle.effective_tensor([xo], phase, L)[:, 0]
+    assert np.max(np.abs(col - Lo)) / np.max(np.abs(Lo)) < 1e-6
+
+
+def test_fp32_plain_converges():
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase, L, L0 = _c1()
+    xo, _ = oracle.cg(phase, L, L0, [1.0, 0.0], tol=1e-13)
+    with fh.Solver(phase, L, precision="fp32") as s:
+        x, col, info = s.solve([1.0, 0.0], tol=1e-5, method="cg")
+    assert info["status"] == "FH_OK", info
+    assert _rel_l2(x.cpu().numpy(), xo) < 1e-4
+
+
+def test_3d_spheres_fp64_and_refined():
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = micro.boolean_spheres(27, 4.0, 0.25, seed=micro.config_seed(3, 1))
+    L = micro.isotropic_table([1.0, 50.0], 3)
+    L0 = oracle.reference_medium(L)
+    xo, _ = oracle.cg(phase, L, L0, [0.0, 0.0, 1.0], tol=1e-13)
+    for prec, tol, bar in (("fp64", 1e-12, 1e-10), ("fp32_refined", 1e-10, 1e-6)):
+        with fh.Solver(phase, L, precision=prec) as s:
+            x, col, info = s.solve([0.0, 0.0, 1.0], tol=tol, method="cg")
+        assert info["status"] == "FH_OK", (prec, info)
+        assert _rel_l2(x.cpu().numpy(), xo) < bar, prec
+
+
+def test_effective_tensor_solve_all_symmetric_bounds():
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = micro.centred_disk(81, 0.45)
+    f2 = micro.digital_fraction(phase)
+    rho = 30.0
+    L = micro.isotropic_table([1.0, rho], 2)
+    L0 = oracle.reference_medium(L)
+    with fh.Solver(phase, L, precision="fp64") as s:
+        Le, infos = s.solve_all(tol=1e-12)
+    xs = [oracle.cg(phase, L, L0, np.eye(2)[b], tol=1e-13)[0] for b in range(2)]
+    Lo = oracle.effective_tensor(xs, phase, L)
+    assert np.max(np.abs(Le - Lo)) / np.max(np.abs(Lo)) < 1e-10
+    assert abs(Le[0, 1] - Le[1, 0]) < 1e-9 * Le[0, 0]
+    voigt = (1 - f2) + f2 * rho
+    reuss = 1.0 / ((1 - f2) + f2 / rho)
+    assert reuss < Le[0, 0] < voigt
+
+
+def test_homogeneous_zero_iterations_exact():
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    N = (45, 45)
+    phase = np.zeros(N, dtype=np.uint8)
+    L = np.array([[[4.0, 1.0], [1.0, 3.0]]])
+    with fh.Solver(phase, L, precision="fp64") as s:
+        x, col, info = s.solve([0.3, -0.7], tol=1e-12)
+    assert info["status"] == "FH_OK" and info["iters"] == 0
+    xe = x.cpu().numpy()
+    assert np.all(xe[0] == 0.3) and np.all(xe[1] == -0.7)
+    assert np.allclose(col, L[0] @ np.array([0.3, -0.7]), rtol=1e-14)
+
+
+def test_laminate_closed_form_gpu():
+    """Layers normal to axis 0: harmonic mean across, arithmetic along (exact)."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    N = (81, 45)
+    phase = micro.laminate(N, [1 / 3, 2 / 3], axis=0, seed=4)
+    c = np.array([1.0, 10.0])
+    L = micro.isotropic_table(c, 2)
+    frac = np.bincount(phase[:, 0], minlength=2) / 81
+    harm, arith = 1.0 / np.sum(frac / c), np.sum(frac * c)
+    for prec in ("fp64", "fp32_refined"):
+        with fh.Solver(phase, L, precision=prec) as s:
+            Le, _ = s.solve_all(tol=1e-11)
+        bar = 1e-10 if prec == "fp64" else 1e-6
+        assert np.max(np.abs(Le - np.diag([harm, arith]))) / arith < bar, (prec, Le)
+
+
+def test_reference_medium_independence_gpu():
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = micro.centred_disk(81, 0.4)
+    rho = 50.0
+    L = micro.isotropic_table([1.0, rho], 2)
+    cols = []
+    for omega in (0.25, 0.5, 0.75):
+        L0 = (1 - omega + rho * omega) * np.eye(2)
+        with fh.Solver(phase, L, L0=L0, precision="fp64") as s:
+            _, col, info = s.solve([1.0, 0.0], tol=1e-12)
+        assert info["status"] == "FH_OK"
+        cols.append(col)
+    assert np.max(np.abs(np.array(cols) - cols[1])) < 1e-10 * abs(cols[1][0])
+
+
+def test_not_converged_and_infinite_contrast_status():
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase, L, L0 = _c1()
+    with fh.Solver(phase, L, precision="fp64") as s:
+        _, _, info = s.solve([1.0, 0.0], tol=1e-12, max_iter=3)
+    assert info["status"] == "FH_ERR_NOT_CONVERGED" and info["iters"] == 3
+    Lr = micro.isotropic_table([1.0, 1e12], 2)
+    with fh.Solver(phase, Lr, precision="fp64") as s:
+        _, _, info = s.solve([1.0, 0.0], tol=1e-8, max_iter=200)
+    assert info["status"] in ("FH_ERR_NOT_CONVERGED", "FH_ERR_BREAKDOWN")
+
+
+def test_eta_e_matches_oracle():
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = micro.centred_disk(45, 0.3)
+    L = micro.isotropic_table([1.0, 10.0], 2)
+    L0 = oracle.reference_medium(L)
+    rng = np.random.default_rng(3)
+    e = rng.normal(size=(2, 45, 45))
+    with fh.Solver(phase, L, precision="fp64") as s:
+        got = s.eta_e(torch.from_numpy(e).cuda())
+        x, _, info = s.solve([1.0, 0.0], tol=1e-12)
+    assert abs(got - oracle.eta_e(e, phase, L)) < 1e-12 * oracle.eta_e(e, phase, L)
+    assert info["eta_e"] < 1e-9
+
+
+def test_invalid_inputs_rejected():
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    with pytest.raises(fh.FhError):
+        fh.Solver(np.zeros((8, 9), np.uint8), micro.isotropic_table([1.0], 2))
+    with pytest.raises(fh.FhError):
+        fh.Solver(np.zeros((9, 9), np.uint8), np.array([[[1.0, 2.0], [2.0, 1.0]]]))
+    with pytest.raises(fh.FhError):
+        fh.Solver(np.full((9, 9), 3, np.uint8), micro.isotropic_table([1.0, 2.0], 2))
