@@ -175,6 +175,46 @@ fh_status fh_eta_e(fh_ctx* ctx, const double* e, double* eta);
  * Synchronises.  Errors: FH_ERR_ARG, FH_ERR_CUDA. */
 fh_status fh_profile(fh_ctx* ctx, int dtype, int what, int reps, double* ms);
 
+/* fh_apply_noalloc -- fh_apply for callers that cannot allocate device memory
+ * (the paper has no counterpart; this is a deployment convenience).
+ *
+ * Some callers cannot call cudaMalloc: a host framework that owns all device
+ * memory through its own pool and forbids outside allocations, a latency-
+ * critical loop where cudaMalloc's implicit device synchronisation is not
+ * acceptable, or an embedded user with a device-memory budget fixed at load
+ * time.  This call computes the same float64 product as fh_apply,
+ *   transpose == 0:  e_out = e_in + F^-1 Gamma0 F (dL e_in)
+ *   transpose != 0:  e_out = e_in + dL F^-1 Gamma0 F e_in
+ * without a context and without allocating: its spectrum scratch and its
+ * twiddle and dL tables live in fixed arrays inside the library, about
+ * 16.1 MiB that every GPU loading the library keeps until the process exits.
+ *
+ *  d, N, Y     as fh_create (d = 2 or 3, odd N, each axis <= 2187 and built
+ *              from 3, 5 and 7; Y may be NULL).  Grids whose float64 half
+ *              spectrum exceeds 16 MiB (for example 2-D above ~1000^2, 3-D
+ *              above ~85^3) are rejected with FH_ERR_UNSUPPORTED.
+ *  phase       device, |N| bytes; ids >= nphase act as L = L0 (dL = 0).
+ *  nphase, L   host, as fh_create.
+ *  L0          host, d*d, required here (no default).
+ *  e_in,e_out  device float64 [d][N...]; e_in == e_out is allowed.
+ *  stream      cudaStream_t as void*, or NULL for the legacy default stream.
+ *  errbuf      optional host buffer for a message (errlen bytes), may be NULL.
+ *
+ * All calls on one device share the fixed arrays and leave their contents
+ * behind; every element is written before it is read within a call, so no
+ * clearing is needed, but calls whose GPU work overlaps (different streams or
+ * host threads) race and give wrong results: order them.  The first call on
+ * each device (with that device current) performs a one-time set-up -- it
+ * looks up the arrays' device addresses and raises the kernels' shared-memory
+ * limit -- and should come before any stream capture on that device.  The
+ * call is asynchronous on `stream` apart from small table uploads from host
+ * memory.  Errors: FH_ERR_ARG, FH_ERR_EVEN_N, FH_ERR_NOT_SPD,
+ * FH_ERR_UNSUPPORTED, FH_ERR_CUDA. */
+fh_status fh_apply_noalloc(int d, const int* N, const double* Y, const uint8_t* phase,
+                           int nphase, const double* L, const double* L0, const double* e_in,
+                           double* e_out, int transpose, void* stream, char* errbuf,
+                           size_t errlen);
+
 /* fh_destroy -- free the context and every buffer it owns.  NULL is a no-op. */
 void fh_destroy(fh_ctx* ctx);
 

@@ -29,7 +29,8 @@ DT_FP64, DT_FP32 = 0, 1
 # Names declared in include/fh.h (checked by the ABI test).
 EXPORTS = (
     "fh_create", "fh_set_phase", "fh_apply", "fh_solve", "fh_solve_all", "fh_effective_column",
-    "fh_eta_e", "fh_profile", "fh_destroy", "fh_status_string", "fh_last_error", "fh_version",
+    "fh_eta_e", "fh_profile", "fh_apply_noalloc", "fh_destroy", "fh_status_string", "fh_last_error",
+    "fh_version",
 )
 
 
@@ -87,6 +88,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fh_eta_e.restype = I
     lib.fh_profile.argtypes = [P, I, I, I, pD]
     lib.fh_profile.restype = I
+    lib.fh_apply_noalloc.argtypes = [I, pI, pD, P, I, pD, pD, P, P, I, P, ctypes.c_char_p, ctypes.c_size_t]
+    lib.fh_apply_noalloc.restype = I
     lib.fh_destroy.argtypes = [P]
     lib.fh_destroy.restype = V
     lib.fh_status_string.argtypes = [I]
