@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT float64 CG baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-iters", type=int, default=6)
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--probe", action="store_true",
                     help="only time each pass kernel a few times (small command for ncu captures)")
     return ap.parse_args()
@@ -293,7 +294,13 @@ def run_fh(args):
 
     phase, tables = make_inputs()
     stream = torch.cuda.Stream()
-    solvers = [fh.Solver(phase, L, precision="fp32_refined", stream=stream) for L in tables]
+    first = fh.Solver(phase, tables[0], precision="fp32_refined", stream=stream)
+    tune = None
+    if not args.no_tune:
+        before, after = first.autotune("fp32")
+        tune = {"ms_per_iter_before": before, "ms_per_iter_after": after,
+                "cache": os.environ.get("FH_TUNE_CACHE")}
+    solvers = [first] + [fh.Solver(phase, L, precision="fp32_refined", stream=stream) for L in tables[1:]]
     nsolve = len(solvers) * len(LOADS)
 
     def step(collect=None):
@@ -448,6 +455,7 @@ def run_fh(args):
                          "algorithmic_bytes_per_launch": kern[dom][1],
                          "ms_per_launch": times[dom]},
             "kernels_ms": times,
+            "autotune": tune,
             "matvec": {"ms": t_apply, "matvecs_per_s": 1e3 / t_apply,
                        "dof_per_s": d * nodes * 1e3 / t_apply,
                        "alg_gbs_B_min": b_min / (t_apply * 1e-3) / 1e9,

@@ -175,6 +175,21 @@ fh_status fh_eta_e(fh_ctx* ctx, const double* e, double* eta);
  * Synchronises.  Errors: FH_ERR_ARG, FH_ERR_CUDA. */
 fh_status fh_profile(fh_ctx* ctx, int dtype, int what, int reps, double* ms);
 
+/* fh_autotune -- choose the launch shapes of the context's pipeline of the
+ * given precision (FH_FP32 or FH_FP64) by timing candidates: half-spectrum
+ * tile width, lines per CTA of the row passes, and the radix plan (threads per
+ * line / column FFT).  Each candidate is a temporary set of buffers of the
+ * same size as the context's; its four CG-iteration pass kernels are timed
+ * with CUDA events (10 launches each).  If a faster shape is found the
+ * pipeline is rebuilt with it (its Krylov vectors are reallocated, so any
+ * solve state is lost).  When the environment variable FH_TUNE_CACHE names a
+ * file, the result is appended to it, and fh_create reads that file to start
+ * every later context of the same shape with the tuned launch shapes.
+ *  ms_before / ms_after  host, may be NULL: summed pass time per CG iteration
+ *                        before and after.
+ * Synchronises.  Errors: FH_ERR_ARG, FH_ERR_OOM, FH_ERR_CUDA, FH_ERR_UNSUPPORTED. */
+fh_status fh_autotune(fh_ctx* ctx, int dtype, double* ms_before, double* ms_after);
+
 /* fh_apply_noalloc -- fh_apply for callers that cannot allocate device memory
  * (the paper has no counterpart; this is a deployment convenience).
  *

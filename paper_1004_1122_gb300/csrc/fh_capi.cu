@@ -3,8 +3,12 @@
 // float32 inner solves with float64 refinement).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <mutex>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -14,6 +18,7 @@
 using fh::Pipeline;
 using fh::Problem;
 using fh::SolveResult;
+using fh::Tuning;
 
 struct fh_ctx {
   Problem pb;
@@ -156,6 +161,58 @@ int to_status(int done) {
   }
 }
 
+// ---- autotuning cache ---------------------------------------------------
+// A plain text file named by the environment variable FH_TUNE_CACHE, one line
+// per problem shape:  <key> C lpc tpl tpc0 tpc1 ms_per_iteration
+std::mutex g_cache_mu;
+
+std::string tune_key(const Problem& pb, int nloads, bool f64) {
+  std::ostringstream k;
+  k << (f64 ? "f64" : "f32") << "_d" << pb.d << "_L" << nloads << "_";
+  for (int a = 0; a < pb.d; ++a) k << (a ? "x" : "") << pb.N[a];
+  return k.str();
+}
+
+bool cache_lookup(const std::string& key, Tuning& t) {
+  const char* path = std::getenv("FH_TUNE_CACHE");
+  if (!path || !*path) return false;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  std::ifstream f(path);
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream ls(line);
+    std::string k;
+    Tuning c;
+    double ms;
+    if (ls >> k >> c.C >> c.lpc >> c.tpl >> c.tpc0 >> c.tpc1 >> ms && k == key) {
+      t = c;
+      found = true;  // the last entry for a key wins
+    }
+  }
+  return found;
+}
+
+void cache_store(const std::string& key, const Tuning& t, double ms) {
+  const char* path = std::getenv("FH_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  std::ofstream f(path, std::ios::app);
+  f << key << " " << t.C << " " << t.lpc << " " << t.tpl << " " << t.tpc0 << " " << t.tpc1 << " "
+    << ms << "\n";
+}
+
+template <typename T>
+int init_tuned(Pipeline<T>* P, const Problem& pb, bool krylov, cudaStream_t st, std::string& err) {
+  Tuning t;
+  if (cache_lookup(tune_key(pb, 1, sizeof(T) == 8), t)) {
+    if (P->init(pb, 1, krylov, st, err, &t) == 0) return 0;
+    P->release();
+    *P = Pipeline<T>();
+  }
+  return P->init(pb, 1, krylov, st, err);
+}
+
 bool l0_isotropic(const Problem& pb, double& l0) {
   const int d = pb.d;
   l0 = pb.L0[0];
@@ -278,12 +335,12 @@ fh_status fh_create(fh_ctx** out, int d, const int* N, const double* Y, const ui
   if (precision == FH_FP64 || precision == FH_FP32_REFINED) {
     c->p64 = new (std::nothrow) Pipeline<double>();
     if (!c->p64) rc = FH_ERR_OOM;
-    if (!rc) rc = c->p64->init(pb, 1, precision == FH_FP64, c->st, err);
+    if (!rc) rc = init_tuned(c->p64, pb, precision == FH_FP64, c->st, err);
   }
   if (!rc && (precision == FH_FP32 || precision == FH_FP32_REFINED)) {
     c->p32 = new (std::nothrow) Pipeline<float>();
     if (!c->p32) rc = FH_ERR_OOM;
-    if (!rc) rc = c->p32->init(pb, 1, true, c->st, err);
+    if (!rc) rc = init_tuned(c->p32, pb, true, c->st, err);
   }
   const size_t vbytes = (size_t)d * pb.nodes * sizeof(double);
   if (!rc && cudaMalloc(&c->d_x64, vbytes) != cudaSuccess) rc = FH_ERR_OOM;
@@ -616,6 +673,52 @@ fh_status fh_profile(fh_ctx* c, int dtype, int what, int reps, double* ms) {
     return fail(c, FH_ERR_ARG, "no Krylov pipeline of that precision in this context");
   }
   return from_rc(c, rc, err);
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+fh_status autotune_one(fh_ctx* c, Pipeline<T>*& P, bool krylov, double* ms_before, double* ms_after) {
+  std::string err;
+  double before = 0.0, t;
+  for (int what = 0; what < 4; ++what) {
+    int rc = P->profile(what, 10, &t, err);
+    if (rc) return from_rc(c, rc, err);
+    before += t;
+  }
+  Tuning best;
+  double best_ms;
+  int rc = Pipeline<T>::autotune(c->pb, 1, c->st, best, best_ms, err);
+  if (rc) return from_rc(c, rc, err);
+  if (ms_before) *ms_before = before;
+  if (best_ms < before && !(best == P->tuning)) {
+    Pipeline<T>* Q = new (std::nothrow) Pipeline<T>();
+    if (!Q) return FH_ERR_OOM;
+    cudaStreamSynchronize(c->st);
+    P->release();
+    delete P;
+    P = Q;
+    rc = P->init(c->pb, 1, krylov, c->st, err, &best);
+    if (rc) return from_rc(c, rc, err);
+  } else {
+    best = P->tuning;
+    best_ms = before;
+  }
+  cache_store(tune_key(c->pb, 1, sizeof(T) == 8), best, best_ms);
+  if (ms_after) *ms_after = best_ms;
+  return FH_OK;
+}
+}  // namespace
+
+extern "C" {
+
+fh_status fh_autotune(fh_ctx* c, int dtype, double* ms_before, double* ms_after) {
+  if (!c) return FH_ERR_ARG;
+  if (dtype == FH_FP32 && c->p32) return autotune_one<float>(c, c->p32, true, ms_before, ms_after);
+  if (dtype == FH_FP64 && c->p64 && c->p64->x[0])
+    return autotune_one<double>(c, c->p64, true, ms_before, ms_after);
+  return fail(c, FH_ERR_ARG, "no Krylov pipeline of that precision in this context");
 }
 
 fh_status fh_effective_column(fh_ctx* c, const double* e, double* col) {

@@ -227,45 +227,59 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
   }
   __syncthreads();
 
-  // 1. gather + polarisation into the packed sequences
-  for (int idx = threadIdx.x; idx < a.lpc * n; idx += blockDim.x) {
-    const int ll = idx / n, i = idx - ll * n;
+  // 1. gather + polarisation into the packed sequences.  Loads of kUnroll
+  // elements per thread are issued before any of them is used, so each thread
+  // keeps several global loads in flight (the row pass is latency-bound
+  // otherwise).
+  constexpr int kUnroll = 8;
+  for (int ll = 0; ll < a.lpc; ++ll) {
     const int line = line0 + ll;
     const bool valid = line < g.nlines;
-    const long long off = (long long)line * n + i;
-    int ph = 0;
-    if (kUseTab && valid) ph = a.phase[off];
+    const long long lo = (long long)line * n;
+    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * blockDim.x) {
+      T v[kUnroll][NL][D];
+      T pv[kUnroll][NL][D];
+      int ph[kUnroll];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-      T v[D];
-      const bool active = valid && lact[l];
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * blockDim.x;
+        const bool ok = valid && i < n;
+        ph[u] = (kUseTab && ok) ? a.phase[lo + i] : 0;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        T x = T(0);
-        if (valid) {
-          if (kDir) {
-            const T r = pin[l][c * g.nodes + off];
-            const T p = pout[l][c * g.nodes + off];
-            x = r + lbeta[l] * p;
-            if (active) pout[l][c * g.nodes + off] = x;
-          } else {
-            x = pin[l][c * g.nodes + off];
+        for (int l = 0; l < NL; ++l)
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            v[u][l][c] = ok ? __ldg(pin[l] + c * g.nodes + lo + i) : T(0);
+            if (kDir) pv[u][l][c] = ok ? pout[l][c * g.nodes + lo + i] : T(0);
           }
-        }
-        v[c] = x;
       }
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        T t = v[c];
-        if (kUseTab) {
-          t = T(0);
-          const T* row = stab + (ph * D + c) * D;
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i >= n) continue;
+        const bool ok = valid;
 #pragma unroll
-          for (int b2 = 0; b2 < D; ++b2) t += row[b2] * v[b2];
+        for (int l = 0; l < NL; ++l) {
+          T x[D];
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            x[c] = kDir ? v[u][l][c] + lbeta[l] * pv[u][l][c] : v[u][l][c];
+            if (kDir && ok && lact[l]) pout[l][c * g.nodes + lo + i] = x[c];
+          }
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            T t = x[c];
+            if (kUseTab) {
+              t = T(0);
+              const T* row = stab + (ph[u] * D + c) * D;
+#pragma unroll
+              for (int b2 = 0; b2 < D; ++b2) t += row[b2] * x[b2];
+            }
+            const int gch = ll * M + l * D + c;
+            T* dst = reinterpret_cast<T*>(&sm[(size_t)(gch >> 1) * n + i]);
+            dst[gch & 1] = t;
+          }
         }
-        const int gch = ll * M + l * D + c;
-        T* dst = reinterpret_cast<T*>(&sm[(size_t)(gch >> 1) * n + i]);
-        dst[gch & 1] = t;
       }
     }
   }
@@ -341,13 +355,40 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
     qvalid = gv * g.C * g.M;
   }
 
-  for (int idx = threadIdx.x; idx < n * Q; idx += blockDim.x) {
-    const int i = idx / Q, q = idx - i * Q;
-    C v;
-    v.x = T(0);
-    v.y = T(0);
-    if (q < qvalid) v = a.S[base + i * b.stride_i + q];
-    sm[idx] = v;
+  // Each row i of the tile is Q contiguous complex values at base + i * stride_i.
+  // When rows are 16-byte multiples (and aligned) they move as float4 / double2
+  // words, kUnroll per thread in flight.
+  constexpr int kUnroll = 4;
+  const int wpr = (int)(Q * sizeof(C) / 16);  // 16-byte words per row
+  const bool vec = qvalid == Q && (Q * sizeof(C)) % 16 == 0 && (base * sizeof(C)) % 16 == 0 &&
+                   (b.stride_i * sizeof(C)) % 16 == 0;
+  if (vec) {
+    const int nw = n * wpr;
+    for (int w0 = threadIdx.x; w0 < nw; w0 += kUnroll * blockDim.x) {
+      float4 buf[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int w = w0 + u * blockDim.x;
+        if (w < nw) {
+          const int i = w / wpr, j = w - i * wpr;
+          buf[u] = __ldg(reinterpret_cast<const float4*>(a.S + base + i * b.stride_i) + j);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int w = w0 + u * blockDim.x;
+        if (w < nw) reinterpret_cast<float4*>(sm)[w] = buf[u];
+      }
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < n * Q; idx += blockDim.x) {
+      const int i = idx / Q, q = idx - i * Q;
+      C v;
+      v.x = T(0);
+      v.y = T(0);
+      if (q < qvalid) v = a.S[base + i * b.stride_i + q];
+      sm[idx] = v;
+    }
   }
   __syncthreads();
 
@@ -434,9 +475,17 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
     run_fft<true, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
   }
 
-  for (int idx = threadIdx.x; idx < n * Q; idx += blockDim.x) {
-    const int i = idx / Q, qq = idx - i * Q;
-    if (qq < qvalid) a.S[base + i * b.stride_i + qq] = sm[idx];
+  if (vec) {
+    const int nw = n * wpr;
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+      const int i = w / wpr, j = w - i * wpr;
+      reinterpret_cast<float4*>(a.S + base + i * b.stride_i)[j] = reinterpret_cast<const float4*>(sm)[w];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < n * Q; idx += blockDim.x) {
+      const int i = idx / Q, qq = idx - i * Q;
+      if (qq < qvalid) a.S[base + i * b.stride_i + qq] = sm[idx];
+    }
   }
 }
 
@@ -470,40 +519,58 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_inv(RowArgs<T> a) {
   }
 
   // 1. rebuild the full spectrum of each packed sequence from the half spectra
+  // (loads of kUnroll items per thread are issued before they are used)
+  constexpr int kUnroll = 8;
   const int per_t = a.nseq * g.C;
-  for (int idx = threadIdx.x; idx < g.Tt * per_t; idx += blockDim.x) {
-    const int t = idx / per_t;
-    const int rem = idx - t * per_t;
-    const int s = rem / g.C, c = rem - s * g.C;
-    const int kx = t * g.C + c;
-    if (kx >= g.H) continue;
-    C y0, y1;
-    y0.x = y0.y = y1.x = y1.y = T(0);
-    const int g0 = 2 * s, g1 = 2 * s + 1;
-    {
-      const int ll = g0 / M, m = g0 - ll * M;
-      const int line = line0 + ll;
-      if (line < g.nlines) y0 = a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m];
+  const int nitems = g.Tt * per_t;
+  for (int base = threadIdx.x; base < nitems; base += kUnroll * blockDim.x) {
+    C y0[kUnroll], y1[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int idx = base + u * blockDim.x;
+      y0[u].x = y0[u].y = y1[u].x = y1[u].y = T(0);
+      if (idx >= nitems) continue;
+      const int t = idx / per_t;
+      const int rem = idx - t * per_t;
+      const int s = rem / g.C, c = rem - s * g.C;
+      const int kx = t * g.C + c;
+      if (kx >= g.H) continue;
+      const int g0 = 2 * s, g1 = 2 * s + 1;
+      {
+        const int ll = g0 / M, m = g0 - ll * M;
+        const int line = line0 + ll;
+        if (line < g.nlines) y0[u] = a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m];
+      }
+      if (g1 < nch) {
+        const int ll = g1 / M, m = g1 - ll * M;
+        const int line = line0 + ll;
+        if (line < g.nlines) y1[u] = a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m];
+      }
     }
-    if (g1 < nch) {
-      const int ll = g1 / M, m = g1 - ll * M;
-      const int line = line0 + ll;
-      if (line < g.nlines) y1 = a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m];
-    }
-    C* seq = sm + (size_t)s * n;
-    if (kx == 0) {
-      C w;
-      w.x = y0.x;
-      w.y = y1.x;
-      seq[0] = w;
-    } else {
-      C w, wm;
-      w.x = y0.x - y1.y;
-      w.y = y0.y + y1.x;
-      wm.x = y0.x + y1.y;
-      wm.y = y1.x - y0.y;
-      seq[kx] = w;
-      seq[n - kx] = wm;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx >= nitems) continue;
+      const int t = idx / per_t;
+      const int rem = idx - t * per_t;
+      const int s = rem / g.C, c = rem - s * g.C;
+      const int kx = t * g.C + c;
+      if (kx >= g.H) continue;
+      C* seq = sm + (size_t)s * n;
+      if (kx == 0) {
+        C w;
+        w.x = y0[u].x;
+        w.y = y1[u].x;
+        seq[0] = w;
+      } else {
+        C w, wm;
+        w.x = y0[u].x - y1[u].y;
+        w.y = y0[u].y + y1[u].x;
+        wm.x = y0[u].x + y1[u].y;
+        wm.y = y1[u].x - y0[u].y;
+        seq[kx] = w;
+        seq[n - kx] = wm;
+      }
     }
   }
   __syncthreads();
@@ -535,57 +602,78 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_inv(RowArgs<T> a) {
     for (int c = 0; c < D; ++c)
       Ec[l][c] = (a.scal != nullptr && (EPI == kEpiFixed || EPI == kEpiResid)) ? T(a.scal[l].E[c]) : T(0);
   }
-  for (int idx = threadIdx.x; idx < a.lpc * n; idx += blockDim.x) {
-    const int ll = idx / n, i = idx - ll * n;
+  constexpr bool kReadIn = true;
+  constexpr bool kReadAux = (EPI == kEpiDirShadow);
+  for (int ll = 0; ll < a.lpc; ++ll) {
     const int line = line0 + ll;
-    if (line >= g.nlines) continue;
-    const long long off = (long long)line * n + i;
-    int ph = 0;
-    if (EPI == kEpiApplyT) ph = a.phase[off];
+    if (line >= g.nlines) break;
+    const long long lo = (long long)line * n;
+    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * blockDim.x) {
+      T vin[kUnroll][NL][D];
+      T vaux[kUnroll][NL][D];
+      T vrhs[kUnroll][NL][D];
+      int ph[kUnroll];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-      if (!lact[l]) continue;
-      T y[D];
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * blockDim.x;
+        const bool ok = i < n;
+        ph[u] = (EPI == kEpiApplyT && ok) ? a.phase[lo + i] : 0;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const int gch = ll * M + l * D + c;
-        const T* src = reinterpret_cast<const T*>(&sm[(size_t)(gch >> 1) * n + i]);
-        y[c] = src[gch & 1];
+        for (int l = 0; l < NL; ++l)
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const long long o = c * g.nodes + lo + i;
+            vin[u][l][c] = (kReadIn && ok && lact[l]) ? pin[l][o] : T(0);
+            vaux[u][l][c] = (kReadAux && ok && lact[l]) ? __ldg(paux[l] + o) : T(0);
+            vrhs[u][l][c] = ((EPI == kEpiFixed || EPI == kEpiResid) && ok && lact[l])
+                                ? (prhs[l] ? __ldg(prhs[l] + o) : Ec[l][c]) : T(0);
+          }
       }
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const long long o = c * g.nodes + off;
-        if (EPI == kEpiApply) {
-          pout[l][o] = pin[l][o] + y[c];
-        } else if (EPI == kEpiApplyT) {
-          const T* row = stab + (ph * D + c) * D;
-          T t = T(0);
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i >= n) continue;
 #pragma unroll
-          for (int b2 = 0; b2 < D; ++b2) t += row[b2] * y[b2];
-          pout[l][o] = pin[l][o] + t;
-        } else if (EPI == kEpiDir) {
-          const T p = pin[l][o];
-          const T ap = p + y[c];
-          pout[l][o] = ap;
-          acc[l].add(p * ap);
-        } else if (EPI == kEpiDirShadow) {
-          const T p = pin[l][o];
-          const T ap = p + y[c];
-          pout[l][o] = ap;
-          acc[l].add(ap * paux[l][o]);
-        } else if (EPI == kEpiFixed) {
-          const T e = pin[l][o];
-          const T rhs = prhs[l] ? prhs[l][o] : Ec[l][c];
-          const T en = rhs - y[c];
-          pout[l][o] = en;
-          const T df = en - e;
-          acc[l].add(df * df);
-        } else {  // kEpiResid
-          const T e = pin[l][o];
-          const T rhs = prhs[l] ? prhs[l][o] : Ec[l][c];
-          const T r = rhs - e - y[c];
-          pout[l][o] = r;
-          acc[l].add(r * r);
+        for (int l = 0; l < NL; ++l) {
+          if (!lact[l]) continue;
+          T y[D];
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const int gch = ll * M + l * D + c;
+            const T* src = reinterpret_cast<const T*>(&sm[(size_t)(gch >> 1) * n + i]);
+            y[c] = src[gch & 1];
+          }
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const long long o = c * g.nodes + lo + i;
+            const T e = vin[u][l][c];
+            if (EPI == kEpiApply) {
+              pout[l][o] = e + y[c];
+            } else if (EPI == kEpiApplyT) {
+              const T* row = stab + (ph[u] * D + c) * D;
+              T t = T(0);
+#pragma unroll
+              for (int b2 = 0; b2 < D; ++b2) t += row[b2] * y[b2];
+              pout[l][o] = e + t;
+            } else if (EPI == kEpiDir) {
+              const T ap = e + y[c];
+              pout[l][o] = ap;
+              acc[l].add(e * ap);
+            } else if (EPI == kEpiDirShadow) {
+              const T ap = e + y[c];
+              pout[l][o] = ap;
+              acc[l].add(ap * vaux[u][l][c]);
+            } else if (EPI == kEpiFixed) {
+              const T en = vrhs[u][l][c] - y[c];
+              pout[l][o] = en;
+              const T df = en - e;
+              acc[l].add(df * df);
+            } else {  // kEpiResid
+              const T r = vrhs[u][l][c] - e - y[c];
+              pout[l][o] = r;
+              acc[l].add(r * r);
+            }
+          }
         }
       }
     }
@@ -618,23 +706,70 @@ template <typename T> struct VecArgs {
   double* part;            // [2][nloads][grid]
 };
 
-// CG: x += alpha p; r -= alpha A p; partial (r, r)
+// 16-byte vector of T (4 floats or 2 doubles)
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <> struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+template <typename V, typename T>
+__device__ __forceinline__ T& vlane(V& v, int k) { return reinterpret_cast<T*>(&v)[k]; }
+
+// CG: x += alpha p; r -= alpha A p; partial (r, r).  16-byte vector accesses
+// over the aligned prefix (cudaMalloc'd vectors), a scalar tail.
 template <typename T, int NL>
 __global__ void k_cg_update(VecArgs<T> a) {
   if (all_done(a.scal, NL)) return;
+  using V = typename Vec16<T>::type;
+  constexpr int W = Vec16<T>::n;
   double acc[NL];
+  const long long nvec = a.b.len / W;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
     acc[l] = 0.0;
     if (a.scal[l].done != kRunning) continue;
     const T al = T(a.scal[l].alpha);
-    T* x = a.x[l];
-    T* r = a.r[l];
-    const T* p = a.p[l];
-    const T* ap = a.ap[l];
+    T* __restrict__ x = a.x[l];
+    T* __restrict__ r = a.r[l];
+    const T* __restrict__ p = a.p[l];
+    const T* __restrict__ ap = a.ap[l];
     DotAcc<T> dot;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.b.len;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = tid; i < nvec; i += 2 * stride) {
+      V xv[2], rv[2], pv[2], av[2];
+      const bool has2 = i + stride < nvec;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 0 || has2) {
+          const long long k = i + u * stride;
+          xv[u] = reinterpret_cast<const V*>(x)[k];
+          rv[u] = reinterpret_cast<const V*>(r)[k];
+          pv[u] = __ldg(reinterpret_cast<const V*>(p) + k);
+          av[u] = __ldg(reinterpret_cast<const V*>(ap) + k);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (u == 0 || has2) {
+          const long long k = i + u * stride;
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            vlane<V, T>(xv[u], w) += al * vlane<V, T>(pv[u], w);
+            const T rn = vlane<V, T>(rv[u], w) - al * vlane<V, T>(av[u], w);
+            vlane<V, T>(rv[u], w) = rn;
+            dot.add(rn * rn);
+          }
+          reinterpret_cast<V*>(x)[k] = xv[u];
+          reinterpret_cast<V*>(r)[k] = rv[u];
+        }
+      }
+    }
+    for (long long i = nvec * W + tid; i < a.b.len; i += stride) {
       x[i] += al * p[i];
       const T rn = r[i] - al * ap[i];
       r[i] = rn;

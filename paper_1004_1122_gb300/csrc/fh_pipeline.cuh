@@ -41,6 +41,18 @@ enum : int {
   kX0Keep = 4     // x already holds the start (restart from the current iterate)
 };
 
+// Launch-shape choices of one pipeline.  Zero means "heuristic default".
+struct Tuning {
+  int C = 0;     // half-spectrum tile width
+  int lpc = 0;   // lines per CTA in the row passes
+  int tpl = 0;   // threads per line FFT (selects the radix plan)
+  int tpc0 = 0;  // threads per column FFT along axis 0
+  int tpc1 = 0;  // threads per column FFT along axis 1 (3-D)
+  bool operator==(const Tuning& o) const {
+    return C == o.C && lpc == o.lpc && tpl == o.tpl && tpc0 == o.tpc0 && tpc1 == o.tpc1;
+  }
+};
+
 struct SolveResult {
   int status = 0;      // kConverged / kBreakdown / kCap
   int iters = 0;
@@ -94,7 +106,13 @@ struct Pipeline {
   long long launches = 0;                    // kernels enqueued (graph replays included)
   std::map<int, long long> graph_kernels;    // kernels per captured chunk
 
-  int init(const Problem& pb, int nloads_, bool krylov, cudaStream_t stream, std::string& err);
+  Tuning tuning{};   // the shape actually in use
+  int init(const Problem& pb, int nloads_, bool krylov, cudaStream_t stream, std::string& err,
+           const Tuning* want = nullptr);
+  // Time the CG-iteration pass kernels for candidate tunings (temporary
+  // pipelines) and return the fastest; `ms` receives its time per iteration.
+  static int autotune(const Problem& pb, int nloads, cudaStream_t stream, Tuning& best, double& ms,
+                      std::string& err, int max_candidates = 64);
   void release();
   void set_phase(const uint8_t* d_phase) { phase = d_phase; }
 

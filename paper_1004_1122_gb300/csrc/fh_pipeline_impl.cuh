@@ -41,7 +41,9 @@ static int dev_alloc(std::vector<void*>& allocs, T** ptr, size_t count, std::str
 
 template <typename T>
 int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t stream,
-                      std::string& err) {
+                      std::string& err, const Tuning* want) {
+  Tuning w;
+  if (want) w = *want;
   st = stream;
   nloads = nloads_;
   const bool f64 = sizeof(T) == 8;
@@ -78,8 +80,9 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
 
   // FFT plans
   int tpc0 = 0, tpc1 = 0;
-  if (!make_fft_plan(g.nlast, f64, kRowMaxThreads, prow, tpl) || !make_fft_plan(pb.N[0], f64, kColMaxThreads, pcol0, tpc0) ||
-      (d == 3 && !make_fft_plan(pb.N[1], f64, kColMaxThreads, pcol1, tpc1))) {
+  if (!make_fft_plan(g.nlast, f64, kRowMaxThreads, prow, tpl, w.tpl) ||
+      !make_fft_plan(pb.N[0], f64, kColMaxThreads, pcol0, tpc0, w.tpc0) ||
+      (d == 3 && !make_fft_plan(pb.N[1], f64, kColMaxThreads, pcol1, tpc1, w.tpc1))) {
     err = "no FFT plan for this grid (axis lengths must factor into 3, 5 and 7)";
     return 9;  // FH_ERR_UNSUPPORTED
   }
@@ -88,9 +91,10 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   // tile width C of the half spectrum
   int Cc = 0;
   for (int cand : {16, 8, 4, 2, 1}) {
+    if (w.C && cand != w.C) continue;
     const int Tt = (g.H + cand - 1) / cand;
     const double pad = double(Tt * cand - g.H) / g.H;
-    if (cand > 1 && pad > 0.15) continue;
+    if (cand > 1 && pad > 0.15 && !w.C) continue;
     if (d == 2) {
       if ((size_t)pb.N[0] * cand * M * esz > smem_green) continue;
       if (round_up(cand * M * tpc0, 32) > kColMaxThreads) continue;
@@ -119,6 +123,7 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     l = std::min(l, cap);
     while (l > 1 && ((size_t)((l * M + 1) / 2) * g.nlast * esz > 96 * 1024)) --l;
     if ((l * M) % 2 && l > 1) --l;
+    if (w.lpc) l = w.lpc;
     lpc = l;
     nseq = (lpc * M + 1) / 2;
     while (lpc > 1 && round_up(((lpc * M + 1) / 2) * tpl, 32) > kRowMaxThreads) --lpc;
@@ -126,7 +131,7 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     row.block = round_up(nseq * tpl, 32);
     row.grid = (g.nlines + lpc - 1) / lpc;
     row.smem = (size_t)nseq * g.nlast * esz + (size_t)std::max(1, nphase) * d * d * sizeof(T);
-    if (row.block > kRowMaxThreads || row.smem > (size_t)optin) {
+    if (row.block > kRowMaxThreads || row.smem > (size_t)optin || (w.lpc && lpc != w.lpc)) {
       err = "row pass does not fit one CTA";
       return 9;
     }
@@ -178,6 +183,11 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     col1.grid = g.Tt * pb.N[0];
     col1.smem = (size_t)pb.N[1] * cb1.Q * esz;
   }
+  tuning.C = g.C;
+  tuning.lpc = lpc;
+  tuning.tpl = tpl;
+  tuning.tpc0 = tpc0;
+  tuning.tpc1 = tpc1;
   vec.block = 256;
   vec.grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 4, (vlen + 255) / 256));
   part_stride = std::max(std::max(row.grid, col0.grid), vec.grid);
@@ -644,6 +654,80 @@ int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int
     res[l].iters = h_scal[l].iter;
     res[l].rel = h_scal[l].rel;
     res[l].alpha = h_scal[l].alpha;
+  }
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::autotune(const Problem& pb, int nloads_, cudaStream_t stream, Tuning& best,
+                          double& best_ms, std::string& err, int max_candidates) {
+  const bool f64 = sizeof(T) == 8;
+  const int d = pb.d;
+  const int nlast = pb.N[d - 1];
+  // candidate plans: every thread count that reaches the minimum stage count
+  // of its axis, plus the next stage count (fewer registers per thread)
+  auto plan_tpls = [&](int n, int maxthr) {
+    std::vector<int> out;
+    int best_st = 1 << 30;
+    std::vector<std::pair<int, int>> all;  // (stages, tpl)
+    for (int t = 1; t <= maxthr; ++t) {
+      std::vector<int> r = plan_radices(n, t, reg_budget(f64));
+      if (r.empty()) continue;
+      const int st = (int)r.size();
+      if (st < best_st) best_st = st;
+      if (all.empty() || all.back().first != st) all.emplace_back(st, t);
+    }
+    for (auto& sv : all)
+      if (sv.first <= best_st + 1) out.push_back(sv.second);
+    return out;
+  };
+  std::vector<int> tpls = plan_tpls(nlast, kRowMaxThreads);
+  std::vector<int> tpc0s = plan_tpls(pb.N[0], kColMaxThreads);
+  std::vector<int> tpc1s = d == 3 ? plan_tpls(pb.N[1], kColMaxThreads) : std::vector<int>{0};
+  std::vector<Tuning> cands;
+  for (int C : {16, 8, 4, 2, 1})
+    for (int lpc : {1, 2, 3, 4, 6, 8})
+      for (int tp : tpls)
+        for (int t0 : tpc0s)
+          for (int t1 : tpc1s) {
+            Tuning c;
+            c.C = C;
+            c.lpc = lpc;
+            c.tpl = tp;
+            c.tpc0 = t0;
+            c.tpc1 = t1;
+            cands.push_back(c);
+          }
+  best_ms = 1e30;
+  int tried = 0;
+  std::string e2;
+  for (const Tuning& c : cands) {
+    if (tried >= max_candidates) break;
+    Pipeline<T> trial;
+    if (trial.init(pb, nloads_, true, stream, e2, &c) != 0) {
+      trial.release();
+      continue;
+    }
+    if (!(trial.tuning == c)) {  // the constraints changed a requested value
+      trial.release();
+      continue;
+    }
+    ++tried;
+    double total = 0.0, t;
+    bool ok = true;
+    for (int what = 0; what < 4 && ok; ++what) {
+      if (trial.profile(what, 10, &t, e2) != 0) ok = false;
+      total += t;
+    }
+    trial.release();
+    if (ok && total < best_ms) {
+      best_ms = total;
+      best = c;
+    }
+  }
+  if (best_ms >= 1e30) {
+    err = "autotune: no candidate could be timed";
+    return 9;
   }
   return 0;
 }

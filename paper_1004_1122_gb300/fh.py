@@ -15,6 +15,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libfh.so")
+# Launch-shape cache read by fh_create and written by fh_autotune (see fh.h);
+# the package ships the shapes tuned on GB300 for its benchmark grids.
+TUNE_CACHE = os.path.join(_HERE, "tune_cache.txt")
+os.environ.setdefault("FH_TUNE_CACHE", TUNE_CACHE)
 
 FH_OK = 0
 STATUS = {
@@ -29,7 +33,7 @@ DT_FP64, DT_FP32 = 0, 1
 # Names declared in include/fh.h (checked by the ABI test).
 EXPORTS = (
     "fh_create", "fh_set_phase", "fh_apply", "fh_solve", "fh_solve_all", "fh_effective_column",
-    "fh_eta_e", "fh_profile", "fh_apply_noalloc", "fh_destroy", "fh_status_string", "fh_last_error",
+    "fh_eta_e", "fh_profile", "fh_autotune", "fh_apply_noalloc", "fh_destroy", "fh_status_string", "fh_last_error",
     "fh_version",
 )
 
@@ -88,6 +92,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fh_eta_e.restype = I
     lib.fh_profile.argtypes = [P, I, I, I, pD]
     lib.fh_profile.restype = I
+    lib.fh_autotune.argtypes = [P, I, pD, pD]
+    lib.fh_autotune.restype = I
     lib.fh_apply_noalloc.argtypes = [I, pI, pD, P, I, pD, pD, P, P, I, P, ctypes.c_char_p, ctypes.c_size_t]
     lib.fh_apply_noalloc.restype = I
     lib.fh_destroy.argtypes = [P]
@@ -253,6 +259,13 @@ class Solver:
         self._check(self.lib.fh_profile(self.ctx, DT_FP64 if dtype == "fp64" else DT_FP32, int(what),
                                         int(reps), _dptr(v)), "fh_profile")
         return float(v[0])
+
+    def autotune(self, dtype: str = "fp32"):
+        """Pick the fastest launch shapes (fh_autotune); returns (ms_before, ms_after)."""
+        b, a = np.zeros(1), np.zeros(1)
+        self._check(self.lib.fh_autotune(self.ctx, DT_FP64 if dtype == "fp64" else DT_FP32, _dptr(b), _dptr(a)),
+                    "fh_autotune")
+        return float(b[0]), float(a[0])
 
     def effective_column(self, e) -> np.ndarray:
         col = np.zeros(self.d)

@@ -114,3 +114,37 @@ def test_apply_full_size_2187():
         ref = oracle.apply_A(ein, phase, L, L0)
         tol = 64 * U[prec] * (1.0 + np.max(np.abs(L - L0[None]))) * np.max(np.abs(e)) * (4.0 if prec == "fp32" else 1.0)
         assert np.max(np.abs(got - ref)) <= tol, (prec, np.max(np.abs(got - ref)), tol)
+
+
+def test_autotune_keeps_parity():
+    """fh_autotune rebuilds the pipeline with another launch shape; the product is unchanged."""
+    torch = cuda_or_skip()
+    import os
+    import tempfile
+
+    from paper_1004_1122_gb300 import fh
+
+    phase, L, L0, e = _problem((243, 135), seed=21)
+    old = os.environ.get("FH_TUNE_CACHE")
+    with tempfile.TemporaryDirectory() as tmp:
+        os.environ["FH_TUNE_CACHE"] = os.path.join(tmp, "tune.txt")
+        try:
+            with fh.Solver(phase, L, L0=L0, precision="fp32") as s:
+                et = torch.from_numpy(e).float().cuda()
+                before = s.apply(et).double().cpu().numpy()
+                ms0, ms1 = s.autotune("fp32")
+                after = s.apply(et).double().cpu().numpy()
+            assert ms1 <= ms0 * 1.0001
+            assert os.path.getsize(os.environ["FH_TUNE_CACHE"]) > 0
+            with fh.Solver(phase, L, L0=L0, precision="fp32") as s2:  # starts from the cache
+                again = s2.apply(et).double().cpu().numpy()
+        finally:
+            if old is None:
+                del os.environ["FH_TUNE_CACHE"]
+            else:
+                os.environ["FH_TUNE_CACHE"] = old
+    ein = e.astype(np.float32).astype(np.float64)
+    ref = oracle.apply_A(ein, phase, L, L0)
+    tol = 64 * U["fp32"] * 4 * (1.0 + np.max(np.abs(L - L0[None]))) * np.max(np.abs(e))
+    for got in (before, after, again):
+        assert np.max(np.abs(got - ref)) <= tol
