@@ -190,6 +190,53 @@ fh_status fh_profile(fh_ctx* ctx, int dtype, int what, int reps, double* ms);
  * Synchronises.  Errors: FH_ERR_ARG, FH_ERR_OOM, FH_ERR_CUDA, FH_ERR_UNSUPPORTED. */
 fh_status fh_autotune(fh_ctx* ctx, int dtype, double* ms_before, double* ms_after);
 
+/* ---- Batches of independent 2-D cells (serving-style sweeps) ------------
+ *
+ * fh_batch_create -- many independent 2-D cells, possibly of different odd
+ * sizes, solved together.  Cells of one size form a group; each group runs
+ * every kernel over all of its cells in one launch (per-cell phase tables,
+ * per-cell reference medium L0 = Eq. (opt_ref) of that cell's phases,
+ * per-(cell, load) Krylov scalars; converged cells are skipped inside the
+ * kernels), and the groups iterate concurrently on their own streams in
+ * CUDA-graph chunks.
+ *  out        host; receives the batch.
+ *  ncells     >= 1.
+ *  N          host, 2*ncells ints (N_0, N_1 of each cell; odd, >= 3, factors 3/5/7).
+ *  phase      host array of ncells host pointers, cell c has N_0*N_1 bytes.
+ *  nphase     host, ncells ints in 1..256.
+ *  L          host array of ncells host pointers, cell c has nphase[c]*4
+ *             float64 (SPD 2x2 tensors, row-major).
+ *  nloads     1 or 2 loads solved per cell.
+ *  precision  FH_FP64 or FH_FP32_REFINED.
+ * Everything is copied; the batch owns its device memory (one stream per
+ * group).  Errors: FH_ERR_ARG, FH_ERR_EVEN_N, FH_ERR_NOT_SPD, FH_ERR_OOM,
+ * FH_ERR_CUDA, FH_ERR_UNSUPPORTED. */
+typedef struct fh_batch fh_batch;
+fh_status fh_batch_create(fh_batch** out, int ncells, const int* N, const uint8_t* const* phase,
+                          const int* nphase, const double* const* L, int nloads, int precision);
+
+/* fh_batch_solve -- solve every (cell, load) to the float64 true relative
+ * residual tol (Section 2.3 solvers; FP32 inner solves with float64
+ * refinement for FH_FP32_REFINED).
+ *  E        host, 2*nloads float64: the loads, E[2*l + a].
+ *  Leff     host, ncells*2*nloads float64: Leff[(c*2 + a)*nloads + l] is
+ *           component a of <L e> of cell c under load l (a column of the
+ *           cell's effective tensor for a unit load).
+ *  status   host, ncells*nloads fh_status per (cell, load), or NULL.
+ *  iters    host, ncells*nloads inner iterations per (cell, load), or NULL.
+ *  summary  host, or NULL: total iterations, refinement steps, worst true
+ *           residual, kernels launched.
+ * Returns FH_OK if every (cell, load) converged, else the first failure
+ * status.  Synchronises. */
+fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, int max_iter,
+                         double* Leff, int* status, int* iters, fh_info* summary);
+
+/* Last error message of a batch (never NULL). */
+const char* fh_batch_last_error(const fh_batch* b);
+
+/* fh_batch_destroy -- free a batch.  NULL is a no-op. */
+void fh_batch_destroy(fh_batch* b);
+
 /* fh_apply_noalloc -- fh_apply for callers that cannot allocate device memory
  * (the paper has no counterpart; this is a deployment convenience).
  *

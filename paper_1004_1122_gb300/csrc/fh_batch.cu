@@ -1,0 +1,469 @@
+// fh_batch.cu -- many independent 2-D cells of uneven sizes solved together.
+//
+// Cells are grouped by grid size.  Every group is one pipeline whose kernels
+// treat the group's cells as extra lines of one launch (per-cell dL tables,
+// per-cell reference media, per-(cell, load) Krylov scalars; a cell whose
+// loads have converged is skipped inside the kernels).  Each group iterates in
+// its own CUDA-graph chunks on its own stream, so the groups run concurrently;
+// the host polls every group's small scalar block once per round.
+// Float32 inner solves with a float64 outer residual per (cell, load) follow
+// the single-cell refinement of fh_solve.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fh.h"
+#include "fh_pipeline.cuh"
+
+using fh::Pipeline;
+using fh::Problem;
+using fh::SolveResult;
+
+namespace {
+
+__global__ void kb_fill(double* x, long long nodes, int d, double e0, double e1) {
+  const long long len = nodes * d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = i < nodes ? e0 : e1;
+}
+__global__ void kb_to_float(const double* in, float* out, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+__global__ void kb_add(double* x, const float* dx, long long len) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] += (double)dx[i];
+}
+// Inner float32 solves stop as stalled after this many iterations without
+// halving their residual (see the single-cell driver).
+constexpr int kInnerStallWindow = 100;
+
+int grid_for(long long len) {
+  const long long g = (len + 255) / 256;
+  return (int)std::max<long long>(1, std::min<long long>(g, 2048));
+}
+
+struct Group {
+  int N[2] = {0, 0};
+  std::vector<int> cells;  // global cell ids, in batch order
+  Problem pb;
+  uint8_t* d_phase = nullptr;
+  cudaStream_t st = nullptr;
+  Pipeline<float>* p32 = nullptr;
+  Pipeline<double>* p64 = nullptr;
+  double* x64[fh::kMaxLoads] = {};  // refinement iterate per load
+  double* r64[fh::kMaxLoads] = {};
+  long long launches0 = 0;
+};
+
+bool spd2(const double* A) {
+  const double s = std::fmax(std::fabs(A[0]), std::fmax(std::fabs(A[1]), std::fabs(A[3])));
+  if (!(s > 0.0) || !std::isfinite(s)) return false;
+  if (std::fabs(A[1] - A[2]) > 1e-12 * s) return false;
+  return A[0] > 0.0 && A[0] * A[3] - A[1] * A[2] > 1e-14 * s * s;
+}
+
+void eig2(const double* A, double& lo, double& hi) {
+  const double tr = A[0] + A[3], det = A[0] * A[3] - A[1] * A[2];
+  const double disc = std::sqrt(std::fmax(0.0, 0.25 * tr * tr - det));
+  lo = 0.5 * tr - disc;
+  hi = 0.5 * tr + disc;
+}
+
+}  // namespace
+
+struct fh_batch {
+  int ncells = 0;
+  int nloads = 0;
+  int precision = FH_FP32_REFINED;
+  std::vector<Group> groups;
+  std::string err;
+  long long own_launches = 0;
+};
+
+extern "C" {
+
+void fh_batch_destroy(fh_batch* b) {
+  if (!b) return;
+  for (Group& g : b->groups) {
+    if (g.st) cudaStreamSynchronize(g.st);
+    if (g.p32) {
+      g.p32->release();
+      delete g.p32;
+    }
+    if (g.p64) {
+      g.p64->release();
+      delete g.p64;
+    }
+    for (int l = 0; l < fh::kMaxLoads; ++l) {
+      if (g.x64[l]) cudaFree(g.x64[l]);
+      if (g.r64[l]) cudaFree(g.r64[l]);
+    }
+    if (g.d_phase) cudaFree(g.d_phase);
+    if (g.st) cudaStreamDestroy(g.st);
+  }
+  delete b;
+}
+
+fh_status fh_batch_create(fh_batch** out, int ncells, const int* N, const uint8_t* const* phase,
+                          const int* nphase, const double* const* L, int nloads, int precision) {
+  if (!out) return FH_ERR_ARG;
+  *out = nullptr;
+  if (ncells < 1 || !N || !phase || !nphase || !L || nloads < 1 || nloads > 2) return FH_ERR_ARG;
+  if (precision != FH_FP64 && precision != FH_FP32_REFINED) return FH_ERR_ARG;
+  std::map<std::pair<int, int>, int> gid;
+  fh_batch* b = new (std::nothrow) fh_batch();
+  if (!b) return FH_ERR_OOM;
+  b->ncells = ncells;
+  b->nloads = nloads;
+  b->precision = precision;
+  for (int c = 0; c < ncells; ++c) {
+    const int n0 = N[2 * c], n1 = N[2 * c + 1];
+    if (n0 < 3 || n1 < 3 || !phase[c] || !L[c] || nphase[c] < 1 || nphase[c] > 256) {
+      fh_batch_destroy(b);
+      return FH_ERR_ARG;
+    }
+    if (n0 % 2 == 0 || n1 % 2 == 0) {
+      fh_batch_destroy(b);
+      return FH_ERR_EVEN_N;
+    }
+    for (int p = 0; p < nphase[c]; ++p)
+      if (!spd2(L[c] + 4 * p)) {
+        fh_batch_destroy(b);
+        return FH_ERR_NOT_SPD;
+      }
+    auto key = std::make_pair(n0, n1);
+    auto it = gid.find(key);
+    if (it == gid.end()) {
+      gid[key] = (int)b->groups.size();
+      b->groups.emplace_back();
+      b->groups.back().N[0] = n0;
+      b->groups.back().N[1] = n1;
+      it = gid.find(key);
+    }
+    b->groups[it->second].cells.push_back(c);
+  }
+  for (Group& g : b->groups) {
+    const int nc = (int)g.cells.size();
+    const long long cn = (long long)g.N[0] * g.N[1];
+    int np = 1;
+    for (int c : g.cells) np = std::max(np, nphase[c]);
+    Problem& pb = g.pb;
+    pb.d = 2;
+    pb.N[0] = g.N[0];
+    pb.N[1] = g.N[1];
+    pb.nodes = cn * nc;
+    pb.nphase = np;
+    pb.ncell = nc;
+    pb.L.assign((size_t)nc * np * 4, 0.0);
+    pb.dL.assign((size_t)nc * np * 4, 0.0);
+    pb.L0cell.assign((size_t)nc * 9, 0.0);
+    for (int k = 0; k < nc; ++k) {
+      const int c = g.cells[k];
+      double lo = 1e300, hi = -1e300;
+      for (int p = 0; p < nphase[c]; ++p) {
+        double a, bb;
+        eig2(L[c] + 4 * p, a, bb);
+        lo = std::fmin(lo, a);
+        hi = std::fmax(hi, bb);
+      }
+      const double l0 = 0.5 * (lo + hi);  // Eq. (opt_ref) per cell
+      pb.L0cell[9 * k + 0] = l0;
+      pb.L0cell[9 * k + 4] = l0;
+      for (int p = 0; p < np; ++p) {
+        const double* src = L[c] + 4 * std::min(p, nphase[c] - 1);
+        for (int i = 0; i < 4; ++i) {
+          pb.L[((size_t)k * np + p) * 4 + i] = src[i];
+          pb.dL[((size_t)k * np + p) * 4 + i] = src[i] - (i == 0 || i == 3 ? l0 : 0.0);
+        }
+      }
+    }
+    pb.L0 = {pb.L0cell[0], 0.0, 0.0, pb.L0cell[4]};
+    cudaError_t e = cudaStreamCreate(&g.st);
+    if (e == cudaSuccess) e = cudaMalloc(&g.d_phase, pb.nodes);
+    if (e != cudaSuccess) {
+      fh_batch_destroy(b);
+      return FH_ERR_OOM;
+    }
+    for (int k = 0; k < nc; ++k) {
+      const uint8_t* src = phase[g.cells[k]];
+      for (long long i = 0; i < cn; ++i)
+        if (src[i] >= nphase[g.cells[k]]) {
+          fh_batch_destroy(b);
+          return FH_ERR_ARG;
+        }
+      e = cudaMemcpy(g.d_phase + (size_t)k * cn, src, cn, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        fh_batch_destroy(b);
+        return FH_ERR_CUDA;
+      }
+    }
+    pb.d_phase = g.d_phase;
+    std::string err;
+    int rc = 0;
+    g.p64 = new (std::nothrow) Pipeline<double>();
+    if (!g.p64) rc = FH_ERR_OOM;
+    if (!rc) rc = g.p64->init(pb, nloads, precision == FH_FP64, g.st, err);
+    if (!rc && precision == FH_FP32_REFINED) {
+      g.p32 = new (std::nothrow) Pipeline<float>();
+      if (!g.p32) rc = FH_ERR_OOM;
+      if (!rc) rc = g.p32->init(pb, nloads, true, g.st, err);
+    }
+    for (int l = 0; l < nloads && !rc; ++l) {
+      if (cudaMalloc(&g.x64[l], 2 * pb.nodes * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&g.r64[l], 2 * pb.nodes * sizeof(double)) != cudaSuccess)
+        rc = FH_ERR_OOM;
+    }
+    if (rc) {
+      b->err = err;
+      fh_batch_destroy(b);
+      return (fh_status)rc;
+    }
+  }
+  *out = b;
+  return FH_OK;
+}
+
+const char* fh_batch_last_error(const fh_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, int max_iter,
+                         double* Leff, int* status, int* iters, fh_info* summary) {
+  if (!b || !E || !Leff || !(tol > 0.0) || max_iter < 0 || method < FH_CG || method > FH_FIXED_POINT)
+    return FH_ERR_ARG;
+  const int nl = b->nloads;
+  double Ev[fh::kMaxLoads][fh::kMaxD] = {};
+  double e2[fh::kMaxLoads] = {};
+  for (int l = 0; l < nl; ++l) {
+    Ev[l][0] = E[2 * l];
+    Ev[l][1] = E[2 * l + 1];
+    e2[l] = Ev[l][0] * Ev[l][0] + Ev[l][1] * Ev[l][1];
+    if (!std::isfinite(e2[l])) return FH_ERR_ARG;
+  }
+  std::string err;
+  auto fail = [&](int rc) {
+    b->err = err;
+    return (fh_status)rc;
+  };
+  const int ng = (int)b->groups.size();
+  long long launches0 = b->own_launches;
+  for (Group& g : b->groups)
+    launches0 += g.p64->launches + (g.p32 ? g.p32->launches : 0);
+  // per (group, item) bookkeeping, item = k * nl + l
+  std::vector<std::vector<int>> st(ng), its(ng);
+  std::vector<std::vector<double>> rel(ng);
+  for (int gi = 0; gi < ng; ++gi) {
+    const int items = (int)b->groups[gi].cells.size() * nl;
+    st[gi].assign(items, fh::kRunning);
+    its[gi].assign(items, 0);
+    rel[gi].assign(items, INFINITY);
+  }
+  int outer = 0;
+  double worst = 0.0;
+
+  if (b->precision == FH_FP64) {
+    for (Group& g : b->groups) {
+      int rc = g.p64->solve_begin(method, Ev, false, fh::kX0Const, nullptr, tol, max_iter, err);
+      if (rc) return fail(rc);
+    }
+    std::vector<bool> done(ng, false);
+    for (long long round = 0;; ++round) {
+      bool all = true;
+      for (int gi = 0; gi < ng; ++gi) {
+        if (done[gi]) continue;
+        int rc = b->groups[gi].p64->solve_step(err);
+        if (rc) return fail(rc);
+      }
+      for (int gi = 0; gi < ng; ++gi) {
+        if (done[gi]) continue;
+        cudaError_t e = cudaStreamSynchronize(b->groups[gi].st);
+        if (e != cudaSuccess) return FH_ERR_CUDA;
+        done[gi] = b->groups[gi].p64->solve_done();
+        all = all && done[gi];
+      }
+      if (all) break;
+      if (round > (long long)max_iter + 64) return FH_ERR_TIMEOUT;
+    }
+    for (int gi = 0; gi < ng; ++gi) {
+      Group& g = b->groups[gi];
+      std::vector<SolveResult> res(g.cells.size() * nl);
+      g.p64->solve_results(res.data());
+      // true residual per item
+      std::vector<double> rr(res.size());
+      const double* xin[fh::kMaxLoads];
+      double* rout[fh::kMaxLoads];
+      for (int l = 0; l < nl; ++l) {
+        xin[l] = g.p64->x[l];
+        rout[l] = g.r64[l];
+      }
+      int rc = g.p64->residual(xin, rout, false, Ev, rr.data(), err);
+      if (rc) return fail(rc);
+      const long long cn = (long long)g.N[0] * g.N[1];
+      for (size_t it = 0; it < res.size(); ++it) {
+        const int l = (int)(it % nl);
+        rel[gi][it] = std::sqrt(rr[it] / std::max(e2[l] * cn, 1e-300));
+        its[gi][it] = res[it].iters;
+        st[gi][it] = (res[it].status == fh::kConverged && rel[gi][it] <= tol) ? fh::kConverged
+                     : res[it].status == fh::kBreakdown                       ? fh::kBreakdown
+                                                                              : fh::kCap;
+      }
+      for (int l = 0; l < nl; ++l)
+        cudaMemcpyAsync(g.x64[l], g.p64->x[l], 2 * g.pb.nodes * sizeof(double), cudaMemcpyDeviceToDevice,
+                        g.st);
+    }
+  } else {
+    // float32 inner solves, float64 outer residual per (cell, load)
+    for (Group& g : b->groups)
+      for (int l = 0; l < nl; ++l) {
+        ++b->own_launches;
+        kb_fill<<<grid_for(2 * g.pb.nodes), 256, 0, g.st>>>(g.x64[l], g.pb.nodes, 2, Ev[l][0], Ev[l][1]);
+      }
+    std::vector<std::vector<double>> prev(ng);
+    for (int gi = 0; gi < ng; ++gi) prev[gi].assign(st[gi].size(), INFINITY);
+    for (;;) {
+      bool any = false;
+      std::vector<std::vector<double>> eta(ng);
+      for (int gi = 0; gi < ng; ++gi) {
+        Group& g = b->groups[gi];
+        std::vector<double> rr(st[gi].size());
+        const double* xin[fh::kMaxLoads];
+        double* rout[fh::kMaxLoads];
+        for (int l = 0; l < nl; ++l) {
+          xin[l] = g.x64[l];
+          rout[l] = g.r64[l];
+        }
+        int rc = g.p64->residual(xin, rout, false, Ev, rr.data(), err);
+        if (rc) return fail(rc);
+        const long long cn = (long long)g.N[0] * g.N[1];
+        eta[gi].assign(st[gi].size(), 1.0);
+        for (size_t it = 0; it < rr.size(); ++it) {
+          const int l = (int)(it % nl);
+          if (st[gi][it] != fh::kRunning) continue;
+          const double r = std::sqrt(rr[it] / std::max(e2[l] * cn, 1e-300));
+          rel[gi][it] = r;
+          if (!std::isfinite(r)) {
+            st[gi][it] = fh::kBreakdown;
+          } else if (r <= tol) {
+            st[gi][it] = fh::kConverged;
+          } else if (its[gi][it] >= max_iter || (outer > 0 && !(r < 0.9 * prev[gi][it]))) {
+            st[gi][it] = fh::kCap;
+          } else {
+            double e = 0.3 * tol / r;
+            eta[gi][it] = std::min(0.1, std::max(2e-6, e));
+            any = true;
+          }
+          prev[gi][it] = r;
+        }
+      }
+      if (!any) break;
+      int budget = 0;
+      for (int gi = 0; gi < ng; ++gi)
+        for (size_t it = 0; it < its[gi].size(); ++it)
+          if (st[gi][it] == fh::kRunning) budget = std::max(budget, max_iter - its[gi][it]);
+      // inner solves of every group, concurrently
+      std::vector<bool> active(ng, false);
+      for (int gi = 0; gi < ng; ++gi) {
+        Group& g = b->groups[gi];
+        bool need = false;
+        for (size_t it = 0; it < st[gi].size(); ++it) need = need || st[gi][it] == fh::kRunning;
+        if (!need) continue;
+        active[gi] = true;
+        for (int l = 0; l < nl; ++l) {
+          ++b->own_launches;
+          kb_to_float<<<grid_for(2 * g.pb.nodes), 256, 0, g.st>>>(g.r64[l], g.p32->rhs[l], 2 * g.pb.nodes);
+        }
+        int x0 = fh::kX0Rhs;
+        if (method != FH_FIXED_POINT) {
+          // start at the exact complement part of the correction, d0 = (I - Q) r
+          int rc0 = g.p32->project_complement(g.p32->rhs, g.p32->x, err);
+          if (rc0) return fail(rc0);
+          x0 = fh::kX0Keep;
+        }
+        int rc = g.p32->solve_begin(method, Ev, true, x0, nullptr, 1.0, budget, err, eta[gi].data(),
+                                    kInnerStallWindow);
+        if (rc) return fail(rc);
+      }
+      for (long long round = 0;; ++round) {
+        bool all = true;
+        for (int gi = 0; gi < ng; ++gi) {
+          if (!active[gi]) continue;
+          int rc = b->groups[gi].p32->solve_step(err);
+          if (rc) return fail(rc);
+        }
+        for (int gi = 0; gi < ng; ++gi) {
+          if (!active[gi]) continue;
+          if (cudaStreamSynchronize(b->groups[gi].st) != cudaSuccess) return FH_ERR_CUDA;
+          if (b->groups[gi].p32->solve_done()) active[gi] = false;
+          all = all && !active[gi];
+        }
+        if (all) break;
+        if (round > (long long)budget + 64) return FH_ERR_TIMEOUT;
+      }
+      for (int gi = 0; gi < ng; ++gi) {
+        Group& g = b->groups[gi];
+        std::vector<SolveResult> res(st[gi].size());
+        g.p32->solve_results(res.data());
+        for (size_t it = 0; it < res.size(); ++it)
+          if (st[gi][it] == fh::kRunning) its[gi][it] += res[it].iters;
+        for (int l = 0; l < nl; ++l) {
+          ++b->own_launches;
+          kb_add<<<grid_for(2 * g.pb.nodes), 256, 0, g.st>>>(g.x64[l], g.p32->x[l], 2 * g.pb.nodes);
+        }
+      }
+      ++outer;
+    }
+  }
+  // effective tensor columns per cell and load (float64)
+  for (int gi = 0; gi < ng; ++gi) {
+    Group& g = b->groups[gi];
+    const int nc = (int)g.cells.size();
+    std::vector<double> col((size_t)nc * 2);
+    for (int l = 0; l < nl; ++l) {
+      int rc = g.p64->current_mean(g.x64[l], col.data(), err);
+      if (rc) return fail(rc);
+      for (int k = 0; k < nc; ++k) {
+        const int c = g.cells[k];
+        for (int a = 0; a < 2; ++a) Leff[((size_t)c * 2 + a) * nl + l] = col[2 * k + a];
+        const int it = k * nl + l;
+        if (status) status[(size_t)c * nl + l] = st[gi][it] == fh::kConverged ? FH_OK
+                                                : st[gi][it] == fh::kBreakdown  ? FH_ERR_BREAKDOWN
+                                                                                : FH_ERR_NOT_CONVERGED;
+        if (iters) iters[(size_t)c * nl + l] = its[gi][it];
+        worst = std::max(worst, rel[gi][it]);
+      }
+    }
+  }
+  fh_status first = FH_OK;
+  for (int gi = 0; gi < ng; ++gi)
+    for (int s2 : st[gi])
+      if (first == FH_OK && s2 != fh::kConverged)
+        first = s2 == fh::kBreakdown ? FH_ERR_BREAKDOWN : FH_ERR_NOT_CONVERGED;
+  if (summary) {
+    long long total = 0;
+    for (auto& v : its)
+      for (int x : v) total += x;
+    long long launches = b->own_launches;
+    for (Group& g : b->groups) launches += g.p64->launches + (g.p32 ? g.p32->launches : 0);
+    summary->iters = (int)std::min<long long>(total, 2147483647LL);
+    summary->outer_iters = outer;
+    summary->matvecs = 0;
+    summary->status = first;
+    summary->rel_res_true = worst;
+    summary->rel_res = NAN;
+    summary->eta_r = NAN;
+    summary->eta_e = NAN;
+    summary->history_len = 0;
+    summary->launches = launches - launches0;
+  }
+  for (Group& g : b->groups)
+    if (cudaStreamSynchronize(g.st) != cudaSuccess) return FH_ERR_CUDA;
+  return first;
+}
+
+}  // extern "C"

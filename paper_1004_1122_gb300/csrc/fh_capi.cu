@@ -213,6 +213,11 @@ int init_tuned(Pipeline<T>* P, const Problem& pb, bool krylov, cudaStream_t st, 
   return P->init(pb, 1, krylov, st, err);
 }
 
+// An inner float32 solve whose recursive residual has not halved for this many
+// iterations has reached float32's noise floor for its right-hand side; the
+// float64 outer residual then decides whether another refinement step helps.
+constexpr int kInnerStallWindow = 100;
+
 bool l0_isotropic(const Problem& pb, double& l0) {
   const int d = pb.d;
   l0 = pb.L0[0];
@@ -584,8 +589,17 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
       ++c->own_launches;
       k_to_float<<<vec_grid(len), 256, 0, c->st>>>(c->d_r64, P->rhs[0], P->x[0], len);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "refine init");
-      rc = P->solve(method, Ev, true, method == fh::kFixed ? fh::kX0Rhs : fh::kX0Zero, nullptr, eta,
-                    max_iter - total, &res, err);
+      int x0 = fh::kX0Rhs;
+      if (method != fh::kFixed) {
+        // start at the exact complement part of the correction, d0 = (I - Q) r
+        float* rr_[fh::kMaxLoads] = {P->rhs[0]};
+        float* xx_[fh::kMaxLoads] = {P->x[0]};
+        rc = P->project_complement(rr_, xx_, err);
+        if (rc) return from_rc(c, rc, err);
+        x0 = fh::kX0Keep;
+      }
+      rc = P->solve(method, Ev, true, x0, nullptr, eta, max_iter - total, &res, err, nullptr,
+                    kInnerStallWindow);
       if (rc) return from_rc(c, rc, err);
       total += res.iters;
       hist_len = res.iters + 1;

@@ -61,9 +61,23 @@ struct Scal {
   int hist_cap;
   double* hist;    // device history array or nullptr
   double E[3];     // constant right-hand side (macroscopic field) when no rhs field
+  double best_rel; // smallest relative residual so far
+  int best_iter;   // iteration at which best_rel last halved
+  int stall_window;// > 0: stop as kStalled after this many iterations without halving
 };
 
-enum : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kCap = 3 };
+// kStalled: the recursive residual stopped decreasing (the working precision's
+// noise floor); refinement drivers continue from it with a float64 residual.
+enum : int { kRunning = 0, kConverged = 1, kBreakdown = 2, kCap = 3, kStalled = 4 };
+
+__device__ __forceinline__ bool stalled(Scal& s) {
+  if (!(s.rel < 0.5 * s.best_rel) && s.best_rel > 0.0) {
+    return s.stall_window > 0 && s.iter - s.best_iter >= s.stall_window;
+  }
+  s.best_rel = s.rel;
+  s.best_iter = s.iter;
+  return false;
+}
 
 struct Mat3 {
   double v[9];
@@ -81,9 +95,16 @@ struct Geom {
   long long nodes;
   int M;          // channels = d * nloads
   int nloads;
+  int cshift;     // log2(C): tile widths are powers of two
   double invY[3];
   double L0[9];
   double inv_nodes;
+  // batches of same-size cells: cell b owns lines [b*lines_cell, (b+1)*lines_cell)
+  // and nodes [b*cell_nodes, (b+1)*cell_nodes) of every component plane
+  int ncell;
+  int lines_cell;
+  long long cell_nodes;
+  int tab_stride;   // table entries per cell (nphase * d * d)
 };
 
 template <typename T> struct RowArgs {
@@ -103,8 +124,8 @@ template <typename T> struct RowArgs {
   const T* aux[kMaxLoads];
   T* aux2[kMaxLoads];
   const T* rhs[kMaxLoads];   // field right-hand side or nullptr for constant scal[l].E
-  Scal* scal;               // nloads entries
-  double* part;             // partials [nloads][gridDim.x]
+  Scal* scal;               // [ncell][NL] entries
+  double* part;             // partials [NL][gridDim.x]
 };
 
 struct ColArgsBase {
@@ -125,6 +146,7 @@ template <typename T> struct ColArgs {
   cplx<T>* S;
   Scal* scal;
   double* part;
+  const double* L0cell;  // per-cell reference medium [ncell][9], or nullptr for g.L0
 };
 
 // ----------------------------------------------------------------------------
@@ -204,10 +226,13 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
   C* sm = reinterpret_cast<C*>(smem_raw);
   T* stab = reinterpret_cast<T*>(sm + (size_t)a.nseq * a.plan.n);
   const Geom& g = a.g;
-  if (all_done(a.scal, NL)) return;
   const int n = a.plan.n;
   constexpr int d = D, M = D * NL;
   const int line0 = blockIdx.x * a.lpc;
+  const int cell = g.ncell > 1 ? line0 / g.lines_cell : 0;
+  Scal* const sc = a.scal ? a.scal + cell * NL : nullptr;
+  const T* const tabc = a.tab + (size_t)cell * g.tab_stride;
+  if (all_done(sc, NL)) return;
 
   constexpr bool kUseTab = (PRO == kProApply || PRO == kProDir);
   constexpr bool kDir = (PRO == kProDir || PRO == kProDirPlain);
@@ -217,13 +242,13 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
   T* pout[NL];
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
-    lact[l] = !kDir || a.scal[l].done == kRunning;
-    lbeta[l] = kDir ? T(a.scal[l].beta) : T(0);
+    lact[l] = !kDir || sc[l].done == kRunning;
+    lbeta[l] = kDir ? T(sc[l].beta) : T(0);
     pin[l] = a.in[l];
     pout[l] = a.out[l];
   }
   if (kUseTab) {
-    for (int i = threadIdx.x; i < a.nphase * d * d; i += blockDim.x) stab[i] = a.tab[i];
+    for (int i = threadIdx.x; i < a.nphase * d * d; i += blockDim.x) stab[i] = tabc[i];
   }
   __syncthreads();
 
@@ -297,35 +322,47 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
     run_fft<false, T>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
   }
 
-  // 3. unpack two real spectra per sequence and store the half spectrum
-  const int CM = g.C * M;
-  const int per_t = a.lpc * CM;
-  for (int idx = threadIdx.x; idx < g.Tt * per_t; idx += blockDim.x) {
-    const int t = idx / per_t;
-    int rem = idx - t * per_t;
-    const int ll = rem / CM;
-    rem -= ll * CM;
-    const int c = rem / M, m = rem - c * M;
+  // 3. unpack two real spectra per sequence and store the half spectrum:
+  // one thread per (line, frequency kx), all M channels of that frequency
+  // (contiguous in the tiled layout) written together.
+  const int TC = g.Tt * g.C;
+  for (int ll = 0; ll < a.lpc; ++ll) {
     const int line = line0 + ll;
-    if (line >= g.nlines) continue;
-    const int kx = t * g.C + c;
-    C val;
-    val.x = T(0);
-    val.y = T(0);
-    if (kx < g.H) {
-      const int gch = ll * M + m;
-      const C* seq = sm + (size_t)(gch >> 1) * n;
-      const C z1 = seq[kx];
-      const C z2 = seq[kx == 0 ? 0 : n - kx];
-      if ((gch & 1) == 0) {
-        val.x = T(0.5) * (z1.x + z2.x);
-        val.y = T(0.5) * (z1.y - z2.y);
+    if (line >= g.nlines) break;
+    for (int kx = threadIdx.x; kx < TC; kx += blockDim.x) {
+      const int t = kx >> g.cshift, c = kx & (g.C - 1);
+      const int kneg = kx == 0 ? 0 : n - kx;
+      C val[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        val[m].x = T(0);
+        val[m].y = T(0);
+        if (kx < g.H) {
+          const int gch = ll * M + m;
+          const C* seq = sm + (size_t)(gch >> 1) * n;
+          const C z1 = seq[kx];
+          const C z2 = seq[kneg];
+          if ((gch & 1) == 0) {
+            val[m].x = T(0.5) * (z1.x + z2.x);
+            val[m].y = T(0.5) * (z1.y - z2.y);
+          } else {
+            val[m].x = T(0.5) * (z1.y + z2.y);
+            val[m].y = T(0.5) * (z2.x - z1.x);
+          }
+        }
+      }
+      C* dst = a.S + (((long long)t * g.nlines + line) * g.C + c) * M;
+      if constexpr (sizeof(C) == 8 && M % 2 == 0) {
+        // float32: two complex values per 16-byte store
+#pragma unroll
+        for (int m = 0; m < M; m += 2)
+          reinterpret_cast<float4*>(dst)[m / 2] =
+              make_float4((float)val[m].x, (float)val[m].y, (float)val[m + 1].x, (float)val[m + 1].y);
       } else {
-        val.x = T(0.5) * (z1.y + z2.y);
-        val.y = T(0.5) * (z2.x - z1.x);
+#pragma unroll
+        for (int m = 0; m < M; ++m) dst[m] = val[m];
       }
     }
-    a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m] = val;
   }
 }
 
@@ -341,11 +378,13 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
   C* sm = reinterpret_cast<C*>(smem_raw);
   const ColArgsBase& b = a.b;
   const Geom& g = b.g;
-  if (all_done(a.scal, g.nloads)) return;
   constexpr int d = D;
   const int n = b.plan.n, Q = b.Q;
   const int blk_outer = blockIdx.x / b.nb_inner;
   const int blk_inner = blockIdx.x - blk_outer * b.nb_inner;
+  // 2-D batches: the inner block index is the cell
+  const int cell = (D == 2 && g.ncell > 1) ? blk_inner : 0;
+  if (all_done(a.scal ? a.scal + cell * g.nloads : nullptr, g.nloads)) return;
   const long long base = blk_outer * b.base_outer + blk_inner * b.base_inner;
   // columns that fall outside the grid (partial G group in 3-D) are zero
   int qvalid = Q;
@@ -407,10 +446,11 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
     T invY[D], L0[D * D];
 #pragma unroll
     for (int p = 0; p < D; ++p) invY[p] = T(g.invY[p]);
+    const double* L0src = a.L0cell ? a.L0cell + 9 * cell : g.L0;
 #pragma unroll
     for (int p = 0; p < D; ++p)
 #pragma unroll
-      for (int r = 0; r < D; ++r) L0[p * D + r] = T(g.L0[p * 3 + r]);
+      for (int r = 0; r < D; ++r) L0[p * D + r] = T(L0src[p * 3 + r]);
     const T inv_nodes = T(g.inv_nodes);
     double acc[2] = {0.0, 0.0};
     for (int idx = threadIdx.x; idx < n * ngrp; idx += blockDim.x) {
@@ -508,68 +548,59 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_inv(RowArgs<T> a) {
   C* sm = reinterpret_cast<C*>(smem_raw);
   T* stab = reinterpret_cast<T*>(sm + (size_t)a.nseq * a.plan.n);
   const Geom& g = a.g;
-  if (all_done(a.scal, NL)) return;
   const int n = a.plan.n;
   constexpr int d = D, M = D * NL;
   const int line0 = blockIdx.x * a.lpc;
   const int nch = a.lpc * M;
+  const int cell = g.ncell > 1 ? line0 / g.lines_cell : 0;
+  Scal* const sc = a.scal ? a.scal + cell * NL : nullptr;
+  const T* const tabc = a.tab + (size_t)cell * g.tab_stride;
+  if (all_done(sc, NL)) return;
 
   if (EPI == kEpiApplyT) {
-    for (int i = threadIdx.x; i < a.nphase * D * D; i += blockDim.x) stab[i] = a.tab[i];
+    for (int i = threadIdx.x; i < a.nphase * D * D; i += blockDim.x) stab[i] = tabc[i];
   }
 
   // 1. rebuild the full spectrum of each packed sequence from the half spectra
-  // (loads of kUnroll items per thread are issued before they are used)
+  // (one thread per (sequence, kx); kUnroll frequencies' loads in flight)
   constexpr int kUnroll = 8;
-  const int per_t = a.nseq * g.C;
-  const int nitems = g.Tt * per_t;
-  for (int base = threadIdx.x; base < nitems; base += kUnroll * blockDim.x) {
-    C y0[kUnroll], y1[kUnroll];
+  for (int s = 0; s < a.nseq; ++s) {
+    const int g0 = 2 * s, g1 = 2 * s + 1;
+    const int ll0 = g0 / M, m0 = g0 - ll0 * M;
+    const int ll1 = g1 / M, m1 = g1 - ll1 * M;
+    const bool has0 = line0 + ll0 < g.nlines;
+    const bool has1 = g1 < nch && line0 + ll1 < g.nlines;
+    C* seq = sm + (size_t)s * n;
+    for (int kb = threadIdx.x; kb < g.H; kb += kUnroll * blockDim.x) {
+      C y0[kUnroll], y1[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int idx = base + u * blockDim.x;
-      y0[u].x = y0[u].y = y1[u].x = y1[u].y = T(0);
-      if (idx >= nitems) continue;
-      const int t = idx / per_t;
-      const int rem = idx - t * per_t;
-      const int s = rem / g.C, c = rem - s * g.C;
-      const int kx = t * g.C + c;
-      if (kx >= g.H) continue;
-      const int g0 = 2 * s, g1 = 2 * s + 1;
-      {
-        const int ll = g0 / M, m = g0 - ll * M;
-        const int line = line0 + ll;
-        if (line < g.nlines) y0[u] = a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m];
+      for (int u = 0; u < kUnroll; ++u) {
+        const int kx = kb + u * blockDim.x;
+        y0[u].x = y0[u].y = y1[u].x = y1[u].y = T(0);
+        if (kx >= g.H) continue;
+        const int t = kx >> g.cshift, c = kx & (g.C - 1);
+        const long long tb = ((long long)t * g.nlines + line0) * g.C + c;
+        if (has0) y0[u] = a.S[(tb + (long long)ll0 * g.C) * M + m0];
+        if (has1) y1[u] = a.S[(tb + (long long)ll1 * g.C) * M + m1];
       }
-      if (g1 < nch) {
-        const int ll = g1 / M, m = g1 - ll * M;
-        const int line = line0 + ll;
-        if (line < g.nlines) y1[u] = a.S[(((long long)t * g.nlines + line) * g.C + c) * M + m];
-      }
-    }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int idx = base + u * blockDim.x;
-      if (idx >= nitems) continue;
-      const int t = idx / per_t;
-      const int rem = idx - t * per_t;
-      const int s = rem / g.C, c = rem - s * g.C;
-      const int kx = t * g.C + c;
-      if (kx >= g.H) continue;
-      C* seq = sm + (size_t)s * n;
-      if (kx == 0) {
-        C w;
-        w.x = y0[u].x;
-        w.y = y1[u].x;
-        seq[0] = w;
-      } else {
-        C w, wm;
-        w.x = y0[u].x - y1[u].y;
-        w.y = y0[u].y + y1[u].x;
-        wm.x = y0[u].x + y1[u].y;
-        wm.y = y1[u].x - y0[u].y;
-        seq[kx] = w;
-        seq[n - kx] = wm;
+      for (int u = 0; u < kUnroll; ++u) {
+        const int kx = kb + u * blockDim.x;
+        if (kx >= g.H) continue;
+        if (kx == 0) {
+          C w;
+          w.x = y0[u].x;
+          w.y = y1[u].x;
+          seq[0] = w;
+        } else {
+          C w, wm;
+          w.x = y0[u].x - y1[u].y;
+          w.y = y0[u].y + y1[u].x;
+          wm.x = y0[u].x + y1[u].y;
+          wm.y = y1[u].x - y0[u].y;
+          seq[kx] = w;
+          seq[n - kx] = wm;
+        }
       }
     }
   }
@@ -593,14 +624,14 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_inv(RowArgs<T> a) {
   T Ec[NL][D];
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
-    lact[l] = !kDot || a.scal == nullptr || a.scal[l].done == kRunning;
+    lact[l] = !kDot || sc == nullptr || sc[l].done == kRunning;
     pin[l] = a.in[l];
     pout[l] = a.out[l];
     paux[l] = a.aux[l];
     prhs[l] = a.rhs[l];
 #pragma unroll
     for (int c = 0; c < D; ++c)
-      Ec[l][c] = (a.scal != nullptr && (EPI == kEpiFixed || EPI == kEpiResid)) ? T(a.scal[l].E[c]) : T(0);
+      Ec[l][c] = (sc != nullptr && (EPI == kEpiFixed || EPI == kEpiResid)) ? T(sc[l].E[c]) : T(0);
   }
   constexpr bool kReadIn = true;
   constexpr bool kReadAux = (EPI == kEpiDirShadow);
@@ -692,6 +723,10 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_inv(RowArgs<T> a) {
 struct VecArgsBase {
   long long len;   // elements per load vector (d * |N|)
   int nloads;
+  int ncell;       // cells in the batch (blocks are split evenly between cells)
+  int d;
+  long long nodes;       // nodes per component plane (all cells)
+  long long cell_nodes;  // nodes per cell
 };
 
 template <typename T> struct VecArgs {
@@ -719,62 +754,131 @@ template <> struct Vec16<double> {
 template <typename V, typename T>
 __device__ __forceinline__ T& vlane(V& v, int k) { return reinterpret_cast<T*>(&v)[k]; }
 
-// CG: x += alpha p; r -= alpha A p; partial (r, r).  16-byte vector accesses
-// over the aligned prefix (cudaMalloc'd vectors), a scalar tail.
+// Range helpers for the vector updates: [b, e) processed by thread t of
+// `stride` threads, 16-byte vectors on the aligned interior, scalar head/tail.
+template <typename T, typename F>
+__device__ __forceinline__ void for_range(long long b, long long e, long long t, long long stride, F&& f) {
+  constexpr int W = Vec16<T>::n;
+  long long hb = (b + W - 1) / W * W;  // first aligned index
+  if (hb > e) hb = e;
+  for (long long i = b + t; i < hb; i += stride) f.scalar(i);
+  const long long nv = (e - hb) / W;
+  for (long long k = t; k < nv; k += 2 * stride) {
+    f.vec2(hb / W + k, k + stride < nv ? hb / W + k + stride : -1);
+  }
+  for (long long i = hb + nv * W + t; i < e; i += stride) f.scalar(i);
+}
+
+template <typename T>
+struct CgUpd {
+  using V = typename Vec16<T>::type;
+  static constexpr int W = Vec16<T>::n;
+  T* __restrict__ x;
+  T* __restrict__ r;
+  const T* __restrict__ p;
+  const T* __restrict__ ap;
+  T al;
+  DotAcc<T>* dot;
+  __device__ __forceinline__ void scalar(long long i) {
+    x[i] += al * p[i];
+    const T rn = r[i] - al * ap[i];
+    r[i] = rn;
+    dot->add(rn * rn);
+  }
+  __device__ __forceinline__ void vec2(long long k0, long long k1) {
+    V xv[2], rv[2], pv[2], av[2];
+    const long long kk[2] = {k0, k1};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (kk[u] < 0) continue;
+      xv[u] = reinterpret_cast<const V*>(x)[kk[u]];
+      rv[u] = reinterpret_cast<const V*>(r)[kk[u]];
+      pv[u] = __ldg(reinterpret_cast<const V*>(p) + kk[u]);
+      av[u] = __ldg(reinterpret_cast<const V*>(ap) + kk[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (kk[u] < 0) continue;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        vlane<V, T>(xv[u], w) += al * vlane<V, T>(pv[u], w);
+        const T rn = vlane<V, T>(rv[u], w) - al * vlane<V, T>(av[u], w);
+        vlane<V, T>(rv[u], w) = rn;
+        dot->add(rn * rn);
+      }
+      reinterpret_cast<V*>(x)[kk[u]] = xv[u];
+      reinterpret_cast<V*>(r)[kk[u]] = rv[u];
+    }
+  }
+};
+
+template <typename T>
+struct BicgUpd {
+  T* __restrict__ x;
+  T* __restrict__ r;
+  T* __restrict__ rs;
+  const T* __restrict__ p;
+  const T* __restrict__ ap;
+  const T* __restrict__ atps;
+  T al;
+  DotAcc<T>* d1;
+  DotAcc<T>* d2;
+  __device__ __forceinline__ void scalar(long long i) {
+    x[i] += al * p[i];
+    const T rn = r[i] - al * ap[i];
+    const T sn = rs[i] - al * atps[i];
+    r[i] = rn;
+    rs[i] = sn;
+    d1->add(rn * sn);
+    d2->add(rn * rn);
+  }
+  __device__ __forceinline__ void vec2(long long k0, long long k1) {
+    constexpr int W = Vec16<T>::n;
+    scalar_block(k0 * W, W);
+    if (k1 >= 0) scalar_block(k1 * W, W);
+  }
+  __device__ __forceinline__ void scalar_block(long long i0, int w) {
+    for (int k = 0; k < w; ++k) scalar(i0 + k);
+  }
+};
+
+// Block b of the launch belongs to cell b / (gridDim / ncell); a cell's data
+// is one contiguous range per component plane (the whole vector when there is
+// a single cell).  Partials: slot l of block b.
+template <typename T, int NL, typename Mk>
+__device__ __forceinline__ void cell_ranges(const VecArgs<T>& a, Mk&& mk) {
+  const int ncell = a.b.ncell;
+  const int bpc = gridDim.x / ncell;
+  const int cell = blockIdx.x / bpc;
+  const long long t = (long long)(blockIdx.x - cell * bpc) * blockDim.x + threadIdx.x;
+  const long long stride = (long long)bpc * blockDim.x;
+  if (ncell == 1) {
+    mk(0, a.b.len, t, stride, cell);
+  } else {
+    for (int c = 0; c < a.b.d; ++c) {
+      const long long b0 = c * a.b.nodes + cell * a.b.cell_nodes;
+      mk(b0, b0 + a.b.cell_nodes, t, stride, cell);
+    }
+  }
+}
+
+// CG: x += alpha p; r -= alpha A p; partial (r, r)
 template <typename T, int NL>
 __global__ void k_cg_update(VecArgs<T> a) {
-  if (all_done(a.scal, NL)) return;
-  using V = typename Vec16<T>::type;
-  constexpr int W = Vec16<T>::n;
+  const int bpc = gridDim.x / a.b.ncell;
+  const int cell = blockIdx.x / bpc;
+  Scal* const sc = a.scal + cell * NL;
+  if (all_done(sc, NL)) return;
   double acc[NL];
-  const long long nvec = a.b.len / W;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
     acc[l] = 0.0;
-    if (a.scal[l].done != kRunning) continue;
-    const T al = T(a.scal[l].alpha);
-    T* __restrict__ x = a.x[l];
-    T* __restrict__ r = a.r[l];
-    const T* __restrict__ p = a.p[l];
-    const T* __restrict__ ap = a.ap[l];
+    if (sc[l].done != kRunning) continue;
     DotAcc<T> dot;
-    for (long long i = tid; i < nvec; i += 2 * stride) {
-      V xv[2], rv[2], pv[2], av[2];
-      const bool has2 = i + stride < nvec;
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        if (u == 0 || has2) {
-          const long long k = i + u * stride;
-          xv[u] = reinterpret_cast<const V*>(x)[k];
-          rv[u] = reinterpret_cast<const V*>(r)[k];
-          pv[u] = __ldg(reinterpret_cast<const V*>(p) + k);
-          av[u] = __ldg(reinterpret_cast<const V*>(ap) + k);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        if (u == 0 || has2) {
-          const long long k = i + u * stride;
-#pragma unroll
-          for (int w = 0; w < W; ++w) {
-            vlane<V, T>(xv[u], w) += al * vlane<V, T>(pv[u], w);
-            const T rn = vlane<V, T>(rv[u], w) - al * vlane<V, T>(av[u], w);
-            vlane<V, T>(rv[u], w) = rn;
-            dot.add(rn * rn);
-          }
-          reinterpret_cast<V*>(x)[k] = xv[u];
-          reinterpret_cast<V*>(r)[k] = rv[u];
-        }
-      }
-    }
-    for (long long i = nvec * W + tid; i < a.b.len; i += stride) {
-      x[i] += al * p[i];
-      const T rn = r[i] - al * ap[i];
-      r[i] = rn;
-      dot.add(rn * rn);
-    }
+    CgUpd<T> f{a.x[l], a.r[l], a.p[l], a.ap[l], T(sc[l].alpha), &dot};
+    cell_ranges<T, NL>(a, [&](long long b0, long long e0, long long t, long long stride, int) {
+      for_range<T>(b0, e0, t, stride, f);
+    });
     acc[l] = dot.get();
   }
   block_reduce_store<NL>(acc, NL, a.part, gridDim.x, blockIdx.x);
@@ -784,31 +888,21 @@ __global__ void k_cg_update(VecArgs<T> a) {
 // partial layout: (r, r*) of load l at slot l, (r, r) at slot kMaxLoads + l.
 template <typename T, int NL>
 __global__ void k_bicg_update(VecArgs<T> a) {
-  if (all_done(a.scal, NL)) return;
+  const int bpc = gridDim.x / a.b.ncell;
+  const int cell = blockIdx.x / bpc;
+  Scal* const sc = a.scal + cell * NL;
+  if (all_done(sc, NL)) return;
   double acc[2 * kMaxLoads];
 #pragma unroll
   for (int i = 0; i < 2 * kMaxLoads; ++i) acc[i] = 0.0;
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
-    if (a.scal[l].done != kRunning) continue;
-    const T al = T(a.scal[l].alpha);
-    T* x = a.x[l];
-    T* r = a.r[l];
-    T* rs = a.rs[l];
-    const T* p = a.p[l];
-    const T* ap = a.ap[l];
-    const T* atps = a.atps[l];
+    if (sc[l].done != kRunning) continue;
     DotAcc<T> d1, d2;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.b.len;
-         i += (long long)gridDim.x * blockDim.x) {
-      x[i] += al * p[i];
-      const T rn = r[i] - al * ap[i];
-      const T sn = rs[i] - al * atps[i];
-      r[i] = rn;
-      rs[i] = sn;
-      d1.add(rn * sn);
-      d2.add(rn * rn);
-    }
+    BicgUpd<T> f{a.x[l], a.r[l], a.rs[l], a.p[l], a.ap[l], a.atps[l], T(sc[l].alpha), &d1, &d2};
+    cell_ranges<T, NL>(a, [&](long long b0, long long e0, long long t, long long stride, int) {
+      for (long long i = b0 + t; i < e0; i += stride) f.scalar(i);
+    });
     acc[l] = d1.get();
     acc[kMaxLoads + l] = d2.get();
   }
@@ -818,19 +912,34 @@ __global__ void k_bicg_update(VecArgs<T> a) {
 // ----------------------------------------------------------------------------
 // scalar control kernels: one CTA of kRedThreads threads
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ double reduce_parts(const double* part, int np) {
-  __shared__ double red[kRedThreads];
+// One warp per item (cell, load): the item's partials are the bpc = np / ncell
+// consecutive slots of its cell in row l of the partial array.
+__device__ __forceinline__ double warp_sum(const double* p, int n) {
+  const int lane = threadIdx.x & 31;
   double x = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) x += part[i];
-  red[threadIdx.x] = x;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
+  for (int i = lane; i < n; i += 32) x += p[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return __shfl_sync(0xffffffffu, x, 0);
+}
+
+struct ItemRef {
+  int item, cell, l, bpc;
+  bool valid;
+};
+
+__device__ __forceinline__ ItemRef item_ref(int np, int ncell, int nl) {
+  ItemRef r;
+  r.item = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  r.valid = r.item < ncell * nl;
+  r.cell = r.item / nl;
+  r.l = r.item - r.cell * nl;
+  r.bpc = np / ncell;
   return r;
+}
+
+__device__ __forceinline__ const double* item_part(const double* part, int row, int np, const ItemRef& r) {
+  return part + (long long)row * np + (long long)r.cell * r.bpc;
 }
 
 __device__ __forceinline__ bool finite_d(double x) { return x == x && x - x == 0.0; }
@@ -841,105 +950,106 @@ __device__ __forceinline__ void record_hist(Scal& s) {
 
 // After the initial residual (kEpiResid partials or a copied rhs):
 // rr = sum, rel = sqrt(rr / b2), beta = 0, iter = 0.
-static __global__ void k_scal_start(Scal* scal, const double* part, int np, int nloads, int bicg) {
-  for (int l = 0; l < nloads; ++l) {
-    const double rr = reduce_parts(part + (long long)l * np, np);
-    if (threadIdx.x == 0) {
-      Scal& s = scal[l];
-      s.rr = rr;
-      s.rho = rr;  // r0* = r0
-      s.beta = 0.0;
-      s.alpha = 0.0;
-      s.iter = 0;
-      s.rel = sqrt(rr / s.b2);
-      s.rel_true = s.rel;
-      record_hist(s);
-      if (!finite_d(rr)) s.done = kBreakdown;
-      else if (rr <= s.tol2 * s.b2) s.done = kConverged;
-      else if (s.max_iter <= 0) s.done = kCap;
-      else s.done = kRunning;
-    }
+static __global__ void k_scal_start(Scal* scal, const double* part, int np, int ncell, int nl) {
+  const ItemRef r = item_ref(np, ncell, nl);
+  if (!r.valid) return;
+  const double rr = warp_sum(item_part(part, r.l, np, r), r.bpc);
+  if ((threadIdx.x & 31) == 0) {
+    Scal& s = scal[r.item];
+    s.rr = rr;
+    s.rho = rr;  // r0* = r0
+    s.beta = 0.0;
+    s.alpha = 0.0;
+    s.iter = 0;
+    s.rel = sqrt(rr / s.b2);
+    s.rel_true = s.rel;
+    s.best_rel = s.rel;
+    s.best_iter = 0;
+    record_hist(s);
+    if (!finite_d(rr)) s.done = kBreakdown;
+    else if (rr <= s.tol2 * s.b2) s.done = kConverged;
+    else if (s.max_iter <= 0) s.done = kCap;
+    else s.done = kRunning;
   }
-  (void)bicg;
 }
 
 // alpha = (r, r) / (A p, p) for CG; alpha = (r, r*) / (A p, p*) for BiCG
-static __global__ void k_scal_alpha(Scal* scal, const double* part, int np, int nloads, int bicg) {
-  for (int l = 0; l < nloads; ++l) {
-    const double den = reduce_parts(part + (long long)l * np, np);
-    if (threadIdx.x == 0) {
-      Scal& s = scal[l];
-      if (s.done != kRunning) continue;
-      s.den = den;
-      const double num = bicg ? s.rho : s.rr;
-      if (!finite_d(den) || (!bicg && den <= 0.0) || den == 0.0) {
-        s.done = kBreakdown;
-      } else {
-        s.alpha = num / den;
-      }
-    }
+static __global__ void k_scal_alpha(Scal* scal, const double* part, int np, int ncell, int nl, int bicg) {
+  const ItemRef r = item_ref(np, ncell, nl);
+  if (!r.valid) return;
+  const double den = warp_sum(item_part(part, r.l, np, r), r.bpc);
+  if ((threadIdx.x & 31) == 0) {
+    Scal& s = scal[r.item];
+    if (s.done != kRunning) return;
+    s.den = den;
+    const double num = bicg ? s.rho : s.rr;
+    if (!finite_d(den) || (!bicg && den <= 0.0) || den == 0.0) s.done = kBreakdown;
+    else s.alpha = num / den;
   }
 }
 
 // CG: beta = (r+, r+) / (r, r); convergence on the recursive residual.
 // BiCG: beta = (r+, r*+) / (r, r*); convergence on (r+, r+).
-static __global__ void k_scal_beta(Scal* scal, const double* part, int np, int nloads, int bicg) {
-  for (int l = 0; l < nloads; ++l) {
-    double rho_new = 0.0, rr_new;
+static __global__ void k_scal_beta(Scal* scal, const double* part, int np, int ncell, int nl, int bicg) {
+  const ItemRef r = item_ref(np, ncell, nl);
+  if (!r.valid) return;
+  double rho_new = 0.0, rr_new;
+  if (bicg) {
+    rho_new = warp_sum(item_part(part, r.l, np, r), r.bpc);
+    rr_new = warp_sum(item_part(part, kMaxLoads + r.l, np, r), r.bpc);
+  } else {
+    rr_new = warp_sum(item_part(part, r.l, np, r), r.bpc);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    Scal& s = scal[r.item];
+    if (s.done != kRunning) return;
+    s.iter += 1;
+    s.rel = sqrt(rr_new / s.b2);
+    record_hist(s);
+    if (!finite_d(rr_new)) { s.done = kBreakdown; return; }
+    if (rr_new <= s.tol2 * s.b2) { s.rr = rr_new; s.done = kConverged; return; }
+    if (s.iter >= s.max_iter) { s.rr = rr_new; s.done = kCap; return; }
+    if (stalled(s)) { s.rr = rr_new; s.done = kStalled; return; }
     if (bicg) {
-      rho_new = reduce_parts(part + (long long)l * np, np);
-      rr_new = reduce_parts(part + (long long)(kMaxLoads + l) * np, np);
+      if (!finite_d(rho_new) || rho_new == 0.0) { s.done = kBreakdown; return; }
+      s.beta = rho_new / s.rho;
+      s.rho = rho_new;
+      s.rr = rr_new;
     } else {
-      rr_new = reduce_parts(part + (long long)l * np, np);
-    }
-    if (threadIdx.x == 0) {
-      Scal& s = scal[l];
-      if (s.done != kRunning) continue;
-      s.iter += 1;
-      s.rel = sqrt(rr_new / s.b2);
-      record_hist(s);
-      if (!finite_d(rr_new)) { s.done = kBreakdown; continue; }
-      if (rr_new <= s.tol2 * s.b2) { s.rr = rr_new; s.done = kConverged; continue; }
-      if (s.iter >= s.max_iter) { s.rr = rr_new; s.done = kCap; continue; }
-      if (bicg) {
-        if (!finite_d(rho_new) || rho_new == 0.0) { s.done = kBreakdown; continue; }
-        s.beta = rho_new / s.rho;
-        s.rho = rho_new;
-        s.rr = rr_new;
-      } else {
-        s.beta = rr_new / s.rr;
-        s.rr = rr_new;
-      }
+      s.beta = rr_new / s.rr;
+      s.rr = rr_new;
     }
   }
 }
 
 // Fixed point: the epilogue produced ||e_new - e||^2 = ||r(e)||^2.
-static __global__ void k_scal_fixed(Scal* scal, const double* part, int np, int nloads) {
-  for (int l = 0; l < nloads; ++l) {
-    const double rr = reduce_parts(part + (long long)l * np, np);
-    if (threadIdx.x == 0) {
-      Scal& s = scal[l];
-      if (s.done != kRunning) continue;
-      s.rr = rr;
-      s.rel = sqrt(rr / s.b2);
-      record_hist(s);
-      if (!finite_d(rr)) { s.done = kBreakdown; continue; }
-      s.iter += 1;
-      if (rr <= s.tol2 * s.b2) { s.done = kConverged; continue; }
-      if (s.iter >= s.max_iter) { s.done = kCap; continue; }
-    }
+static __global__ void k_scal_fixed(Scal* scal, const double* part, int np, int ncell, int nl) {
+  const ItemRef r = item_ref(np, ncell, nl);
+  if (!r.valid) return;
+  const double rr = warp_sum(item_part(part, r.l, np, r), r.bpc);
+  if ((threadIdx.x & 31) == 0) {
+    Scal& s = scal[r.item];
+    if (s.done != kRunning) return;
+    s.rr = rr;
+    s.rel = sqrt(rr / s.b2);
+    record_hist(s);
+    if (!finite_d(rr)) { s.done = kBreakdown; return; }
+    s.iter += 1;
+    if (rr <= s.tol2 * s.b2) { s.done = kConverged; return; }
+    if (s.iter >= s.max_iter) { s.done = kCap; return; }
+    if (stalled(s)) { s.done = kStalled; return; }
   }
 }
 
-// Reduce one partial array into out[l] (plain sum per load); used for the
-// true residual, norms, the effective tensor and the equilibrium norm.
-static __global__ void k_reduce_to(const double* part, int np, int nv, double* out) {
-  for (int v = 0; v < nv; ++v) {
-    const double x = reduce_parts(part + (long long)v * np, np);
-    if (threadIdx.x == 0) out[v] = x;
-  }
+// out[cell * nv + v] = sum of row v of the partials over the cell's slots.
+static __global__ void k_reduce_items(const double* part, int np, int ncell, int nv, double* out) {
+  const ItemRef r = item_ref(np, ncell, nv);
+  if (!r.valid) return;
+  const double x = warp_sum(item_part(part, r.l, np, r), r.bpc);
+  if ((threadIdx.x & 31) == 0) out[r.item] = x;
 }
+
+inline int item_blocks(int items) { return (items * 32 + kRedThreads - 1) / kRedThreads; }
 
 // ----------------------------------------------------------------------------
 // misc elementwise kernels
@@ -954,44 +1064,55 @@ __global__ void k_fill_const(T* x, long long nodes, int d, double E0, double E1,
     x[i] = T(E[i / nodes]);
 }
 
-// partial sums of (Tab[phase] e)_c over nodes, c < D (effective tensor column)
+// Per-cell partial sums of (Tab[phase] e)_c over the cell's nodes (effective
+// tensor column); blocks are split evenly between cells, slot c of block b.
 template <typename T, int D>
 __global__ void k_current_sum(const T* e, const uint8_t* phase, const double* tab, long long nodes,
-                              double* part) {
+                              int ncell, long long cell_nodes, int tab_stride, double* part) {
+  const int bpc = gridDim.x / ncell;
+  const int cell = blockIdx.x / bpc;
+  const long long t = (long long)(blockIdx.x - cell * bpc) * blockDim.x + threadIdx.x;
+  const long long stride = (long long)bpc * blockDim.x;
+  const double* tb = tab + (size_t)cell * tab_stride;
   double acc[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) acc[c] = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int ph = phase[i];
+  const long long base = (long long)cell * cell_nodes;
+  for (long long i = t; i < cell_nodes; i += stride) {
+    const int ph = phase[base + i];
     double v[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) v[c] = (double)e[c * nodes + i];
+    for (int c = 0; c < D; ++c) v[c] = (double)e[c * nodes + base + i];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       double s = 0.0;
 #pragma unroll
-      for (int b2 = 0; b2 < D; ++b2) s += tab[(ph * D + c) * D + b2] * v[b2];
+      for (int b2 = 0; b2 < D; ++b2) s += tb[(ph * D + c) * D + b2] * v[b2];
       acc[c] += s;
     }
   }
   block_reduce_store<D>(acc, D, part, gridDim.x, blockIdx.x);
 }
 
-// partial sums of |M e|^2 with a constant D x D matrix (norms, eta_r numerator)
+// Per-cell partial sums of |M e|^2 with a constant D x D matrix (norms, eta_r numerator)
 template <typename T, int D>
-__global__ void k_matnorm2(const T* e, long long nodes, Mat3 m, double* part) {
+__global__ void k_matnorm2(const T* e, long long nodes, int ncell, long long cell_nodes, Mat3 m,
+                           double* part) {
+  const int bpc = gridDim.x / ncell;
+  const int cell = blockIdx.x / bpc;
+  const long long t = (long long)(blockIdx.x - cell * bpc) * blockDim.x + threadIdx.x;
+  const long long stride = (long long)bpc * blockDim.x;
   T Mx[D * D];
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) Mx[i * D + j] = T(m.v[i * 3 + j]);
   DotAcc<T> dot;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long base = (long long)cell * cell_nodes;
+  for (long long i = t; i < cell_nodes; i += stride) {
     T v[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) v[c] = e[c * nodes + i];
+    for (int c = 0; c < D; ++c) v[c] = e[c * nodes + base + i];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       T s = T(0);

@@ -22,10 +22,11 @@ struct LaunchTable {
   cudaError_t (*col)(int mode, const Launch&, const ColArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*cg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*bicg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
-  cudaError_t (*current_sum)(const Launch&, const T*, const uint8_t*, const double*, long long,
-                             double*, cudaStream_t) = nullptr;
-  cudaError_t (*matnorm2)(const Launch&, const T*, long long, const Mat3&, double*,
-                          cudaStream_t) = nullptr;
+  cudaError_t (*current_sum)(const Launch&, const T*, const uint8_t*, const double*, long long nodes,
+                             int ncell, long long cell_nodes, int tab_stride, double*,
+                             cudaStream_t) = nullptr;
+  cudaError_t (*matnorm2)(const Launch&, const T*, long long nodes, int ncell, long long cell_nodes,
+                          const Mat3&, double*, cudaStream_t) = nullptr;
 };
 
 // Supported (D, NL): (2, 1), (2, 2), (3, 1), (3, 3).

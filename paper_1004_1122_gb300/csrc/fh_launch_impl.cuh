@@ -89,13 +89,14 @@ struct Launchers {
     return cudaGetLastError();
   }
   static cudaError_t current_sum(const Launch& L, const T* e, const uint8_t* ph, const double* tab,
-                                 long long nodes, double* part, cudaStream_t st) {
-    k_current_sum<T, D><<<L.grid, L.block, 0, st>>>(e, ph, tab, nodes, part);
+                                 long long nodes, int ncell, long long cell_nodes, int tab_stride,
+                                 double* part, cudaStream_t st) {
+    k_current_sum<T, D><<<L.grid, L.block, 0, st>>>(e, ph, tab, nodes, ncell, cell_nodes, tab_stride, part);
     return cudaGetLastError();
   }
-  static cudaError_t matnorm2(const Launch& L, const T* e, long long nodes, const Mat3& m,
-                              double* part, cudaStream_t st) {
-    k_matnorm2<T, D><<<L.grid, L.block, 0, st>>>(e, nodes, m, part);
+  static cudaError_t matnorm2(const Launch& L, const T* e, long long nodes, int ncell,
+                              long long cell_nodes, const Mat3& m, double* part, cudaStream_t st) {
+    k_matnorm2<T, D><<<L.grid, L.block, 0, st>>>(e, nodes, ncell, cell_nodes, m, part);
     return cudaGetLastError();
   }
   static LaunchTable<T> table() {

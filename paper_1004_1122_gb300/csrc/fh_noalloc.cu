@@ -185,6 +185,12 @@ extern "C" fh_status fh_apply_noalloc(int d, const int* N, const double* Y, cons
   if (C == 0) { set_err(errbuf, errlen, "no column tiling fits"); return FH_ERR_UNSUPPORTED; }
   g.C = C;
   g.Tt = (g.H + C - 1) / C;
+  g.cshift = 0;
+  while ((1 << g.cshift) < C) ++g.cshift;
+  g.ncell = 1;
+  g.lines_cell = g.nlines;
+  g.cell_nodes = nodes;
+  g.tab_stride = 256 * d * d;
   const size_t spec_bytes = (size_t)g.Tt * C * g.nlines * M * esz;
   if (spec_bytes > kScratchBytes) {
     char msg[200];

@@ -21,12 +21,14 @@ struct Problem {
   int d = 2;
   int N[3] = {1, 1, 1};
   double Y[3] = {1.0, 1.0, 1.0};
-  long long nodes = 0;
+  long long nodes = 0;      // all cells together (ncell * prod N)
   int nphase = 0;
-  std::vector<double> L;    // nphase * d * d
-  std::vector<double> L0;   // d * d
-  std::vector<double> dL;   // nphase * d * d, L - L0
-  const uint8_t* d_phase = nullptr;  // device, owned by the context
+  int ncell = 1;            // same-size cells solved together (2-D batches)
+  std::vector<double> L;    // [ncell][nphase][d][d]
+  std::vector<double> L0;   // d * d (common reference medium)
+  std::vector<double> L0cell;  // [ncell][3][3] per-cell reference media, or empty
+  std::vector<double> dL;   // [ncell][nphase][d][d], L - L0 of the cell
+  const uint8_t* d_phase = nullptr;  // device [ncell][N...], owned by the caller of init
 };
 
 // Krylov methods (mirror fh_method)
@@ -73,6 +75,7 @@ struct Pipeline {
   C* tw1 = nullptr;
   C* S = nullptr;
   T* dtab = nullptr;   // dL per phase
+  T* qtab = nullptr;   // L0 for every phase: the passes then apply Q = Gamma0 L0
   T* ltab = nullptr;   // L per phase
   double* ltab64 = nullptr;
   const uint8_t* phase = nullptr;
@@ -85,6 +88,9 @@ struct Pipeline {
   double* d_red = nullptr;
   int part_stride = 0;       // max grid over all partial producers
   int nloads = 1;
+  int ncell = 1;
+  int items = 1;             // ncell * nloads
+  double* L0cell_dev = nullptr;
   long long vlen = 0;        // d * nodes
   T* x[kMaxLoads] = {};
   T* r[kMaxLoads] = {};
@@ -129,8 +135,24 @@ struct Pipeline {
   // ---- Krylov solve ------------------------------------------------------
   // Solves A x = rhs for every load.  rhs is the constant E[l] when
   // rhs_field is false, else the field in this->rhs[l].  x0 per kX0*.
+  // tol_item (optional, [ncell * nloads]) overrides tol per (cell, load).
+  // stall_window > 0 ends an item as kStalled once its recursive residual has
+  // not halved for that many iterations.
   int solve(int method, const double (*E)[kMaxD], bool rhs_field, int x0, const T* const* x_init,
-            double tol, int max_iter, SolveResult* res, std::string& err);
+            double tol, int max_iter, SolveResult* res, std::string& err,
+            const double* tol_item = nullptr, int stall_window = 0);
+  // The same solve in pieces, for drivers that run several pipelines at once:
+  // solve_begin (asynchronous set-up), then repeatedly solve_step (one graph
+  // chunk + async copy of the scalars), a stream synchronisation and
+  // solve_done; finally solve_results.
+  int solve_begin(int method, const double (*E)[kMaxD], bool rhs_field, int x0,
+                  const T* const* x_init, double tol, int max_iter, std::string& err,
+                  const double* tol_item = nullptr, int stall_window = 0);
+  int solve_step(std::string& err);
+  bool solve_done() const;
+  void solve_results(SolveResult* res) const;
+  int run_method_ = 0, run_K_ = 8;
+  long long run_guard_ = 0, run_guard_max_ = 0;
   cudaError_t enqueue_iter(int method);
   cudaError_t enqueue_chunk(int method, int K);
   int chunk_size(int method) const;
@@ -145,6 +167,11 @@ struct Pipeline {
   int current_mean(const T* e, double* col, std::string& err);
   int eta_e(const T* e, double* eta, std::string& err);
   int matnorm2(const T* e, const double* M, double* out, std::string& err);
+  // out_l = (I - Q) r_l with Q = F^-1 Gamma0 F L0 (asynchronous).  Q projects
+  // onto the compatible (gradient) fields along the complement on which
+  // I + B is the identity, so for A d = r the complement part of d is exactly
+  // (I - Q) r; starting a Krylov solve there leaves its residual compatible.
+  int project_complement(T* const* r, T* const* out, std::string& err);
 
   // ---- measurement --------------------------------------------------------
   // Average device time (ms, CUDA events on the pipeline stream) of `reps`

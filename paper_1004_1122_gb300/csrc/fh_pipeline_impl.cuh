@@ -64,11 +64,21 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   g.n1 = d == 3 ? pb.N[1] : 1;
   g.M = d * nloads;
   g.nloads = nloads;
+  ncell = pb.ncell < 1 ? 1 : pb.ncell;
+  items = ncell * nloads;
+  if (ncell > 1 && d != 2) {
+    err = "batches of cells are 2-D only";
+    return 1;
+  }
+  g.ncell = ncell;
+  g.cell_nodes = pb.nodes / ncell;
+  g.lines_cell = (int)(g.cell_nodes / pb.N[d - 1]);
+  g.tab_stride = pb.nphase * d * d;
   for (int a = 0; a < 3; ++a) g.invY[a] = a < d ? 1.0 / pb.Y[a] : 0.0;
   for (int i = 0; i < 9; ++i) g.L0[i] = 0.0;
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) g.L0[i * 3 + j] = pb.L0[i * d + j];
-  g.inv_nodes = 1.0 / (double)pb.nodes;
+  g.inv_nodes = 1.0 / (double)g.cell_nodes;
   vlen = (long long)d * pb.nodes;
   phase = pb.d_phase;
   nphase = pb.nphase;
@@ -113,6 +123,8 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   }
   g.C = Cc;
   g.Tt = (g.H + Cc - 1) / Cc;
+  g.cshift = 0;
+  while ((1 << g.cshift) < Cc) ++g.cshift;
   const long long CM = (long long)Cc * M;
 
   // row passes
@@ -124,6 +136,7 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     while (l > 1 && ((size_t)((l * M + 1) / 2) * g.nlast * esz > 96 * 1024)) --l;
     if ((l * M) % 2 && l > 1) --l;
     if (w.lpc) l = w.lpc;
+    while (ncell > 1 && l > 1 && g.lines_cell % l) --l;
     lpc = l;
     nseq = (lpc * M + 1) / 2;
     while (lpc > 1 && round_up(((lpc * M + 1) / 2) * tpl, 32) > kRowMaxThreads) --lpc;
@@ -131,7 +144,8 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     row.block = round_up(nseq * tpl, 32);
     row.grid = (g.nlines + lpc - 1) / lpc;
     row.smem = (size_t)nseq * g.nlast * esz + (size_t)std::max(1, nphase) * d * d * sizeof(T);
-    if (row.block > kRowMaxThreads || row.smem > (size_t)optin || (w.lpc && lpc != w.lpc)) {
+    if (row.block > kRowMaxThreads || row.smem > (size_t)optin || (w.lpc && lpc != w.lpc) ||
+        (ncell > 1 && g.lines_cell % lpc)) {
       err = "row pass does not fit one CTA";
       return 9;
     }
@@ -157,8 +171,8 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     cb0.base_outer = (long long)g.nlines * CM;
     if (d == 2) {
       cb0.stride_i = CM;
-      cb0.nb_inner = 1;
-      cb0.base_inner = 0;
+      cb0.nb_inner = ncell;
+      cb0.base_inner = (long long)g.lines_cell * CM;
     } else {
       cb0.stride_i = (long long)g.n1 * CM;
       cb0.nb_inner = (g.n1 + G - 1) / G;
@@ -189,7 +203,12 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   tuning.tpc0 = tpc0;
   tuning.tpc1 = tpc1;
   vec.block = 256;
-  vec.grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 4, (vlen + 255) / 256));
+  {
+    const long long cell_len = (long long)d * g.cell_nodes;
+    const long long want = std::max<long long>(1, ((long long)sms * 4 + ncell - 1) / ncell);
+    const long long bpc = std::max<long long>(1, std::min<long long>(want, (cell_len + 255) / 256));
+    vec.grid = (int)(bpc * ncell);
+  }
   part_stride = std::max(std::max(row.grid, col0.grid), vec.grid);
 
   FH_CKS(lt.set_smem(row.smem, col0.smem, d == 3 ? col1.smem : 0));
@@ -215,26 +234,45 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   if ((rc = upload_tw(pb.N[0], &tw0))) return rc;
   if (d == 3 && (rc = upload_tw(pb.N[1], &tw1))) return rc;
   {
-    const int nt = std::max(1, nphase) * d * d;
+    const int nt = std::max(1, nphase) * d * d * ncell;
     std::vector<T> hd(nt), hl(nt);
-    for (int i = 0; i < nphase * d * d; ++i) {
+    for (int i = 0; i < nphase * d * d * ncell; ++i) {
       hd[i] = T(pb.dL[i]);
       hl[i] = T(pb.L[i]);
     }
     if ((rc = dev_alloc(allocs, &dtab, nt, err))) return rc;
+    {
+      std::vector<T> hq(nt);
+      for (int c = 0; c < ncell; ++c)
+        for (int ph = 0; ph < std::max(1, nphase); ++ph)
+          for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+              const double v = pb.L0cell.empty() ? pb.L0[i * d + j] : pb.L0cell[9 * c + i * 3 + j];
+              hq[((size_t)c * std::max(1, nphase) + ph) * d * d + i * d + j] = T(v);
+            }
+      if ((rc = dev_alloc(allocs, &qtab, nt, err))) return rc;
+      FH_CKS(cudaMemcpy(qtab, hq.data(), nt * sizeof(T), cudaMemcpyHostToDevice));
+    }
     if ((rc = dev_alloc(allocs, &ltab, nt, err))) return rc;
     if ((rc = dev_alloc(allocs, &ltab64, nt, err))) return rc;
     FH_CKS(cudaMemcpy(dtab, hd.data(), nt * sizeof(T), cudaMemcpyHostToDevice));
     FH_CKS(cudaMemcpy(ltab, hl.data(), nt * sizeof(T), cudaMemcpyHostToDevice));
-    FH_CKS(cudaMemcpy(ltab64, pb.L.data(), nphase * d * d * sizeof(double), cudaMemcpyHostToDevice));
+    FH_CKS(cudaMemcpy(ltab64, pb.L.data(), (size_t)nphase * d * d * ncell * sizeof(double),
+                      cudaMemcpyHostToDevice));
   }
-  if ((rc = dev_alloc(allocs, &scal, kMaxLoads, err))) return rc;
-  if ((rc = dev_alloc(allocs, &scal_aux, kMaxLoads, err))) return rc;
+  const int nscal = std::max(items, kMaxLoads);
+  const int nred = std::max(std::max(items, ncell * d), 16);
+  if ((rc = dev_alloc(allocs, &scal, nscal, err))) return rc;
+  if ((rc = dev_alloc(allocs, &scal_aux, nscal, err))) return rc;
   if ((rc = dev_alloc(allocs, &part, (size_t)2 * kMaxLoads * part_stride, err))) return rc;
-  if ((rc = dev_alloc(allocs, &d_red, 16, err))) return rc;
-  FH_CKS(cudaMallocHost(&h_scal, 2 * kMaxLoads * sizeof(Scal)));
-  FH_CKS(cudaMallocHost(&h_red, 16 * sizeof(double)));
-  std::memset(h_scal, 0, 2 * kMaxLoads * sizeof(Scal));
+  if ((rc = dev_alloc(allocs, &d_red, nred, err))) return rc;
+  FH_CKS(cudaMallocHost(&h_scal, 2 * nscal * sizeof(Scal)));
+  FH_CKS(cudaMallocHost(&h_red, nred * sizeof(double)));
+  std::memset(h_scal, 0, 2 * nscal * sizeof(Scal));
+  if (!pb.L0cell.empty()) {
+    if ((rc = dev_alloc(allocs, &L0cell_dev, (size_t)9 * ncell, err))) return rc;
+    FH_CKS(cudaMemcpy(L0cell_dev, pb.L0cell.data(), 9 * ncell * sizeof(double), cudaMemcpyHostToDevice));
+  }
   if (krylov) {
     for (int l = 0; l < nloads; ++l) {
       if ((rc = dev_alloc(allocs, &x[l], vlen, err))) return rc;
@@ -297,12 +335,14 @@ cudaError_t Pipeline<T>::launch_green(int mode, Scal* sc, double* pt) {
   m.S = S;
   m.scal = sc;
   m.part = pt;
+  m.L0cell = L0cell_dev;
   ColArgs<T> a;
   a.b = cb0;
   a.tw = tw0;
   a.S = S;
   a.scal = sc;
   a.part = pt;
+  a.L0cell = L0cell_dev;
   if (g.d == 3) {
     ++launches;
     FH_CK(lt.col(kColFwd, col1, m, st));
@@ -359,12 +399,16 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
     }
     FH_CK(passes(kProDir, kEpiDir, f, i, scal));
     ++launches;
-    k_scal_alpha<<<1, kRedThreads, 0, st>>>(scal, part, row.grid, nloads, 0);
+    k_scal_alpha<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, row.grid, ncell, nloads, 0);
     FH_CK(cudaGetLastError());
     VecArgs<T> v;
     std::memset(&v, 0, sizeof(v));
     v.b.len = vlen;
     v.b.nloads = nloads;
+    v.b.ncell = ncell;
+    v.b.d = g.d;
+    v.b.nodes = g.nodes;
+    v.b.cell_nodes = g.cell_nodes;
     for (int l = 0; l < nloads; ++l) {
       v.x[l] = x[l];
       v.r[l] = r[l];
@@ -376,7 +420,7 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
     ++launches;
     FH_CK(lt.cg_update(vec, v, st));
     ++launches;
-    k_scal_beta<<<1, kRedThreads, 0, st>>>(scal, part, vec.grid, nloads, 0);
+    k_scal_beta<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, vec.grid, ncell, nloads, 0);
     return cudaGetLastError();
   }
   if (method == kBiCG) {
@@ -396,12 +440,16 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
     FH_CK(passes(kProDirPlain, kEpiApplyT, ft, it, scal));
     FH_CK(passes(kProDir, kEpiDirShadow, f, i, scal));
     ++launches;
-    k_scal_alpha<<<1, kRedThreads, 0, st>>>(scal, part, row.grid, nloads, 1);
+    k_scal_alpha<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, row.grid, ncell, nloads, 1);
     FH_CK(cudaGetLastError());
     VecArgs<T> v;
     std::memset(&v, 0, sizeof(v));
     v.b.len = vlen;
     v.b.nloads = nloads;
+    v.b.ncell = ncell;
+    v.b.d = g.d;
+    v.b.nodes = g.nodes;
+    v.b.cell_nodes = g.cell_nodes;
     for (int l = 0; l < nloads; ++l) {
       v.x[l] = x[l];
       v.r[l] = r[l];
@@ -415,7 +463,7 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
     ++launches;
     FH_CK(lt.bicg_update(vec, v, st));
     ++launches;
-    k_scal_beta<<<1, kRedThreads, 0, st>>>(scal, part, vec.grid, nloads, 1);
+    k_scal_beta<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, vec.grid, ncell, nloads, 1);
     return cudaGetLastError();
   }
   // fixed point: e <- rhs - B e
@@ -428,7 +476,7 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
   }
   FH_CK(passes(kProApply, kEpiFixed, f, i, scal));
   ++launches;
-  k_scal_fixed<<<1, kRedThreads, 0, st>>>(scal, part, row.grid, nloads);
+  k_scal_fixed<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, row.grid, ncell, nloads);
   return cudaGetLastError();
 }
 
@@ -460,13 +508,16 @@ cudaError_t Pipeline<T>::enqueue_chunk(int method, int K) {
 template <typename T>
 int Pipeline<T>::norm2(T* const* v, double* out, std::string& err) {
   const Mat3 I = {{1, 0, 0, 0, 1, 0, 0, 0, 1}};
-  for (int l = 0; l < nloads; ++l) { ++launches; FH_CKS(lt.matnorm2(vec, v[l], g.nodes, I, part + (long long)l * vec.grid, st)); }
+  for (int l = 0; l < nloads; ++l) {
+    ++launches;
+    FH_CKS(lt.matnorm2(vec, v[l], g.nodes, ncell, g.cell_nodes, I, part + (long long)l * vec.grid, st));
+  }
   ++launches;
-  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, vec.grid, nloads, d_red);
+  k_reduce_items<<<item_blocks(items), kRedThreads, 0, st>>>(part, vec.grid, ncell, nloads, d_red);
   FH_CKS(cudaGetLastError());
-  FH_CKS(cudaMemcpyAsync(h_red, d_red, nloads * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FH_CKS(cudaMemcpyAsync(h_red, d_red, items * sizeof(double), cudaMemcpyDeviceToHost, st));
   FH_CKS(cudaStreamSynchronize(st));
-  for (int l = 0; l < nloads; ++l) out[l] = h_red[l];
+  for (int i = 0; i < items; ++i) out[i] = h_red[i];
   return 0;
 }
 
@@ -475,27 +526,29 @@ int Pipeline<T>::matnorm2(const T* e, const double* Mx, double* out, std::string
   Mat3 m;
   for (int i = 0; i < 9; ++i) m.v[i] = Mx[i];
   ++launches;
-  FH_CKS(lt.matnorm2(vec, e, g.nodes, m, part, st));
+  FH_CKS(lt.matnorm2(vec, e, g.nodes, ncell, g.cell_nodes, m, part, st));
   ++launches;
-  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, vec.grid, 1, d_red);
+  k_reduce_items<<<item_blocks(ncell), kRedThreads, 0, st>>>(part, vec.grid, ncell, 1, d_red);
   FH_CKS(cudaGetLastError());
-  FH_CKS(cudaMemcpyAsync(h_red, d_red, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FH_CKS(cudaMemcpyAsync(h_red, d_red, ncell * sizeof(double), cudaMemcpyDeviceToHost, st));
   FH_CKS(cudaStreamSynchronize(st));
-  *out = h_red[0];
+  for (int i = 0; i < ncell; ++i) out[i] = h_red[i];
   return 0;
 }
 
 template <typename T>
 int Pipeline<T>::residual(const T* const* xin, T* const* rout, bool rhs_field,
                           const double (*E)[kMaxD], double* out, std::string& err) {
-  for (int l = 0; l < nloads; ++l) {
-    Scal& s = h_scal[kMaxLoads + l];
+  const int nscal = std::max(items, kMaxLoads);
+  for (int it = 0; it < items; ++it) {
+    const int l = it % nloads;
+    Scal& s = h_scal[nscal + it];
     std::memset(&s, 0, sizeof(Scal));
     s.done = kRunning;
     s.b2 = 1.0;
     for (int c = 0; c < kMaxD; ++c) s.E[c] = c < g.d ? E[l][c] : 0.0;
   }
-  FH_CKS(cudaMemcpyAsync(scal_aux, h_scal + kMaxLoads, nloads * sizeof(Scal), cudaMemcpyHostToDevice, st));
+  FH_CKS(cudaMemcpyAsync(scal_aux, h_scal + nscal, items * sizeof(Scal), cudaMemcpyHostToDevice, st));
   RowArgs<T> a = row_args();
   a.scal = scal_aux;
   for (int l = 0; l < nloads; ++l) {
@@ -505,31 +558,54 @@ int Pipeline<T>::residual(const T* const* xin, T* const* rout, bool rhs_field,
   }
   FH_CKS(passes(kProApply, kEpiResid, a, a, scal_aux));
   ++launches;
-  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, row.grid, nloads, d_red);
+  k_reduce_items<<<item_blocks(items), kRedThreads, 0, st>>>(part, row.grid, ncell, nloads, d_red);
   FH_CKS(cudaGetLastError());
-  FH_CKS(cudaMemcpyAsync(h_red, d_red, nloads * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FH_CKS(cudaMemcpyAsync(h_red, d_red, items * sizeof(double), cudaMemcpyDeviceToHost, st));
   FH_CKS(cudaStreamSynchronize(st));
-  for (int l = 0; l < nloads; ++l) out[l] = h_red[l];
+  for (int i = 0; i < items; ++i) out[i] = h_red[i];
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::project_complement(T* const* r, T* const* out, std::string& err) {
+  const int nscal = std::max(items, kMaxLoads);
+  for (int it = 0; it < items; ++it) {
+    Scal& s = h_scal[nscal + it];
+    std::memset(&s, 0, sizeof(Scal));
+    s.done = kRunning;
+    s.b2 = 1.0;
+  }
+  FH_CKS(cudaMemcpyAsync(scal_aux, h_scal + nscal, items * sizeof(Scal), cudaMemcpyHostToDevice, st));
+  RowArgs<T> a = row_args();
+  a.tab = qtab;
+  a.scal = scal_aux;
+  for (int l = 0; l < nloads; ++l) {
+    a.in[l] = r[l];
+    a.out[l] = out[l];
+    a.rhs[l] = r[l];
+  }
+  // y = Q r;  out = r - y  (the fixed-point epilogue with right-hand side r)
+  FH_CKS(passes(kProApply, kEpiFixed, a, a, scal_aux));
   return 0;
 }
 
 template <typename T>
 int Pipeline<T>::current_mean(const T* e, double* col, std::string& err) {
   ++launches;
-  FH_CKS(lt.current_sum(vec, e, phase, ltab64, g.nodes, part, st));
+  FH_CKS(lt.current_sum(vec, e, phase, ltab64, g.nodes, ncell, g.cell_nodes, g.tab_stride, part, st));
   ++launches;
-  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, vec.grid, g.d, d_red);
+  k_reduce_items<<<item_blocks(ncell * g.d), kRedThreads, 0, st>>>(part, vec.grid, ncell, g.d, d_red);
   FH_CKS(cudaGetLastError());
-  FH_CKS(cudaMemcpyAsync(h_red, d_red, g.d * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FH_CKS(cudaMemcpyAsync(h_red, d_red, ncell * g.d * sizeof(double), cudaMemcpyDeviceToHost, st));
   FH_CKS(cudaStreamSynchronize(st));
-  for (int c = 0; c < g.d; ++c) col[c] = h_red[c] / (double)g.nodes;
+  for (int c = 0; c < ncell * g.d; ++c) col[c] = h_red[c] / (double)g.cell_nodes;
   return 0;
 }
 
 template <typename T>
 int Pipeline<T>::eta_e(const T* e, double* eta, std::string& err) {
-  if (nloads != 1) {
-    err = "eta_e needs a single-load pipeline";
+  if (nloads != 1 || ncell != 1) {
+    err = "eta_e needs a single-load, single-cell pipeline";
     return 1;
   }
   RowArgs<T> a = row_args();
@@ -538,7 +614,7 @@ int Pipeline<T>::eta_e(const T* e, double* eta, std::string& err) {
   FH_CKS(launch_row_fwd(kProApply, a));
   FH_CKS(launch_green(kColEta, nullptr, part));
   ++launches;
-  k_reduce_to<<<1, kRedThreads, 0, st>>>(part, col0.grid, 2, d_red);
+  k_reduce_items<<<item_blocks(2), kRedThreads, 0, st>>>(part, col0.grid, 1, 2, d_red);
   FH_CKS(cudaGetLastError());
   FH_CKS(cudaMemcpyAsync(h_red, d_red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   FH_CKS(cudaStreamSynchronize(st));
@@ -549,7 +625,51 @@ int Pipeline<T>::eta_e(const T* e, double* eta, std::string& err) {
 template <typename T>
 int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int x0,
                        const T* const* x_init, double tol, int max_iter, SolveResult* res,
-                       std::string& err) {
+                       std::string& err, const double* tol_item, int stall_window) {
+  int rc = solve_begin(method, E, rhs_field, x0, x_init, tol, max_iter, err, tol_item, stall_window);
+  if (rc) return rc;
+  while (true) {
+    rc = solve_step(err);
+    if (rc) return rc;
+    FH_CKS(cudaStreamSynchronize(st));
+    if (solve_done()) break;
+    if (++run_guard_ > run_guard_max_) {
+      err = "iteration guard exceeded without a device status";
+      return 8;  // FH_ERR_TIMEOUT
+    }
+  }
+  solve_results(res);
+  return 0;
+}
+
+template <typename T>
+int Pipeline<T>::solve_step(std::string& err) {
+  FH_CKS(enqueue_chunk(run_method_, run_K_));
+  FH_CKS(cudaMemcpyAsync(h_scal, scal, items * sizeof(Scal), cudaMemcpyDeviceToHost, st));
+  return 0;
+}
+
+template <typename T>
+bool Pipeline<T>::solve_done() const {
+  for (int it = 0; it < items; ++it)
+    if (h_scal[it].done == kRunning) return false;
+  return true;
+}
+
+template <typename T>
+void Pipeline<T>::solve_results(SolveResult* res) const {
+  for (int it = 0; it < items; ++it) {
+    res[it].status = h_scal[it].done;
+    res[it].iters = h_scal[it].iter;
+    res[it].rel = h_scal[it].rel;
+    res[it].alpha = h_scal[it].alpha;
+  }
+}
+
+template <typename T>
+int Pipeline<T>::solve_begin(int method, const double (*E)[kMaxD], bool rhs_field, int x0,
+                             const T* const* x_init, double tol, int max_iter, std::string& err,
+                             const double* tol_item, int stall_window) {
   int rc;
   if (method == kBiCG && rs[0] == nullptr) {
     for (int l = 0; l < nloads; ++l) {
@@ -559,28 +679,32 @@ int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int
     }
   }
   rhs_active_ = rhs_field;
-  double b2[kMaxLoads];
+  std::vector<double> b2(items);
   if (rhs_field) {
-    if ((rc = norm2(rhs, b2, err))) return rc;
+    if ((rc = norm2(rhs, b2.data(), err))) return rc;
   } else {
-    for (int l = 0; l < nloads; ++l) {
+    for (int it = 0; it < items; ++it) {
+      const int l = it % nloads;
       double e2 = 0.0;
       for (int c = 0; c < g.d; ++c) e2 += E[l][c] * E[l][c];
-      b2[l] = e2 * (double)g.nodes;
+      b2[it] = e2 * (double)g.cell_nodes;
     }
   }
-  for (int l = 0; l < nloads; ++l) {
-    Scal& s = h_scal[l];
+  for (int it = 0; it < items; ++it) {
+    const int l = it % nloads;
+    Scal& s = h_scal[it];
     std::memset(&s, 0, sizeof(Scal));
-    s.b2 = b2[l] > 0.0 ? b2[l] : 1.0;
-    s.tol2 = tol * tol;
+    s.b2 = b2[it] > 0.0 ? b2[it] : 1.0;
+    const double tl = tol_item ? tol_item[it] : tol;
+    s.tol2 = tl * tl;
     s.max_iter = max_iter;
     s.done = kRunning;
-    s.hist = hist;
-    s.hist_cap = hist_cap;
+    s.stall_window = stall_window;
+    s.hist = items == 1 ? hist : nullptr;
+    s.hist_cap = items == 1 ? hist_cap : 0;
     for (int c = 0; c < kMaxD; ++c) s.E[c] = (!rhs_field && c < g.d) ? E[l][c] : 0.0;
   }
-  FH_CKS(cudaMemcpyAsync(scal, h_scal, nloads * sizeof(Scal), cudaMemcpyHostToDevice, st));
+  FH_CKS(cudaMemcpyAsync(scal, h_scal, items * sizeof(Scal), cudaMemcpyHostToDevice, st));
   const size_t vbytes = (size_t)vlen * sizeof(T);
   for (int l = 0; l < nloads; ++l) {
     switch (x0) {
@@ -609,10 +733,10 @@ int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int
       for (int l = 0; l < nloads; ++l) {
         FH_CKS(cudaMemcpyAsync(r[l], rhs[l], vbytes, cudaMemcpyDeviceToDevice, st));
         ++launches;
-        FH_CKS(lt.matnorm2(vec, r[l], g.nodes, I, part + (long long)l * vec.grid, st));
+        FH_CKS(lt.matnorm2(vec, r[l], g.nodes, ncell, g.cell_nodes, I, part + (long long)l * vec.grid, st));
       }
       ++launches;
-      k_scal_start<<<1, kRedThreads, 0, st>>>(scal, part, vec.grid, nloads, method == kBiCG);
+      k_scal_start<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, vec.grid, ncell, nloads);
     } else {
       RowArgs<T> a = row_args();
       a.scal = scal;
@@ -623,7 +747,7 @@ int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int
       }
       FH_CKS(passes(kProApply, kEpiResid, a, a, scal));
       ++launches;
-      k_scal_start<<<1, kRedThreads, 0, st>>>(scal, part, row.grid, nloads, method == kBiCG);
+      k_scal_start<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, row.grid, ncell, nloads);
     }
     FH_CKS(cudaGetLastError());
     for (int l = 0; l < nloads; ++l) {
@@ -634,27 +758,10 @@ int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int
       }
     }
   }
-  const int K = chunk_size(method);
-  long long guard = 0;
-  const long long guard_max = (long long)max_iter / K + 4;
-  while (true) {
-    FH_CKS(enqueue_chunk(method, K));
-    FH_CKS(cudaMemcpyAsync(h_scal, scal, nloads * sizeof(Scal), cudaMemcpyDeviceToHost, st));
-    FH_CKS(cudaStreamSynchronize(st));
-    bool all = true;
-    for (int l = 0; l < nloads; ++l) all = all && h_scal[l].done != kRunning;
-    if (all) break;
-    if (++guard > guard_max) {
-      err = "iteration guard exceeded without a device status";
-      return 8;  // FH_ERR_TIMEOUT
-    }
-  }
-  for (int l = 0; l < nloads; ++l) {
-    res[l].status = h_scal[l].done;
-    res[l].iters = h_scal[l].iter;
-    res[l].rel = h_scal[l].rel;
-    res[l].alpha = h_scal[l].alpha;
-  }
+  run_method_ = method;
+  run_K_ = chunk_size(method);
+  run_guard_ = 0;
+  run_guard_max_ = (long long)max_iter / run_K_ + 4;
   return 0;
 }
 
@@ -738,8 +845,8 @@ int Pipeline<T>::profile(int what, int reps, double* ms, std::string& err) {
     err = "profiling needs a context with Krylov buffers";
     return 1;
   }
-  for (int l = 0; l < nloads; ++l) {
-    Scal& s = h_scal[l];
+  for (int it = 0; it < items; ++it) {
+    Scal& s = h_scal[it];
     std::memset(&s, 0, sizeof(Scal));
     s.done = kRunning;
     s.alpha = 1e-3;
@@ -747,7 +854,7 @@ int Pipeline<T>::profile(int what, int reps, double* ms, std::string& err) {
     s.b2 = 1.0;
     s.max_iter = 1 << 30;
   }
-  FH_CKS(cudaMemcpyAsync(scal, h_scal, nloads * sizeof(Scal), cudaMemcpyHostToDevice, st));
+  FH_CKS(cudaMemcpyAsync(scal, h_scal, items * sizeof(Scal), cudaMemcpyHostToDevice, st));
   const size_t vbytes = (size_t)vlen * sizeof(T);
   for (int l = 0; l < nloads; ++l) {
     FH_CKS(cudaMemsetAsync(x[l], 0, vbytes, st));
@@ -771,6 +878,10 @@ int Pipeline<T>::profile(int what, int reps, double* ms, std::string& err) {
   std::memset(&v, 0, sizeof(v));
   v.b.len = vlen;
   v.b.nloads = nloads;
+  v.b.ncell = ncell;
+  v.b.d = g.d;
+  v.b.nodes = g.nodes;
+  v.b.cell_nodes = g.cell_nodes;
   for (int l = 0; l < nloads; ++l) {
     v.x[l] = x[l];
     v.r[l] = r[l];

@@ -33,7 +33,8 @@ DT_FP64, DT_FP32 = 0, 1
 # Names declared in include/fh.h (checked by the ABI test).
 EXPORTS = (
     "fh_create", "fh_set_phase", "fh_apply", "fh_solve", "fh_solve_all", "fh_effective_column",
-    "fh_eta_e", "fh_profile", "fh_autotune", "fh_apply_noalloc", "fh_destroy", "fh_status_string", "fh_last_error",
+    "fh_eta_e", "fh_profile", "fh_autotune", "fh_apply_noalloc", "fh_batch_create", "fh_batch_solve",
+    "fh_batch_last_error", "fh_batch_destroy", "fh_destroy", "fh_status_string", "fh_last_error",
     "fh_version",
 )
 
@@ -92,6 +93,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fh_eta_e.restype = I
     lib.fh_profile.argtypes = [P, I, I, I, pD]
     lib.fh_profile.restype = I
+    lib.fh_batch_create.argtypes = [ctypes.POINTER(P), I, pI, ctypes.POINTER(ctypes.c_void_p), pI,
+                                    ctypes.POINTER(ctypes.c_void_p), I, I]
+    lib.fh_batch_create.restype = I
+    lib.fh_batch_solve.argtypes = [P, pD, D, I, I, pD, pI, pI, ctypes.POINTER(FhInfo)]
+    lib.fh_batch_solve.restype = I
+    lib.fh_batch_last_error.argtypes = [P]
+    lib.fh_batch_last_error.restype = ctypes.c_char_p
+    lib.fh_batch_destroy.argtypes = [P]
+    lib.fh_batch_destroy.restype = V
     lib.fh_autotune.argtypes = [P, I, pD, pD]
     lib.fh_autotune.restype = I
     lib.fh_apply_noalloc.argtypes = [I, pI, pD, P, I, pD, pD, P, P, I, P, ctypes.c_char_p, ctypes.c_size_t]
@@ -277,6 +287,64 @@ class Solver:
         v = np.zeros(1)
         self._check(self.lib.fh_eta_e(self.ctx, ctypes.c_void_p(e.data_ptr()), _dptr(v)), "fh_eta_e")
         return float(v[0])
+
+
+class Batch:
+    """Independent 2-D cells of (possibly) different sizes solved together
+    (fh_batch_create / fh_batch_solve / fh_batch_destroy).
+
+    phases   list of uint8 images (each 2-D, odd sizes)
+    tables   list of per-phase tensor tables, each (nphase, 2, 2)
+    """
+
+    def __init__(self, phases, tables, nloads: int = 2, precision: str = "fp32_refined"):
+        self.lib = load_library()
+        self.n = len(phases)
+        self.nloads = nloads
+        self._ph = [np.ascontiguousarray(p, dtype=np.uint8) for p in phases]
+        self._L = [np.ascontiguousarray(t, dtype=np.float64) for t in tables]
+        N = np.array([s for p in self._ph for s in p.shape], dtype=np.int32)
+        nph = np.array([t.shape[0] for t in self._L], dtype=np.int32)
+        php = (ctypes.c_void_p * self.n)(*[p.ctypes.data for p in self._ph])
+        Lp = (ctypes.c_void_p * self.n)(*[t.ctypes.data for t in self._L])
+        b = ctypes.c_void_p()
+        rc = self.lib.fh_batch_create(ctypes.byref(b), self.n, N.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      php, nph.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), Lp, nloads,
+                                      PRECISIONS[precision])
+        if rc != FH_OK:
+            raise FhError(rc, "fh_batch_create failed")
+        self.b = b
+
+    def solve(self, E, tol: float = 1e-6, method: str = "cg", max_iter: int = 20000):
+        """Returns (Leff [ncells, 2, nloads], status [ncells, nloads], iters, summary)."""
+        Eh = np.ascontiguousarray(E, dtype=np.float64).reshape(-1)
+        Leff = np.zeros((self.n, 2, self.nloads))
+        st = np.zeros((self.n, self.nloads), dtype=np.int32)
+        it = np.zeros((self.n, self.nloads), dtype=np.int32)
+        info = FhInfo()
+        rc = self.lib.fh_batch_solve(self.b, _dptr(Eh), float(tol), METHODS[method], int(max_iter), _dptr(Leff),
+                                     st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(info))
+        if rc not in (FH_OK, 6, 7):
+            raise FhError(rc, self.lib.fh_batch_last_error(self.b).decode())
+        return Leff, st, it, _info_dict(info, None)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.fh_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def version() -> str:

@@ -25,6 +25,11 @@ CASES_2D = [
     ((375, 9), (1.0, 1.0)),        # 3 5^3
     ((243, 729), (1.0, 1.0)),      # several tiles and a ragged tail
     ((7, 49), (1.0, 1.0)),         # 7^2
+    ((15, 21), (1.0, 1.0)),        # single-stage radix-15 columns, one thread per FFT
+    ((21, 15), (1.0, 1.0)),
+    ((15, 15), (1.0, 1.0)),
+    ((25, 9), (1.0, 1.0)),
+    ((5, 7), (1.0, 1.0)),
 ]
 CASES_3D = [
     ((9, 15, 27), (1.0, 1.0, 1.0)),

@@ -219,3 +219,24 @@ def test_invalid_inputs_rejected():
         fh.Solver(np.zeros((9, 9), np.uint8), np.array([[[1.0, 2.0], [2.0, 1.0]]]))
     with pytest.raises(fh.FhError):
         fh.Solver(np.full((9, 9), 3, np.uint8), micro.isotropic_table([1.0, 2.0], 2))
+
+
+@pytest.mark.parametrize("N,axis", [((27, 27), 1), ((81, 45), 0), ((15, 21), None)])
+def test_fp32_refined_reaches_tight_tolerance_on_noise_dominated_corrections(N, axis):
+    """Once the float32 solution is accurate, the float64 residual is rounding
+    noise with a large component outside the compatible fields, where I + B is
+    not symmetric; the refinement starts each inner CG at the exact complement
+    part (I - Q) r of the correction so that CG only sees compatible fields."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = micro.laminate(N, [0.4, 0.6], axis=axis, seed=3) if axis is not None else micro.centred_disk(N, 0.3)
+    L = micro.isotropic_table([1.0, 55.0], 2)
+    L0 = oracle.reference_medium(L)
+    E = np.array([0.6, 0.8])
+    xo, _ = oracle.cg(phase, L, L0, E, tol=1e-13)
+    for method in ("cg", "bicg"):
+        with fh.Solver(phase, L, precision="fp32_refined") as s:
+            x, col, info = s.solve(E, tol=1e-10, method=method, max_iter=5000)
+        assert info["status"] == "FH_OK", (method, info)
+        assert _rel_l2(x.cpu().numpy(), xo) < 1e-6
