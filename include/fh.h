@@ -146,9 +146,13 @@ fh_status fh_apply(fh_ctx* ctx, const void* e_in, void* e_out, int transpose, in
 fh_status fh_solve(fh_ctx* ctx, const double* E, double tol, int method, int max_iter,
                    const double* e_init, double* e_out, double* Leff_col, fh_info* info);
 
-/* fh_solve_all -- d solves with E = e_1 ... e_d; Leff receives the full
- * d x d effective tensor, row-major (column b from load b).  infos: host
- * array of d fh_info, or NULL.  Returns the first non-OK status. */
+/* fh_solve_all -- the full d x d effective tensor: the d unit loads E = e_1
+ * ... e_d are solved together, each kernel launch carrying all d loads (for
+ * FH_FP64 and FH_FP32_REFINED contexts; an FH_FP32 context solves them one by
+ * one).  The first call allocates a second set of buffers sized for d loads,
+ * kept until fh_destroy.  Leff receives L_eff row-major (column b from load b).
+ * infos: host array of d fh_info (iters, outer_iters, status, rel_res_true,
+ * launches are filled), or NULL.  Returns the first non-OK status. */
 fh_status fh_solve_all(fh_ctx* ctx, double tol, int method, int max_iter,
                        double* Leff, fh_info* infos);
 

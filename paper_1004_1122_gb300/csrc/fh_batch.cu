@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/fh.h"
+#include "fh_groups.h"
 #include "fh_pipeline.cuh"
 
 using fh::Pipeline;
@@ -25,11 +26,13 @@ using fh::SolveResult;
 
 namespace {
 
-__global__ void kb_fill(double* x, long long nodes, int d, double e0, double e1) {
+__global__ void kb_fill(double* x, long long nodes, int d, double e0, double e1, double e2) {
   const long long len = nodes * d;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
-       i += (long long)gridDim.x * blockDim.x)
-    x[i] = i < nodes ? e0 : e1;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / nodes;
+    x[i] = c == 0 ? e0 : (c == 1 ? e1 : e2);
+  }
 }
 __global__ void kb_to_float(const double* in, float* out, long long len) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
@@ -55,6 +58,7 @@ struct Group {
   std::vector<int> cells;  // global cell ids, in batch order
   Problem pb;
   uint8_t* d_phase = nullptr;
+  bool own_phase = true;
   cudaStream_t st = nullptr;
   Pipeline<float>* p32 = nullptr;
   Pipeline<double>* p64 = nullptr;
@@ -106,7 +110,7 @@ void fh_batch_destroy(fh_batch* b) {
       if (g.x64[l]) cudaFree(g.x64[l]);
       if (g.r64[l]) cudaFree(g.r64[l]);
     }
-    if (g.d_phase) cudaFree(g.d_phase);
+    if (g.d_phase && g.own_phase) cudaFree(g.d_phase);
     if (g.st) cudaStreamDestroy(g.st);
   }
   delete b;
@@ -233,42 +237,38 @@ fh_status fh_batch_create(fh_batch** out, int ncells, const int* N, const uint8_
 
 const char* fh_batch_last_error(const fh_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
-fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, int max_iter,
-                         double* Leff, int* status, int* iters, fh_info* summary) {
-  if (!b || !E || !Leff || !(tol > 0.0) || max_iter < 0 || method < FH_CG || method > FH_FIXED_POINT)
-    return FH_ERR_ARG;
-  const int nl = b->nloads;
-  double Ev[fh::kMaxLoads][fh::kMaxD] = {};
+}  // extern "C"
+
+namespace {
+
+// Solve every (cell, load) of every group (any dimension; groups of several
+// cells are 2-D).  Ev[l] is load l.  Results per group gi, item = k * nl + l:
+// st (kConverged / kBreakdown / kCap), its (inner iterations), rel (float64
+// true relative residual); x64[l] of each group holds the solution fields.
+fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double (*Ev)[fh::kMaxD],
+                       double tol, int method, int max_iter, int precision,
+                       std::vector<std::vector<int>>& st, std::vector<std::vector<int>>& its,
+                       std::vector<std::vector<double>>& rel, int& outer, long long& own_launches,
+                       std::string& err) {
   double e2[fh::kMaxLoads] = {};
-  for (int l = 0; l < nl; ++l) {
-    Ev[l][0] = E[2 * l];
-    Ev[l][1] = E[2 * l + 1];
-    e2[l] = Ev[l][0] * Ev[l][0] + Ev[l][1] * Ev[l][1];
-    if (!std::isfinite(e2[l])) return FH_ERR_ARG;
-  }
-  std::string err;
-  auto fail = [&](int rc) {
-    b->err = err;
-    return (fh_status)rc;
-  };
-  const int ng = (int)b->groups.size();
-  long long launches0 = b->own_launches;
-  for (Group& g : b->groups)
-    launches0 += g.p64->launches + (g.p32 ? g.p32->launches : 0);
-  // per (group, item) bookkeeping, item = k * nl + l
-  std::vector<std::vector<int>> st(ng), its(ng);
-  std::vector<std::vector<double>> rel(ng);
+  for (int l = 0; l < nl; ++l)
+    for (int a = 0; a < d; ++a) e2[l] += Ev[l][a] * Ev[l][a];
+  auto fail = [&](int rc) { return (fh_status)rc; };
+  const int ng = (int)groups.size();
+  st.assign(ng, {});
+  its.assign(ng, {});
+  rel.assign(ng, {});
   for (int gi = 0; gi < ng; ++gi) {
-    const int items = (int)b->groups[gi].cells.size() * nl;
+    const int items = (int)(*groups[gi]).cells.size() * nl;
     st[gi].assign(items, fh::kRunning);
     its[gi].assign(items, 0);
     rel[gi].assign(items, INFINITY);
   }
-  int outer = 0;
-  double worst = 0.0;
+  outer = 0;
 
-  if (b->precision == FH_FP64) {
-    for (Group& g : b->groups) {
+  if (precision == FH_FP64) {
+    for (Group* gp : groups) {
+      Group& g = *gp;
       int rc = g.p64->solve_begin(method, Ev, false, fh::kX0Const, nullptr, tol, max_iter, err);
       if (rc) return fail(rc);
     }
@@ -277,21 +277,21 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
       bool all = true;
       for (int gi = 0; gi < ng; ++gi) {
         if (done[gi]) continue;
-        int rc = b->groups[gi].p64->solve_step(err);
+        int rc = (*groups[gi]).p64->solve_step(err);
         if (rc) return fail(rc);
       }
       for (int gi = 0; gi < ng; ++gi) {
         if (done[gi]) continue;
-        cudaError_t e = cudaStreamSynchronize(b->groups[gi].st);
+        cudaError_t e = cudaStreamSynchronize((*groups[gi]).st);
         if (e != cudaSuccess) return FH_ERR_CUDA;
-        done[gi] = b->groups[gi].p64->solve_done();
+        done[gi] = (*groups[gi]).p64->solve_done();
         all = all && done[gi];
       }
       if (all) break;
       if (round > (long long)max_iter + 64) return FH_ERR_TIMEOUT;
     }
     for (int gi = 0; gi < ng; ++gi) {
-      Group& g = b->groups[gi];
+      Group& g = *groups[gi];
       std::vector<SolveResult> res(g.cells.size() * nl);
       g.p64->solve_results(res.data());
       // true residual per item
@@ -304,7 +304,7 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
       }
       int rc = g.p64->residual(xin, rout, false, Ev, rr.data(), err);
       if (rc) return fail(rc);
-      const long long cn = (long long)g.N[0] * g.N[1];
+      const long long cn = g.pb.nodes / g.pb.ncell;
       for (size_t it = 0; it < res.size(); ++it) {
         const int l = (int)(it % nl);
         rel[gi][it] = std::sqrt(rr[it] / std::max(e2[l] * cn, 1e-300));
@@ -314,15 +314,16 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
                                                                               : fh::kCap;
       }
       for (int l = 0; l < nl; ++l)
-        cudaMemcpyAsync(g.x64[l], g.p64->x[l], 2 * g.pb.nodes * sizeof(double), cudaMemcpyDeviceToDevice,
+        cudaMemcpyAsync(g.x64[l], g.p64->x[l], (long long)d * g.pb.nodes * sizeof(double), cudaMemcpyDeviceToDevice,
                         g.st);
     }
   } else {
     // float32 inner solves, float64 outer residual per (cell, load)
-    for (Group& g : b->groups)
+    for (Group* gp : groups)
       for (int l = 0; l < nl; ++l) {
-        ++b->own_launches;
-        kb_fill<<<grid_for(2 * g.pb.nodes), 256, 0, g.st>>>(g.x64[l], g.pb.nodes, 2, Ev[l][0], Ev[l][1]);
+        Group& g = *gp;
+        ++own_launches;
+        kb_fill<<<grid_for((long long)d * g.pb.nodes), 256, 0, g.st>>>(g.x64[l], g.pb.nodes, d, Ev[l][0], Ev[l][1], Ev[l][2]);
       }
     std::vector<std::vector<double>> prev(ng);
     for (int gi = 0; gi < ng; ++gi) prev[gi].assign(st[gi].size(), INFINITY);
@@ -330,7 +331,7 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
       bool any = false;
       std::vector<std::vector<double>> eta(ng);
       for (int gi = 0; gi < ng; ++gi) {
-        Group& g = b->groups[gi];
+        Group& g = *groups[gi];
         std::vector<double> rr(st[gi].size());
         const double* xin[fh::kMaxLoads];
         double* rout[fh::kMaxLoads];
@@ -340,7 +341,7 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
         }
         int rc = g.p64->residual(xin, rout, false, Ev, rr.data(), err);
         if (rc) return fail(rc);
-        const long long cn = (long long)g.N[0] * g.N[1];
+        const long long cn = g.pb.nodes / g.pb.ncell;
         eta[gi].assign(st[gi].size(), 1.0);
         for (size_t it = 0; it < rr.size(); ++it) {
           const int l = (int)(it % nl);
@@ -369,14 +370,14 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
       // inner solves of every group, concurrently
       std::vector<bool> active(ng, false);
       for (int gi = 0; gi < ng; ++gi) {
-        Group& g = b->groups[gi];
+        Group& g = *groups[gi];
         bool need = false;
         for (size_t it = 0; it < st[gi].size(); ++it) need = need || st[gi][it] == fh::kRunning;
         if (!need) continue;
         active[gi] = true;
         for (int l = 0; l < nl; ++l) {
-          ++b->own_launches;
-          kb_to_float<<<grid_for(2 * g.pb.nodes), 256, 0, g.st>>>(g.r64[l], g.p32->rhs[l], 2 * g.pb.nodes);
+          ++own_launches;
+          kb_to_float<<<grid_for((long long)d * g.pb.nodes), 256, 0, g.st>>>(g.r64[l], g.p32->rhs[l], (long long)d * g.pb.nodes);
         }
         int x0 = fh::kX0Rhs;
         if (method != FH_FIXED_POINT) {
@@ -393,32 +394,66 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
         bool all = true;
         for (int gi = 0; gi < ng; ++gi) {
           if (!active[gi]) continue;
-          int rc = b->groups[gi].p32->solve_step(err);
+          int rc = (*groups[gi]).p32->solve_step(err);
           if (rc) return fail(rc);
         }
         for (int gi = 0; gi < ng; ++gi) {
           if (!active[gi]) continue;
-          if (cudaStreamSynchronize(b->groups[gi].st) != cudaSuccess) return FH_ERR_CUDA;
-          if (b->groups[gi].p32->solve_done()) active[gi] = false;
+          if (cudaStreamSynchronize((*groups[gi]).st) != cudaSuccess) return FH_ERR_CUDA;
+          if ((*groups[gi]).p32->solve_done()) active[gi] = false;
           all = all && !active[gi];
         }
         if (all) break;
         if (round > (long long)budget + 64) return FH_ERR_TIMEOUT;
       }
       for (int gi = 0; gi < ng; ++gi) {
-        Group& g = b->groups[gi];
+        Group& g = *groups[gi];
         std::vector<SolveResult> res(st[gi].size());
         g.p32->solve_results(res.data());
         for (size_t it = 0; it < res.size(); ++it)
           if (st[gi][it] == fh::kRunning) its[gi][it] += res[it].iters;
         for (int l = 0; l < nl; ++l) {
-          ++b->own_launches;
-          kb_add<<<grid_for(2 * g.pb.nodes), 256, 0, g.st>>>(g.x64[l], g.p32->x[l], 2 * g.pb.nodes);
+          ++own_launches;
+          kb_add<<<grid_for((long long)d * g.pb.nodes), 256, 0, g.st>>>(g.x64[l], g.p32->x[l], (long long)d * g.pb.nodes);
         }
       }
       ++outer;
     }
   }
+  return FH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, int max_iter,
+                         double* Leff, int* status, int* iters, fh_info* summary) {
+  if (!b || !E || !Leff || !(tol > 0.0) || max_iter < 0 || method < FH_CG || method > FH_FIXED_POINT)
+    return FH_ERR_ARG;
+  const int nl = b->nloads;
+  double Ev[fh::kMaxLoads][fh::kMaxD] = {};
+  for (int l = 0; l < nl; ++l) {
+    Ev[l][0] = E[2 * l];
+    Ev[l][1] = E[2 * l + 1];
+    if (!std::isfinite(Ev[l][0]) || !std::isfinite(Ev[l][1])) return FH_ERR_ARG;
+  }
+  std::vector<Group*> groups;
+  for (Group& g : b->groups) groups.push_back(&g);
+  const int ng = (int)groups.size();
+  long long launches0 = b->own_launches;
+  for (Group* g : groups) launches0 += g->p64->launches + (g->p32 ? g->p32->launches : 0);
+  std::vector<std::vector<int>> st, its;
+  std::vector<std::vector<double>> rel;
+  int outer = 0;
+  std::string err;
+  fh_status rs = solve_groups(groups, 2, nl, Ev, tol, method, max_iter, b->precision, st, its, rel, outer,
+                              b->own_launches, err);
+  if (rs != FH_OK) {
+    b->err = err;
+    return rs;
+  }
+  double worst = 0.0;
   // effective tensor columns per cell and load (float64)
   for (int gi = 0; gi < ng; ++gi) {
     Group& g = b->groups[gi];
@@ -426,7 +461,10 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
     std::vector<double> col((size_t)nc * 2);
     for (int l = 0; l < nl; ++l) {
       int rc = g.p64->current_mean(g.x64[l], col.data(), err);
-      if (rc) return fail(rc);
+      if (rc) {
+        b->err = err;
+        return (fh_status)rc;
+      }
       for (int k = 0; k < nc; ++k) {
         const int c = g.cells[k];
         for (int a = 0; a < 2; ++a) Leff[((size_t)c * 2 + a) * nl + l] = col[2 * k + a];
@@ -467,3 +505,84 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
 }
 
 }  // extern "C"
+
+namespace fh {
+
+void release_loads_group(void* cache) {
+  Group* g = static_cast<Group*>(cache);
+  if (!g) return;
+  if (g->st) cudaStreamSynchronize(g->st);
+  if (g->p32) {
+    g->p32->release();
+    delete g->p32;
+  }
+  if (g->p64) {
+    g->p64->release();
+    delete g->p64;
+  }
+  for (int l = 0; l < kMaxLoads; ++l) {
+    if (g->x64[l]) cudaFree(g->x64[l]);
+    if (g->r64[l]) cudaFree(g->r64[l]);
+  }
+  if (g->st) cudaStreamDestroy(g->st);
+  delete g;
+}
+
+int solve_all_loads(const Problem& pb, int precision, double tol, int method, int max_iter,
+                    double* Leff, LoadsResult& res, void** cache, std::string& err) {
+  const int d = pb.d;
+  Group* g = static_cast<Group*>(*cache);
+  if (!g) {
+    g = new (std::nothrow) Group();
+    if (!g) return FH_ERR_OOM;
+    g->pb = pb;
+    g->d_phase = const_cast<uint8_t*>(pb.d_phase);
+    g->own_phase = false;
+    g->cells = {0};
+    int rc = 0;
+    if (cudaStreamCreate(&g->st) != cudaSuccess) rc = FH_ERR_CUDA;
+    if (!rc) {
+      g->p64 = new (std::nothrow) Pipeline<double>();
+      rc = g->p64 ? g->p64->init(pb, d, precision == FH_FP64, g->st, err) : FH_ERR_OOM;
+    }
+    if (!rc && precision != FH_FP64) {
+      g->p32 = new (std::nothrow) Pipeline<float>();
+      rc = g->p32 ? g->p32->init(pb, d, true, g->st, err) : FH_ERR_OOM;
+    }
+    for (int l = 0; l < d && !rc; ++l)
+      if (cudaMalloc(&g->x64[l], (size_t)d * pb.nodes * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&g->r64[l], (size_t)d * pb.nodes * sizeof(double)) != cudaSuccess)
+        rc = FH_ERR_OOM;
+    if (rc) {
+      release_loads_group(g);
+      return rc;
+    }
+    *cache = g;
+  }
+  double Ev[kMaxLoads][kMaxD] = {};
+  for (int l = 0; l < d; ++l) Ev[l][l] = 1.0;
+  std::vector<Group*> groups = {g};
+  std::vector<std::vector<int>> st, its;
+  std::vector<std::vector<double>> rel;
+  long long own = 0;
+  const long long l0 = g->p64->launches + (g->p32 ? g->p32->launches : 0);
+  fh_status rs = solve_groups(groups, d, d, Ev, tol, method, max_iter,
+                              precision == FH_FP64 ? FH_FP64 : FH_FP32_REFINED, st, its, rel, res.outer,
+                              own, err);
+  if (rs != FH_OK) return rs;
+  std::vector<double> col(d);
+  for (int l = 0; l < d; ++l) {
+    int rc = g->p64->current_mean(g->x64[l], col.data(), err);
+    if (rc) return rc;
+    for (int a = 0; a < d; ++a) Leff[a * d + l] = col[a];
+    res.status[l] = st[0][l] == kConverged ? FH_OK : st[0][l] == kBreakdown ? FH_ERR_BREAKDOWN
+                                                                           : FH_ERR_NOT_CONVERGED;
+    res.iters[l] = its[0][l];
+    res.rel[l] = rel[0][l];
+  }
+  res.launches = own + g->p64->launches + (g->p32 ? g->p32->launches : 0) - l0;
+  if (cudaStreamSynchronize(g->st) != cudaSuccess) return FH_ERR_CUDA;
+  return 0;
+}
+
+}  // namespace fh

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/fh.h"
+#include "fh_groups.h"
 #include "fh_pipeline.cuh"
 
 using fh::Pipeline;
@@ -31,6 +32,7 @@ struct fh_ctx {
   double* d_x64 = nullptr;   // float64 solution (refinement iterate / output staging)
   double* d_r64 = nullptr;   // float64 residual
   long long own_launches = 0;  // kernels launched directly by this file
+  void* loads_group = nullptr; // persistent all-loads group of fh_solve_all
   std::string err;
 };
 
@@ -254,6 +256,7 @@ void fh_destroy(fh_ctx* c) {
     c->p64->release();
     delete c->p64;
   }
+  fh::release_loads_group(c->loads_group);
   if (c->d_phase) cudaFree(c->d_phase);
   if (c->d_x64) cudaFree(c->d_x64);
   if (c->d_r64) cudaFree(c->d_r64);
@@ -661,16 +664,44 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
 fh_status fh_solve_all(fh_ctx* c, double tol, int method, int max_iter, double* Leff,
                        fh_info* infos) {
   if (!c || !Leff) return FH_ERR_ARG;
+  if (!(tol > 0.0) || max_iter < 0) return fail(c, FH_ERR_ARG, "tol must be > 0, max_iter >= 0");
+  if (method < FH_CG || method > FH_FIXED_POINT) return fail(c, FH_ERR_ARG, "unknown method");
   const int d = c->pb.d;
+  if (c->precision == FH_FP32) {
+    // no float64 pipeline to check the loads against: solve them one by one
+    fh_status first = FH_OK;
+    for (int b = 0; b < d; ++b) {
+      double E[3] = {0, 0, 0};
+      E[b] = 1.0;
+      double col[3];
+      fh_status s = fh_solve(c, E, tol, method, max_iter, nullptr, nullptr, col, infos ? &infos[b] : nullptr);
+      if (s == FH_ERR_CUDA || s == FH_ERR_OOM || s == FH_ERR_ARG || s == FH_ERR_TIMEOUT) return s;
+      if (first == FH_OK && s != FH_OK) first = s;
+      for (int a = 0; a < d; ++a) Leff[a * d + b] = col[a];
+    }
+    return first;
+  }
+  // all d loads batched into every launch
+  fh::LoadsResult r;
+  std::string err;
+  int rc = fh::solve_all_loads(c->pb, c->precision, tol, method, max_iter, Leff, r, &c->loads_group, err);
+  if (rc) return fail(c, (fh_status)rc, err);
   fh_status first = FH_OK;
   for (int b = 0; b < d; ++b) {
-    double E[3] = {0, 0, 0};
-    E[b] = 1.0;
-    double col[3];
-    fh_status s = fh_solve(c, E, tol, method, max_iter, nullptr, nullptr, col, infos ? &infos[b] : nullptr);
-    if (s == FH_ERR_CUDA || s == FH_ERR_OOM || s == FH_ERR_ARG || s == FH_ERR_TIMEOUT) return s;
-    if (first == FH_OK && s != FH_OK) first = s;
-    for (int a = 0; a < d; ++a) Leff[a * d + b] = col[a];
+    if (first == FH_OK && r.status[b] != FH_OK) first = (fh_status)r.status[b];
+    if (infos) {
+      fh_info& inf = infos[b];
+      inf.iters = r.iters[b];
+      inf.outer_iters = r.outer;
+      inf.matvecs = 0;
+      inf.status = r.status[b];
+      inf.rel_res_true = r.rel[b];
+      inf.rel_res = NAN;
+      inf.eta_r = NAN;
+      inf.eta_e = NAN;
+      inf.history_len = 0;
+      inf.launches = r.launches;
+    }
   }
   return first;
 }

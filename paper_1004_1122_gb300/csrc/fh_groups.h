@@ -1,0 +1,28 @@
+// fh_groups.h -- internal entry into the concurrent group solver of
+// fh_batch.cu for one context's problem with all d unit loads batched into
+// every launch (the full effective tensor in one solve).
+#pragma once
+
+#include <string>
+
+#include "fh_pipeline.cuh"
+
+namespace fh {
+
+struct LoadsResult {
+  int status[kMaxLoads];   // fh_status per load
+  int iters[kMaxLoads];
+  double rel[kMaxLoads];   // float64 true relative residual per load
+  int outer = 0;
+  long long launches = 0;
+};
+
+// Solves (I + B) e = e_b for b = 1..d with the loads batched (NL = d).  The
+// first call allocates a persistent group (pipelines and float64 iterates)
+// stored in *cache; free it with release_loads_group.  Leff is row-major d x d,
+// column b from load b.  Returns 0 or an fh_status code (err set).
+int solve_all_loads(const Problem& pb, int precision, double tol, int method, int max_iter,
+                    double* Leff, LoadsResult& res, void** cache, std::string& err);
+void release_loads_group(void* cache);
+
+}  // namespace fh

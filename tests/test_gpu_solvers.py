@@ -240,3 +240,22 @@ def test_fp32_refined_reaches_tight_tolerance_on_noise_dominated_corrections(N, 
             x, col, info = s.solve(E, tol=1e-10, method=method, max_iter=5000)
         assert info["status"] == "FH_OK", (method, info)
         assert _rel_l2(x.cpu().numpy(), xo) < 1e-6
+
+
+@pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-10), ("fp32_refined", 1e-10, 1e-6)])
+def test_3d_full_tensor_loads_batched(prec, tol, bar):
+    """Config-3 path at a small size: all three unit loads in every launch
+    (fh_solve_all), Boolean spheres, against three oracle solves."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = micro.boolean_spheres(27, 3.0, 0.25, seed=micro.config_seed(3, 2))
+    L = micro.isotropic_table([1.0, 1e3], 3)
+    L0 = oracle.reference_medium(L)
+    xs = [oracle.cg(phase, L, L0, np.eye(3)[b], tol=1e-13, max_iter=3000)[0] for b in range(3)]
+    Lo = oracle.effective_tensor(xs, phase, L)
+    with fh.Solver(phase, L, precision=prec) as s:
+        Le, infos = s.solve_all(tol=tol, max_iter=20000)
+    assert all(i["status"] == "FH_OK" for i in infos), infos
+    assert np.max(np.abs(Le - Lo)) / np.max(np.abs(Lo)) < bar
+    assert np.max(np.abs(Le - Le.T)) < 10 * bar * np.max(np.abs(Lo))
