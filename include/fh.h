@@ -281,6 +281,15 @@ fh_status fh_apply_noalloc(int d, const int* N, const double* Y, const uint8_t* 
                            double* e_out, int transpose, void* stream, char* errbuf,
                            size_t errlen);
 
+/* fh_project_compatible -- out = Q in with Q = F^-1 Gamma0 F L0 (Section 2.1):
+ * the projection onto the compatible (curl-free, zero-mean) fields along the
+ * complement on which I + B acts as the identity.  A warm start x0 for the
+ * load E is admissible for CG when x0 - E is compatible; use
+ * x0 = E + Q (guess - E).  in, out: device float64 [d][N...] (in == out
+ * allowed).  Float64 pipeline (float32 for FH_FP32 contexts).  Asynchronous.
+ * Errors: FH_ERR_ARG, FH_ERR_CUDA. */
+fh_status fh_project_compatible(fh_ctx* ctx, const double* in, double* out);
+
 /* fh_destroy -- free the context and every buffer it owns.  NULL is a no-op. */
 void fh_destroy(fh_ctx* ctx);
 

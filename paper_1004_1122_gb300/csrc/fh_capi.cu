@@ -125,6 +125,11 @@ __global__ void k_to_float(const double* in, float* out, float* zero1, long long
     zero1[i] = 0.0f;
   }
 }
+__global__ void k_sub_from(const double* a, double* b, long long len) {  // b = a - b
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i] - b[i];
+}
 __global__ void k_add_float(double* x, const float* d, long long len) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
        i += (long long)gridDim.x * blockDim.x)
@@ -704,6 +709,40 @@ fh_status fh_solve_all(fh_ctx* c, double tol, int method, int max_iter, double* 
     }
   }
   return first;
+}
+
+fh_status fh_project_compatible(fh_ctx* c, const double* in, double* out) {
+  if (!c || !in || !out) return FH_ERR_ARG;
+  const long long len = (long long)c->pb.d * c->pb.nodes;
+  std::string err;
+  cudaError_t e;
+  if (c->p64) {
+    // scratch = (I - Q) in, then scratch = in - scratch = Q in, copied to out
+    double* rin[fh::kMaxLoads] = {const_cast<double*>(in)};
+    double* rout[fh::kMaxLoads] = {c->d_r64};
+    int rc = c->p64->project_complement(rin, rout, err);
+    if (rc) return from_rc(c, rc, err);
+    ++c->own_launches;
+    k_sub_from<<<vec_grid(len), 256, 0, c->st>>>(in, c->d_r64, len);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "project");
+    if ((e = cudaMemcpyAsync(out, c->d_r64, len * sizeof(double), cudaMemcpyDeviceToDevice, c->st)) != cudaSuccess)
+      return cuda_fail(c, e, "copy");
+    return FH_OK;
+  }
+  // float32 context
+  ++c->own_launches;
+  k_convert_vec<float><<<vec_grid(len), 256, 0, c->st>>>(in, c->p32->rhs[0], len);
+  float* rin[fh::kMaxLoads] = {c->p32->rhs[0]};
+  float* rout[fh::kMaxLoads] = {c->p32->ap[0]};
+  int rc = c->p32->project_complement(rin, rout, err);
+  if (rc) return from_rc(c, rc, err);
+  ++c->own_launches;
+  k_widen_vec<float><<<vec_grid(len), 256, 0, c->st>>>(c->p32->ap[0], c->d_r64, len);
+  ++c->own_launches;
+  k_sub_from<<<vec_grid(len), 256, 0, c->st>>>(in, c->d_r64, len);
+  if ((e = cudaMemcpyAsync(out, c->d_r64, len * sizeof(double), cudaMemcpyDeviceToDevice, c->st)) != cudaSuccess)
+    return cuda_fail(c, e, "copy");
+  return FH_OK;
 }
 
 fh_status fh_profile(fh_ctx* c, int dtype, int what, int reps, double* ms) {

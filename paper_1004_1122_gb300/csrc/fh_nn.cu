@@ -1,0 +1,669 @@
+// fh_nn.cu -- the learned warm start's 3-D convolutional network: forward,
+// backward and Adam, all in hand-written kernels.
+//
+// Activations are float32 [channels][N0][N1][N2]; weights are kept as float32
+// masters for Adam and rounded to bfloat16 (round to nearest even) for every
+// product; products accumulate in float32.  Architecture (levels N, N/3,
+// N/9, N/27; channels c0..c3):
+//   a0 = leaky(conv(x))            a1 = leaky(conv(pool(a0)))
+//   a2 = leaky(conv(pool(a1)))     a3 = leaky(conv(pool(a2)))
+//   u2 = up(leaky(conv(a3))) + a2  u1 = up(leaky(conv(u2))) + a1
+//   u0 = up(leaky(conv(u1))) + a0  y  = conv(u0)
+// conv = 3x3x3 with periodic padding (the unit cell is periodic), pool = mean
+// over 3x3x3 blocks, up = nearest-neighbour upsampling by 3.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fh_nn.h"
+
+namespace {
+
+constexpr float kSlope = 0.1f;
+constexpr int kOC = 16;      // output channels per conv CTA
+constexpr int kCC = 8;       // input channels staged per step
+constexpr int kThreads = 256;
+
+struct Dims {
+  int n0, n1, n2;
+  __host__ __device__ long long v() const { return (long long)n0 * n1 * n2; }
+};
+
+// y[o] = b[o] + sum_c sum_t w(o, c, t) x[c](. + t), periodic.
+// TRANS: backward data, y = gradient wrt the input: y[c] = sum_o sum_t
+// w[o][c][t] x[o](. - t), i.e. the same loop with w(c_out, c_in, t) =
+// W[c_in][c_out][26 - t].
+template <bool TRANS>
+__global__ void __launch_bounds__(kThreads) k_conv(const float* __restrict__ x, int C,
+                                                   float* __restrict__ y, int O,
+                                                   const __nv_bfloat16* __restrict__ W,
+                                                   const float* __restrict__ b, Dims dm) {
+  __shared__ float ws[kOC][kCC][27];
+  const long long V = dm.v();
+  const long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int o0 = blockIdx.y * kOC;
+  const bool live = vox < V;
+  int off[27];
+  if (live) {
+    const int z = (int)(vox / ((long long)dm.n1 * dm.n2));
+    const int rem = (int)(vox - (long long)z * dm.n1 * dm.n2);
+    const int yy = rem / dm.n2, xx = rem - yy * dm.n2;
+    int t = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = (z + dz + dm.n0) % dm.n0;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int y2 = (yy + dy + dm.n1) % dm.n1;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int x2 = (xx + dx + dm.n2) % dm.n2;
+          off[t++] = (zz * dm.n1 + y2) * dm.n2 + x2;
+        }
+      }
+    }
+  }
+  float acc[kOC];
+#pragma unroll
+  for (int k = 0; k < kOC; ++k) acc[k] = 0.0f;
+  for (int c0 = 0; c0 < C; c0 += kCC) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOC * kCC * 27; i += blockDim.x) {
+      const int oo = i / (kCC * 27), rem = i - oo * kCC * 27;
+      const int cc = rem / 27, t = rem - cc * 27;
+      const int o = o0 + oo, c = c0 + cc;
+      float w = 0.0f;
+      if (o < O && c < C) {
+        w = TRANS ? __bfloat162float(W[((long long)c * O + o) * 27 + (26 - t)])
+                  : __bfloat162float(W[((long long)o * C + c) * 27 + t]);
+      }
+      ws[oo][cc][t] = w;
+    }
+    __syncthreads();
+    if (!live) continue;
+    const int cn = min(kCC, C - c0);
+    for (int cc = 0; cc < cn; ++cc) {
+      const float* xc = x + (long long)(c0 + cc) * V;
+      float v[27];
+#pragma unroll
+      for (int t = 0; t < 27; ++t) v[t] = __ldg(xc + off[t]);
+#pragma unroll
+      for (int k = 0; k < kOC; ++k) {
+        float s = acc[k];
+#pragma unroll
+        for (int t = 0; t < 27; ++t) s = fmaf(ws[k][cc][t], v[t], s);
+        acc[k] = s;
+      }
+    }
+  }
+  if (!live) return;
+#pragma unroll
+  for (int k = 0; k < kOC; ++k) {
+    const int o = o0 + k;
+    if (o < O) y[(long long)o * V + vox] = acc[k] + (b ? b[o] : 0.0f);
+  }
+}
+
+// dW[o][c][t] = sum_z gy[o](z) x[c](z + t);  db[o] = sum_z gy[o](z).
+// One CTA per (o, c): 27 tap sums reduced over the voxels, no atomics.
+__global__ void __launch_bounds__(kThreads) k_conv_wgrad(const float* __restrict__ x, int C,
+                                                         const float* __restrict__ gy, int O,
+                                                         float* __restrict__ gW, float* __restrict__ gb,
+                                                         Dims dm) {
+  const int o = blockIdx.x / C, c = blockIdx.x - (blockIdx.x / C) * C;
+  const long long V = dm.v();
+  const float* xc = x + (long long)c * V;
+  const float* go = gy + (long long)o * V;
+  float acc[27];
+#pragma unroll
+  for (int t = 0; t < 27; ++t) acc[t] = 0.0f;
+  float accb = 0.0f;
+  for (long long vox = threadIdx.x; vox < V; vox += blockDim.x) {
+    const int z = (int)(vox / ((long long)dm.n1 * dm.n2));
+    const int rem = (int)(vox - (long long)z * dm.n1 * dm.n2);
+    const int yy = rem / dm.n2, xx = rem - yy * dm.n2;
+    const float g = __ldg(go + vox);
+    accb += g;
+    int t = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = (z + dz + dm.n0) % dm.n0;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int y2 = (yy + dy + dm.n1) % dm.n1;
+        const int rowo = (zz * dm.n1 + y2) * dm.n2;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int x2 = (xx + dx + dm.n2) % dm.n2;
+          acc[t] = fmaf(g, __ldg(xc + rowo + x2), acc[t]);
+          ++t;
+        }
+      }
+    }
+  }
+  __shared__ float red[kThreads / 32][28];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < 28; ++t) {
+    float s = t < 27 ? acc[t] : accb;
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) s += __shfl_down_sync(0xffffffffu, s, k);
+    if (lane == 0) red[warp][t] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 28) {
+    float s = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+    if (threadIdx.x < 27) gW[((long long)o * C + c) * 27 + threadIdx.x] = s;
+    else if (c == 0) gb[o] = s;
+  }
+}
+
+__global__ void k_leaky(const float* __restrict__ z, float* __restrict__ a, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float v = z[i];
+    a[i] = v > 0.0f ? v : kSlope * v;
+  }
+}
+
+// g <- g * leaky'(z)
+__global__ void k_leaky_bwd(const float* __restrict__ z, float* __restrict__ g, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!(z[i] > 0.0f)) g[i] *= kSlope;
+}
+
+// coarse[c][Z][Y][X] = mean of the 3x3x3 fine block (fine dims = 3 * coarse dims)
+__global__ void k_pool(const float* __restrict__ fine, float* __restrict__ coarse, int C, Dims cd) {
+  const long long Vc = cd.v();
+  const long long n = Vc * C;
+  const int f1 = 3 * cd.n1, f2 = 3 * cd.n2;
+  const long long Vf = 27 * Vc;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / Vc);
+    const long long v = i - (long long)c * Vc;
+    const int Z = (int)(v / ((long long)cd.n1 * cd.n2));
+    const int rem = (int)(v - (long long)Z * cd.n1 * cd.n2);
+    const int Y = rem / cd.n2, X = rem - Y * cd.n2;
+    const float* fc = fine + (long long)c * Vf;
+    float s = 0.0f;
+    for (int a = 0; a < 3; ++a)
+      for (int bb = 0; bb < 3; ++bb)
+        for (int e = 0; e < 3; ++e) s += fc[((long long)(3 * Z + a) * f1 + 3 * Y + bb) * f2 + 3 * X + e];
+    coarse[i] = s * (1.0f / 27.0f);
+  }
+}
+
+// fine[c][z][y][x] = scale * coarse[c][z/3][y/3][x/3] (+ add[c][z][y][x] if add, + fine if accumulate)
+__global__ void k_up(const float* __restrict__ coarse, float* __restrict__ fine, const float* __restrict__ add,
+                     int C, Dims fd, float scale, int accumulate) {
+  const long long Vf = fd.v();
+  const long long n = Vf * C;
+  const int c1 = fd.n1 / 3, c2 = fd.n2 / 3;
+  const long long Vc = Vf / 27;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / Vf);
+    const long long v = i - (long long)c * Vf;
+    const int z = (int)(v / ((long long)fd.n1 * fd.n2));
+    const int rem = (int)(v - (long long)z * fd.n1 * fd.n2);
+    const int y = rem / fd.n2, x = rem - y * fd.n2;
+    float s = scale * coarse[(long long)c * Vc + ((long long)(z / 3) * c1 + y / 3) * c2 + x / 3];
+    if (add) s += add[i];
+    if (accumulate) s += fine[i];
+    fine[i] = s;
+  }
+}
+
+// coarse[c][Z][Y][X] = sum of the fine block (adjoint of nearest upsampling)
+__global__ void k_up_bwd(const float* __restrict__ fine, float* __restrict__ coarse, int C, Dims cd) {
+  const long long Vc = cd.v();
+  const long long n = Vc * C;
+  const int f1 = 3 * cd.n1, f2 = 3 * cd.n2;
+  const long long Vf = 27 * Vc;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / Vc);
+    const long long v = i - (long long)c * Vc;
+    const int Z = (int)(v / ((long long)cd.n1 * cd.n2));
+    const int rem = (int)(v - (long long)Z * cd.n1 * cd.n2);
+    const int Y = rem / cd.n2, X = rem - Y * cd.n2;
+    const float* fc = fine + (long long)c * Vf;
+    float s = 0.0f;
+    for (int a = 0; a < 3; ++a)
+      for (int bb = 0; bb < 3; ++bb)
+        for (int e = 0; e < 3; ++e) s += fc[((long long)(3 * Z + a) * f1 + 3 * Y + bb) * f2 + 3 * X + e];
+    coarse[i] = s;
+  }
+}
+
+// g = 2 (y - t) / n; per-block partial sums of (y - t)^2 in float64
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ g,
+                      long long n, double* part) {
+  double acc = 0.0;
+  const float sc = 2.0f / (float)n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float dlt = y[i] - t[i];
+    g[i] = sc * dlt;
+    acc += (double)dlt * (double)dlt;
+  }
+  __shared__ double red[kThreads];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ q, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    q[i] = __float2bfloat16_rn(p[i]);
+}
+
+// x[0] = tab0[phase], x[1] = tab1[phase]  (input features from the phase image)
+__global__ void k_features(const uint8_t* __restrict__ phase, const float* __restrict__ t0,
+                           const float* __restrict__ t1, float* __restrict__ x, long long V) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+    const int p = phase[i];
+    x[i] = t0[p];
+    x[V + i] = t1[p];
+  }
+}
+
+// target[b * d + a] = e^(b)_a - delta_ab  (fields: d loads, each [d][V] float64)
+__global__ void k_targets(const double* __restrict__ f0, const double* __restrict__ f1,
+                          const double* __restrict__ f2, int d, float* __restrict__ t, long long V) {
+  const double* f[3] = {f0, f1, f2};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
+    for (int b = 0; b < d; ++b)
+      for (int a = 0; a < d; ++a) t[(long long)(b * d + a) * V + i] = (float)(f[b][(long long)a * V + i] - (a == b ? 1.0 : 0.0));
+}
+
+// g[a] = sum_b E_b pred[b * d + a]  (fluctuation of load E predicted by the network)
+__global__ void k_combine(const float* __restrict__ pred, int d, double E0, double E1, double E2,
+                          double* __restrict__ g, long long V) {
+  const double E[3] = {E0, E1, E2};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
+    for (int a = 0; a < d; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < d; ++b) s += E[b] * (double)pred[(long long)(b * d + a) * V + i];
+      g[(long long)a * V + i] = s;
+    }
+}
+
+// x = E + g  (g already projected)
+__global__ void k_add_E(double* __restrict__ x, int d, double E0, double E1, double E2, long long V) {
+  const double E[3] = {E0, E1, E2};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)d * V; i += (long long)gridDim.x * blockDim.x)
+    x[i] += E[i / V];
+}
+
+int grid1(long long n) {
+  const long long g = (n + kThreads - 1) / kThreads;
+  return (int)(g < 4096 ? (g < 1 ? 1 : g) : 4096);
+}
+
+}  // namespace
+
+struct fh_nn {
+  Dims lv[4];
+  int cin = 0, cout = 0;
+  int ch[4] = {16, 32, 48, 64};
+  int lo[8], li[8], ll[8];     // layer out / in channels, level
+  long long woff[8], boff[8];  // offsets in the flat parameter vector
+  long long nparam = 0;
+  cudaStream_t st = nullptr;
+  float *P = nullptr, *G = nullptr, *Mo = nullptr, *Ve = nullptr;
+  __nv_bfloat16* Wb = nullptr;
+  // activations
+  float *x = nullptr, *z[8] = {}, *a[4] = {}, *pl[3] = {}, *u[3] = {}, *y = nullptr;
+  float *gtmp[2] = {}, *gy = nullptr, *gu[3] = {}, *ga[4] = {}, *gp[3] = {};
+  double* part = nullptr;
+  double* h_part = nullptr;
+  int npart = 0;
+  std::vector<void*> allocs;
+  long long launches = 0;
+};
+
+namespace {
+
+template <typename T>
+int nn_alloc(fh_nn* n, T** p, long long count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, (size_t)count * sizeof(T) + 16) != cudaSuccess) return FH_ERR_OOM;
+  n->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return 0;
+}
+
+cudaError_t conv(fh_nn* n, int layer, const float* in, float* out, bool trans) {
+  const int O = trans ? n->li[layer] : n->lo[layer];
+  const int C = trans ? n->lo[layer] : n->li[layer];
+  const Dims d = n->lv[n->ll[layer]];
+  dim3 grid((unsigned)((d.v() + kThreads - 1) / kThreads), (unsigned)((O + kOC - 1) / kOC));
+  ++n->launches;
+  if (trans)
+    k_conv<true><<<grid, kThreads, 0, n->st>>>(in, C, out, O, n->Wb + n->woff[layer], nullptr, d);
+  else
+    k_conv<false><<<grid, kThreads, 0, n->st>>>(in, C, out, O, n->Wb + n->woff[layer], n->P + n->boff[layer], d);
+  return cudaGetLastError();
+}
+
+cudaError_t wgrad(fh_nn* n, int layer, const float* in, const float* gy) {
+  const Dims d = n->lv[n->ll[layer]];
+  ++n->launches;
+  k_conv_wgrad<<<n->lo[layer] * n->li[layer], kThreads, 0, n->st>>>(in, n->li[layer], gy, n->lo[layer],
+                                                                     n->G + n->woff[layer], n->G + n->boff[layer], d);
+  return cudaGetLastError();
+}
+
+void leaky(fh_nn* n, const float* z, float* a, long long cnt) {
+  ++n->launches;
+  k_leaky<<<grid1(cnt), kThreads, 0, n->st>>>(z, a, cnt);
+}
+void leaky_bwd(fh_nn* n, const float* z, float* g, long long cnt) {
+  ++n->launches;
+  k_leaky_bwd<<<grid1(cnt), kThreads, 0, n->st>>>(z, g, cnt);
+}
+void pool(fh_nn* n, const float* f, float* c, int C, Dims cd) {
+  ++n->launches;
+  k_pool<<<grid1(cd.v() * C), kThreads, 0, n->st>>>(f, c, C, cd);
+}
+void up(fh_nn* n, const float* c, float* f, const float* add, int C, Dims fd, float scale, int accum) {
+  ++n->launches;
+  k_up<<<grid1(fd.v() * C), kThreads, 0, n->st>>>(c, f, add, C, fd, scale, accum);
+}
+void up_bwd(fh_nn* n, const float* f, float* c, int C, Dims cd) {
+  ++n->launches;
+  k_up_bwd<<<grid1(cd.v() * C), kThreads, 0, n->st>>>(f, c, C, cd);
+}
+
+cudaError_t forward(fh_nn* n) {
+  cudaError_t e;
+  const long long V0 = n->lv[0].v(), V1 = n->lv[1].v(), V2 = n->lv[2].v(), V3 = n->lv[3].v();
+  ++n->launches;
+  k_to_bf16<<<grid1(n->nparam), kThreads, 0, n->st>>>(n->P, n->Wb, n->nparam);
+  if ((e = conv(n, 0, n->x, n->z[0], false))) return e;
+  leaky(n, n->z[0], n->a[0], V0 * n->ch[0]);
+  pool(n, n->a[0], n->pl[0], n->ch[0], n->lv[1]);
+  if ((e = conv(n, 1, n->pl[0], n->z[1], false))) return e;
+  leaky(n, n->z[1], n->a[1], V1 * n->ch[1]);
+  pool(n, n->a[1], n->pl[1], n->ch[1], n->lv[2]);
+  if ((e = conv(n, 2, n->pl[1], n->z[2], false))) return e;
+  leaky(n, n->z[2], n->a[2], V2 * n->ch[2]);
+  pool(n, n->a[2], n->pl[2], n->ch[2], n->lv[3]);
+  if ((e = conv(n, 3, n->pl[2], n->z[3], false))) return e;
+  leaky(n, n->z[3], n->a[3], V3 * n->ch[3]);
+  // decoder: z4 at level 3, u2 = up(leaky(z4)) + a2 at level 2 (gtmp[0] holds leaky(z4))
+  if ((e = conv(n, 4, n->a[3], n->z[4], false))) return e;
+  leaky(n, n->z[4], n->gtmp[0], V3 * n->ch[2]);
+  up(n, n->gtmp[0], n->u[2], n->a[2], n->ch[2], n->lv[2], 1.0f, 0);
+  if ((e = conv(n, 5, n->u[2], n->z[5], false))) return e;
+  leaky(n, n->z[5], n->gtmp[0], V2 * n->ch[1]);
+  up(n, n->gtmp[0], n->u[1], n->a[1], n->ch[1], n->lv[1], 1.0f, 0);
+  if ((e = conv(n, 6, n->u[1], n->z[6], false))) return e;
+  leaky(n, n->z[6], n->gtmp[0], V1 * n->ch[0]);
+  up(n, n->gtmp[0], n->u[0], n->a[0], n->ch[0], n->lv[0], 1.0f, 0);
+  if ((e = conv(n, 7, n->u[0], n->y, false))) return e;
+  return cudaGetLastError();
+}
+
+// gradients of sum(gy * y) (gy already in n->gy)
+cudaError_t backward(fh_nn* n) {
+  cudaError_t e;
+  // layer 7
+  if ((e = wgrad(n, 7, n->u[0], n->gy))) return e;
+  if ((e = conv(n, 7, n->gy, n->gu[0], true))) return e;          // g_u0 (c0, level 0)
+  // u0 = up(leaky(z6)) + a0:  g_a0 = g_u0 ; g_z6 = leaky'(z6) * upT(g_u0)
+  up_bwd(n, n->gu[0], n->gtmp[1], n->ch[0], n->lv[1]);            // c0 at level 1
+  leaky_bwd(n, n->z[6], n->gtmp[1], n->lv[1].v() * n->ch[0]);
+  if ((e = wgrad(n, 6, n->u[1], n->gtmp[1]))) return e;
+  if ((e = conv(n, 6, n->gtmp[1], n->gu[1], true))) return e;      // g_u1 (c1, level 1)
+  up_bwd(n, n->gu[1], n->gtmp[1], n->ch[1], n->lv[2]);            // c1 at level 2
+  leaky_bwd(n, n->z[5], n->gtmp[1], n->lv[2].v() * n->ch[1]);
+  if ((e = wgrad(n, 5, n->u[2], n->gtmp[1]))) return e;
+  if ((e = conv(n, 5, n->gtmp[1], n->gu[2], true))) return e;      // g_u2 (c2, level 2)
+  up_bwd(n, n->gu[2], n->gtmp[1], n->ch[2], n->lv[3]);            // c2 at level 3
+  leaky_bwd(n, n->z[4], n->gtmp[1], n->lv[3].v() * n->ch[2]);
+  if ((e = wgrad(n, 4, n->a[3], n->gtmp[1]))) return e;
+  if ((e = conv(n, 4, n->gtmp[1], n->ga[3], true))) return e;      // g_a3
+  leaky_bwd(n, n->z[3], n->ga[3], n->lv[3].v() * n->ch[3]);        // -> g_z3
+  if ((e = wgrad(n, 3, n->pl[2], n->ga[3]))) return e;
+  if ((e = conv(n, 3, n->ga[3], n->gp[2], true))) return e;        // g_p2 (c2, level 3)
+  // g_a2 = g_u2 + poolT(g_p2)
+  up(n, n->gp[2], n->gu[2], nullptr, n->ch[2], n->lv[2], 1.0f / 27.0f, 1);
+  leaky_bwd(n, n->z[2], n->gu[2], n->lv[2].v() * n->ch[2]);        // -> g_z2
+  if ((e = wgrad(n, 2, n->pl[1], n->gu[2]))) return e;
+  if ((e = conv(n, 2, n->gu[2], n->gp[1], true))) return e;        // g_p1 (c1, level 2)
+  up(n, n->gp[1], n->gu[1], nullptr, n->ch[1], n->lv[1], 1.0f / 27.0f, 1);
+  leaky_bwd(n, n->z[1], n->gu[1], n->lv[1].v() * n->ch[1]);        // -> g_z1
+  if ((e = wgrad(n, 1, n->pl[0], n->gu[1]))) return e;
+  if ((e = conv(n, 1, n->gu[1], n->gp[0], true))) return e;        // g_p0 (c0, level 1)
+  up(n, n->gp[0], n->gu[0], nullptr, n->ch[0], n->lv[0], 1.0f / 27.0f, 1);
+  leaky_bwd(n, n->z[0], n->gu[0], n->lv[0].v() * n->ch[0]);        // -> g_z0
+  if ((e = wgrad(n, 0, n->x, n->gu[0]))) return e;
+  return cudaGetLastError();
+}
+
+int loss_grad(fh_nn* n, const float* target, double* loss) {
+  const long long cnt = n->lv[0].v() * n->cout;
+  const int g = std::min(n->npart, grid1(cnt));
+  ++n->launches;
+  k_mse<<<g, kThreads, 0, n->st>>>(n->y, target, n->gy, cnt, n->part);
+  if (cudaMemcpyAsync(n->h_part, n->part, g * sizeof(double), cudaMemcpyDeviceToHost, n->st) != cudaSuccess)
+    return FH_ERR_CUDA;
+  if (cudaStreamSynchronize(n->st) != cudaSuccess) return FH_ERR_CUDA;
+  double s = 0.0;
+  for (int i = 0; i < g; ++i) s += n->h_part[i];
+  if (loss) *loss = s / (double)cnt;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fh_nn_destroy(fh_nn* n) {
+  if (!n) return;
+  if (n->st) cudaStreamSynchronize(n->st);
+  for (void* p : n->allocs) cudaFree(p);
+  if (n->h_part) cudaFreeHost(n->h_part);
+  delete n;
+}
+
+fh_status fh_nn_create(fh_nn** out, const int* N, int cin, int cout, const int* channels, void* stream) {
+  if (!out || !N || cin < 1 || cout < 1) return FH_ERR_ARG;
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a)
+    if (N[a] < 27 || N[a] % 27) return FH_ERR_ARG;
+  fh_nn* n = new (std::nothrow) fh_nn();
+  if (!n) return FH_ERR_OOM;
+  n->cin = cin;
+  n->cout = cout;
+  if (channels)
+    for (int k = 0; k < 4; ++k) {
+      if (channels[k] < 1) {
+        delete n;
+        return FH_ERR_ARG;
+      }
+      n->ch[k] = channels[k];
+    }
+  for (int l = 0; l < 4; ++l) {
+    int f = 1;
+    for (int k = 0; k < l; ++k) f *= 3;
+    n->lv[l] = Dims{N[0] / f, N[1] / f, N[2] / f};
+  }
+  const int io[8][3] = {{cin, n->ch[0], 0},        {n->ch[0], n->ch[1], 1}, {n->ch[1], n->ch[2], 2},
+                        {n->ch[2], n->ch[3], 3},   {n->ch[3], n->ch[2], 3}, {n->ch[2], n->ch[1], 2},
+                        {n->ch[1], n->ch[0], 1},   {n->ch[0], cout, 0}};
+  long long off = 0;
+  for (int k = 0; k < 8; ++k) {
+    n->li[k] = io[k][0];
+    n->lo[k] = io[k][1];
+    n->ll[k] = io[k][2];
+    n->woff[k] = off;
+    off += (long long)n->lo[k] * n->li[k] * 27;
+    n->boff[k] = off;
+    off += n->lo[k];
+  }
+  n->nparam = off;
+  n->st = (cudaStream_t)stream;
+  int rc = 0;
+  const long long V[4] = {n->lv[0].v(), n->lv[1].v(), n->lv[2].v(), n->lv[3].v()};
+  int cmax = cout;
+  for (int k = 0; k < 4; ++k) cmax = std::max(cmax, n->ch[k]);
+  rc |= nn_alloc(n, &n->P, off);
+  rc |= nn_alloc(n, &n->G, off);
+  rc |= nn_alloc(n, &n->Mo, off);
+  rc |= nn_alloc(n, &n->Ve, off);
+  rc |= nn_alloc(n, &n->Wb, off);
+  rc |= nn_alloc(n, &n->x, V[0] * cin);
+  for (int k = 0; k < 4; ++k) rc |= nn_alloc(n, &n->z[k], V[k] * n->ch[k]);
+  rc |= nn_alloc(n, &n->z[4], V[3] * n->ch[2]);
+  rc |= nn_alloc(n, &n->z[5], V[2] * n->ch[1]);
+  rc |= nn_alloc(n, &n->z[6], V[1] * n->ch[0]);
+  for (int k = 0; k < 4; ++k) rc |= nn_alloc(n, &n->a[k], V[k] * n->ch[k]);
+  for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->pl[k], V[k + 1] * n->ch[k]);
+  for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->u[k], V[k] * n->ch[k]);
+  rc |= nn_alloc(n, &n->y, V[0] * cout);
+  rc |= nn_alloc(n, &n->gy, V[0] * cout);
+  for (int k = 0; k < 2; ++k) rc |= nn_alloc(n, &n->gtmp[k], V[1] * cmax);
+  for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->gu[k], V[k] * n->ch[k]);
+  for (int k = 0; k < 4; ++k) rc |= nn_alloc(n, &n->ga[k], V[k] * n->ch[k]);
+  for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->gp[k], V[k + 1] * n->ch[k]);
+  n->npart = 4096;
+  rc |= nn_alloc(n, &n->part, n->npart);
+  if (!rc && cudaMallocHost(&n->h_part, n->npart * sizeof(double)) != cudaSuccess) rc = FH_ERR_OOM;
+  if (!rc && (cudaMemsetAsync(n->Mo, 0, off * sizeof(float), n->st) != cudaSuccess ||
+              cudaMemsetAsync(n->Ve, 0, off * sizeof(float), n->st) != cudaSuccess ||
+              cudaMemsetAsync(n->P, 0, off * sizeof(float), n->st) != cudaSuccess))
+    rc = FH_ERR_CUDA;
+  if (rc) {
+    fh_nn_destroy(n);
+    return FH_ERR_OOM;
+  }
+  *out = n;
+  return FH_OK;
+}
+
+long long fh_nn_param_count(const fh_nn* n) { return n ? n->nparam : 0; }
+
+long long fh_nn_launches(const fh_nn* n) { return n ? n->launches : 0; }
+
+fh_status fh_nn_set_params(fh_nn* n, const float* host, long long count) {
+  if (!n || !host || count != n->nparam) return FH_ERR_ARG;
+  if (cudaMemcpyAsync(n->P, host, count * sizeof(float), cudaMemcpyHostToDevice, n->st) != cudaSuccess ||
+      cudaMemsetAsync(n->Mo, 0, count * sizeof(float), n->st) != cudaSuccess ||
+      cudaMemsetAsync(n->Ve, 0, count * sizeof(float), n->st) != cudaSuccess ||
+      cudaStreamSynchronize(n->st) != cudaSuccess)
+    return FH_ERR_CUDA;
+  return FH_OK;
+}
+
+fh_status fh_nn_get_params(fh_nn* n, float* host, long long count) {
+  if (!n || !host || count != n->nparam) return FH_ERR_ARG;
+  if (cudaMemcpyAsync(host, n->P, count * sizeof(float), cudaMemcpyDeviceToHost, n->st) != cudaSuccess ||
+      cudaStreamSynchronize(n->st) != cudaSuccess)
+    return FH_ERR_CUDA;
+  return FH_OK;
+}
+
+fh_status fh_nn_forward(fh_nn* n, const float* x, float* y) {
+  if (!n || !x || !y) return FH_ERR_ARG;
+  const long long Vx = n->lv[0].v() * n->cin, Vy = n->lv[0].v() * n->cout;
+  if (cudaMemcpyAsync(n->x, x, Vx * sizeof(float), cudaMemcpyDeviceToDevice, n->st) != cudaSuccess)
+    return FH_ERR_CUDA;
+  if (forward(n) != cudaSuccess) return FH_ERR_CUDA;
+  if (cudaMemcpyAsync(y, n->y, Vy * sizeof(float), cudaMemcpyDeviceToDevice, n->st) != cudaSuccess)
+    return FH_ERR_CUDA;
+  return FH_OK;
+}
+
+fh_status fh_nn_gradients(fh_nn* n, const float* x, const float* target, double* loss, float* grad_host) {
+  if (!n || !x || !target) return FH_ERR_ARG;
+  const long long Vx = n->lv[0].v() * n->cin;
+  if (cudaMemcpyAsync(n->x, x, Vx * sizeof(float), cudaMemcpyDeviceToDevice, n->st) != cudaSuccess)
+    return FH_ERR_CUDA;
+  if (forward(n) != cudaSuccess) return FH_ERR_CUDA;
+  int rc = loss_grad(n, target, loss);
+  if (rc) return (fh_status)rc;
+  if (backward(n) != cudaSuccess) return FH_ERR_CUDA;
+  if (grad_host) {
+    if (cudaMemcpyAsync(grad_host, n->G, n->nparam * sizeof(float), cudaMemcpyDeviceToHost, n->st) != cudaSuccess ||
+        cudaStreamSynchronize(n->st) != cudaSuccess)
+      return FH_ERR_CUDA;
+  }
+  return FH_OK;
+}
+
+fh_status fh_nn_train_step(fh_nn* n, const float* x, const float* target, float lr, int step, double* loss) {
+  if (!n || step < 1 || !(lr > 0.0f)) return FH_ERR_ARG;
+  fh_status s = fh_nn_gradients(n, x, target, loss, nullptr);
+  if (s != FH_OK) return s;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - (float)std::pow(0.9, step), c2 = 1.0f - (float)std::pow(0.999, step);
+  ++n->launches;
+  k_adam<<<grid1(n->nparam), kThreads, 0, n->st>>>(n->P, n->G, n->Mo, n->Ve, n->nparam, lr, b1, b2, 1e-8f, c1, c2);
+  return cudaGetLastError() == cudaSuccess ? FH_OK : FH_ERR_CUDA;
+}
+
+fh_status fh_nn_features(const uint8_t* phase, int nphase, const double* L, int d, long long nodes,
+                         float* x, void* stream) {
+  if (!phase || !L || !x || nphase < 1 || nphase > 256 || (d != 2 && d != 3)) return FH_ERR_ARG;
+  // channel 0: log10(L_p / L_0) / 4 (isotropic phases, first diagonal entry), channel 1: indicator
+  std::vector<float> h(512, 0.0f);
+  const double l0 = L[0];
+  if (!(l0 > 0.0)) return FH_ERR_NOT_SPD;
+  for (int p = 0; p < nphase; ++p) {
+    const double lp = L[(size_t)p * d * d];
+    if (!(lp > 0.0)) return FH_ERR_NOT_SPD;
+    h[p] = (float)(std::log10(lp / l0) / 4.0);
+    h[256 + p] = p > 0 ? 1.0f : 0.0f;
+  }
+  float* dt = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMallocAsync((void**)&dt, 512 * sizeof(float), st) != cudaSuccess) return FH_ERR_OOM;
+  cudaMemcpyAsync(dt, h.data(), 512 * sizeof(float), cudaMemcpyHostToDevice, st);
+  k_features<<<grid1(nodes), kThreads, 0, st>>>(phase, dt, dt + 256, x, nodes);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(dt, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? FH_OK : FH_ERR_CUDA;
+}
+
+fh_status fh_nn_targets(const double* const* fields, int d, long long nodes, float* target, void* stream) {
+  if (!fields || !target || (d != 2 && d != 3)) return FH_ERR_ARG;
+  for (int b = 0; b < d; ++b)
+    if (!fields[b]) return FH_ERR_ARG;
+  k_targets<<<grid1(nodes), kThreads, 0, (cudaStream_t)stream>>>(fields[0], fields[1], d > 2 ? fields[2] : fields[0], d,
+                                                                  target, nodes);
+  return cudaGetLastError() == cudaSuccess ? FH_OK : FH_ERR_CUDA;
+}
+
+fh_status fh_nn_warm_start(fh_ctx* ctx, const float* pred, const double* E, int d, long long nodes, double* x0,
+                           void* stream) {
+  if (!ctx || !pred || !E || !x0 || (d != 2 && d != 3)) return FH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_combine<<<grid1(nodes), kThreads, 0, st>>>(pred, d, E[0], E[1], d > 2 ? E[2] : 0.0, x0, nodes);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return FH_ERR_CUDA;
+  fh_status s = fh_project_compatible(ctx, x0, x0);
+  if (s != FH_OK) return s;
+  cudaDeviceSynchronize();
+  k_add_E<<<grid1((long long)d * nodes), kThreads, 0, st>>>(x0, d, E[0], E[1], d > 2 ? E[2] : 0.0, nodes);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return FH_ERR_CUDA;
+  return FH_OK;
+}
+
+}  // extern "C"

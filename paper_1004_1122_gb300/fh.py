@@ -34,8 +34,12 @@ DT_FP64, DT_FP32 = 0, 1
 EXPORTS = (
     "fh_create", "fh_set_phase", "fh_apply", "fh_solve", "fh_solve_all", "fh_effective_column",
     "fh_eta_e", "fh_profile", "fh_autotune", "fh_apply_noalloc", "fh_batch_create", "fh_batch_solve",
-    "fh_batch_last_error", "fh_batch_destroy", "fh_destroy", "fh_status_string", "fh_last_error",
+    "fh_batch_last_error", "fh_batch_destroy", "fh_project_compatible", "fh_destroy", "fh_status_string", "fh_last_error",
     "fh_version",
+    # fh_nn.h
+    "fh_nn_create", "fh_nn_param_count", "fh_nn_launches", "fh_nn_set_params", "fh_nn_get_params",
+    "fh_nn_forward", "fh_nn_gradients", "fh_nn_train_step", "fh_nn_destroy", "fh_nn_features",
+    "fh_nn_targets", "fh_nn_warm_start",
 )
 
 
@@ -102,6 +106,34 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fh_batch_last_error.restype = ctypes.c_char_p
     lib.fh_batch_destroy.argtypes = [P]
     lib.fh_batch_destroy.restype = V
+    lib.fh_project_compatible.argtypes = [P, P, P]
+    lib.fh_project_compatible.restype = I
+    LL = ctypes.c_longlong
+    pF = ctypes.POINTER(ctypes.c_float)
+    lib.fh_nn_create.argtypes = [ctypes.POINTER(P), pI, I, I, pI, P]
+    lib.fh_nn_create.restype = I
+    lib.fh_nn_param_count.argtypes = [P]
+    lib.fh_nn_param_count.restype = LL
+    lib.fh_nn_launches.argtypes = [P]
+    lib.fh_nn_launches.restype = LL
+    lib.fh_nn_set_params.argtypes = [P, pF, LL]
+    lib.fh_nn_set_params.restype = I
+    lib.fh_nn_get_params.argtypes = [P, pF, LL]
+    lib.fh_nn_get_params.restype = I
+    lib.fh_nn_forward.argtypes = [P, P, P]
+    lib.fh_nn_forward.restype = I
+    lib.fh_nn_gradients.argtypes = [P, P, P, pD, pF]
+    lib.fh_nn_gradients.restype = I
+    lib.fh_nn_train_step.argtypes = [P, P, P, ctypes.c_float, I, pD]
+    lib.fh_nn_train_step.restype = I
+    lib.fh_nn_destroy.argtypes = [P]
+    lib.fh_nn_destroy.restype = V
+    lib.fh_nn_features.argtypes = [P, I, pD, I, LL, P, P]
+    lib.fh_nn_features.restype = I
+    lib.fh_nn_targets.argtypes = [ctypes.POINTER(ctypes.c_void_p), I, LL, P, P]
+    lib.fh_nn_targets.restype = I
+    lib.fh_nn_warm_start.argtypes = [P, P, pD, I, LL, P, P]
+    lib.fh_nn_warm_start.restype = I
     lib.fh_autotune.argtypes = [P, I, pD, pD]
     lib.fh_autotune.restype = I
     lib.fh_apply_noalloc.argtypes = [I, pI, pD, P, I, pD, pD, P, P, I, P, ctypes.c_char_p, ctypes.c_size_t]
@@ -277,6 +309,14 @@ class Solver:
                     "fh_autotune")
         return float(b[0]), float(a[0])
 
+    def project_compatible(self, f, out=None):
+        """Q f: the compatible part of a float64 field (fh_project_compatible)."""
+        if out is None:
+            out = self._torch.empty_like(f)
+        self._check(self.lib.fh_project_compatible(self.ctx, ctypes.c_void_p(f.data_ptr()),
+                                                   ctypes.c_void_p(out.data_ptr())), "fh_project_compatible")
+        return out
+
     def effective_column(self, e) -> np.ndarray:
         col = np.zeros(self.d)
         self._check(self.lib.fh_effective_column(self.ctx, ctypes.c_void_p(e.data_ptr()), _dptr(col)),
@@ -345,6 +385,120 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Net:
+    """The warm-start network (fh_nn_*): float32 activations, bfloat16 weights.
+
+    N        grid (3 ints, multiples of 27); cin / cout channels;
+    channels (c0, c1, c2, c3) or None for (16, 32, 48, 64).
+    """
+
+    def __init__(self, N, cin: int, cout: int, channels=None, stream=None):
+        import torch
+
+        self._torch = torch
+        self.lib = load_library()
+        self.N = tuple(int(n) for n in N)
+        self.cin, self.cout = cin, cout
+        Nh = (ctypes.c_int * 3)(*self.N)
+        ch = None if channels is None else (ctypes.c_int * 4)(*channels)
+        st = 0 if stream is None else stream.cuda_stream
+        h = ctypes.c_void_p()
+        rc = self.lib.fh_nn_create(ctypes.byref(h), Nh, cin, cout, ch, ctypes.c_void_p(st))
+        if rc != FH_OK:
+            raise FhError(rc, "fh_nn_create failed")
+        self.h = h
+        self.nparam = int(self.lib.fh_nn_param_count(h))
+        self.step = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fh_nn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc, what):
+        if rc != FH_OK:
+            raise FhError(rc, what)
+
+    def set_params(self, flat: np.ndarray):
+        f = np.ascontiguousarray(flat, dtype=np.float32)
+        self._chk(self.lib.fh_nn_set_params(self.h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), f.size),
+                  "fh_nn_set_params")
+        self.step = 0
+
+    def get_params(self) -> np.ndarray:
+        f = np.zeros(self.nparam, dtype=np.float32)
+        self._chk(self.lib.fh_nn_get_params(self.h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), f.size),
+                  "fh_nn_get_params")
+        return f
+
+    def forward(self, x, out=None):
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.cout,) + self.N, dtype=torch.float32, device=x.device)
+        self._chk(self.lib.fh_nn_forward(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr())),
+                  "fh_nn_forward")
+        return out
+
+    def gradients(self, x, target):
+        g = np.zeros(self.nparam, dtype=np.float32)
+        loss = np.zeros(1)
+        self._chk(self.lib.fh_nn_gradients(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                           _dptr(loss), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+                  "fh_nn_gradients")
+        return float(loss[0]), g
+
+    def train_step(self, x, target, lr: float) -> float:
+        self.step += 1
+        loss = np.zeros(1)
+        self._chk(self.lib.fh_nn_train_step(self.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                            float(lr), self.step, _dptr(loss)), "fh_nn_train_step")
+        return float(loss[0])
+
+    def launches(self) -> int:
+        return int(self.lib.fh_nn_launches(self.h))
+
+
+def nn_features(phase_dev, L, out):
+    """Network input (2 channels) from a device phase image and its isotropic table."""
+    lib = load_library()
+    Lh = np.ascontiguousarray(L, dtype=np.float64)
+    rc = lib.fh_nn_features(ctypes.c_void_p(phase_dev.data_ptr()), Lh.shape[0], _dptr(Lh), Lh.shape[-1],
+                            phase_dev.numel(), ctypes.c_void_p(out.data_ptr()), None)
+    if rc != FH_OK:
+        raise FhError(rc, "fh_nn_features")
+    return out
+
+
+def nn_targets(fields, out):
+    """Training target (d*d channels) from the d solved unit-load fields (float64, device)."""
+    lib = load_library()
+    d = len(fields)
+    arr = (ctypes.c_void_p * d)(*[f.data_ptr() for f in fields])
+    nodes = fields[0].numel() // d
+    rc = lib.fh_nn_targets(arr, d, nodes, ctypes.c_void_p(out.data_ptr()), None)
+    if rc != FH_OK:
+        raise FhError(rc, "fh_nn_targets")
+    return out
+
+
+def nn_warm_start(solver: "Solver", pred, E, out):
+    """x0 = E + Q(sum_b E_b pred_b): the projected warm start for load E."""
+    lib = load_library()
+    Eh = np.ascontiguousarray(E, dtype=np.float64)
+    nodes = int(np.prod(solver.N))
+    rc = lib.fh_nn_warm_start(solver.ctx, ctypes.c_void_p(pred.data_ptr()), _dptr(Eh), solver.d, nodes,
+                              ctypes.c_void_p(out.data_ptr()), None)
+    if rc != FH_OK:
+        raise FhError(rc, "fh_nn_warm_start")
+    return out
 
 
 def version() -> str:

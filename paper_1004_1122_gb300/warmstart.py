@@ -1,0 +1,137 @@
+"""Learned warm start for the CG solve of Eq. (linear_system).
+
+The solution of (I + B) e = E is linear in the macroscopic field E, so one
+network prediction per microstructure serves every load: the network
+(``fh_nn_*``, hand-written kernels) maps the phase image to the fluctuation
+fields e^(b) - e_b of the d unit loads, and the warm start for a load E is
+
+    x0 = E + Q ( sum_b E_b (e^(b) - e_b) ),
+
+with Q the compatible projection of Section 2.1 (``fh_nn_warm_start``), so
+that x0 - E is a zero-mean compatible field, the subspace on which the
+Krylov iterates of Section 3 live.  Plain CG from e = E stays the judge: the
+warm start is used only when its true residual is below the cold start's,
+and both run to the same tolerance on the same operator.
+
+This module sequences the library calls (features, targets, training steps,
+prediction, solves); every arithmetic step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import math
+import time
+from typing import Sequence
+
+import numpy as np
+
+from . import fh
+
+
+def init_params(N, d: int, seed: int, channels=None) -> np.ndarray:
+    """He-normal weights (std sqrt(2 / (27 * fan_in))) and zero biases, flat float32,
+    in the library's parameter order (per layer: weights [out][in][27], biases)."""
+    c0, c1, c2, c3 = channels if channels is not None else (16, 32, 48, 64)
+    io = [(2, c0), (c0, c1), (c1, c2), (c2, c3), (c3, c2), (c2, c1), (c1, c0), (c0, d * d)]
+    rng = np.random.default_rng(seed)
+    parts = []
+    for (ci, co) in io:
+        parts.append(rng.normal(0.0, math.sqrt(2.0 / (27.0 * ci)), size=co * ci * 27))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def features(phase_dev, L):
+    """Network input [2][N...] float32 for a device phase image and its isotropic table."""
+    import torch
+
+    x = torch.empty((2,) + tuple(phase_dev.shape), dtype=torch.float32, device=phase_dev.device)
+    return fh.nn_features(phase_dev, L, x)
+
+
+def training_pair(solver: fh.Solver, phase_dev, L, tol: float = 1e-6, max_iter: int = 20000):
+    """(input, target) for one microstructure: the d unit loads solved to tol.
+
+    Returns (x, target, infos); target[b * d + a] = e^(b)_a - delta_ab."""
+    import torch
+
+    d = solver.d
+    fields = []
+    infos = []
+    for b in range(d):
+        E = np.zeros(d)
+        E[b] = 1.0
+        e, _, info = solver.solve(E, tol=tol, method="cg", max_iter=max_iter)
+        fields.append(e)
+        infos.append(info)
+    t = torch.empty((d * d,) + solver.N, dtype=torch.float32, device=solver.dev)
+    fh.nn_targets(fields, t)
+    return features(phase_dev, L), t, infos
+
+
+def start(solver: fh.Solver, pred, E):
+    """x0 = E + Q(sum_b E_b pred_b), device float64 [d][N...]."""
+    import torch
+
+    x0 = torch.empty((solver.d,) + solver.N, dtype=torch.float64, device=solver.dev)
+    return fh.nn_warm_start(solver, pred, E, x0)
+
+
+class WarmStart:
+    """A network for grids N (each a multiple of 27) predicting d unit-load fluctuations."""
+
+    def __init__(self, N: Sequence[int], d: int = 3, channels=None, seed: int = 0):
+        self.N = tuple(int(n) for n in N)
+        self.d = d
+        self.net = fh.Net(self.N, 2, d * d, channels)
+        self.net.set_params(init_params(self.N, d, seed, channels))
+
+    def close(self):
+        self.net.close()
+
+    def train(self, pairs, steps: int, lr: float = 2e-3, lr_final: float = 1e-4, seed: int = 0):
+        """Adam on the mean squared error, one pair per step (order shuffled per
+        epoch), cosine learning-rate decay from lr to lr_final.  Returns the losses."""
+        rng = np.random.default_rng(seed)
+        losses = []
+        order = []
+        for s in range(steps):
+            if not order:
+                order = list(rng.permutation(len(pairs)))
+            x, t = pairs[order.pop()]
+            cur = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * s / max(steps - 1, 1)))
+            losses.append(self.net.train_step(x, t, cur))
+        return losses
+
+    def loss(self, x, t) -> float:
+        return self.net.gradients(x, t)[0]
+
+    def predict(self, x):
+        return self.net.forward(x)
+
+    def solve(self, solver: fh.Solver, pred, E, tol: float = 1e-6, method: str = "cg",
+              max_iter: int = 20000, x0=None):
+        """Solve for load E from the warm start, falling back to e = E when the
+        warm start's true residual is not smaller.  Returns (field, column, info)
+        with info["start"] in {"warm", "cold"} and the two initial residuals."""
+        if x0 is None:
+            x0 = start(solver, pred, E)
+        _, _, probe_w = solver.solve(E, tol=tol, method=method, max_iter=0, e_init=x0, want_field=False)
+        _, _, probe_c = solver.solve(E, tol=tol, method=method, max_iter=0, want_field=False)
+        warm = probe_w["rel_res_true"] < probe_c["rel_res_true"]
+        e, col, info = solver.solve(E, tol=tol, method=method, max_iter=max_iter,
+                                    e_init=x0 if warm else None)
+        info["start"] = "warm" if warm else "cold"
+        info["res0_warm"] = probe_w["rel_res_true"]
+        info["res0_cold"] = probe_c["rel_res_true"]
+        return e, col, info
+
+
+def timed(fn, *args, **kw):
+    """(result, wall seconds) with a device synchronisation on both sides."""
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn(*args, **kw)
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
