@@ -59,7 +59,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+    ap.add_argument("--c5-n", type=int, default=81, help="grid of the warm-start workload (a multiple of 27)")
+    ap.add_argument("--c5-train", type=int, default=200, help="training cells of the warm-start workload")
+    ap.add_argument("--c5-eval", type=int, default=32, help="held-out cells of the warm-start workload")
+    ap.add_argument("--c5-epochs", type=int, default=20, help="training epochs of the warm-start workload")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: 2187^2 contrast sweep (default); c3: 243^3 full tensor; c4: 512-cell sweep")
     ap.add_argument("--probe", action="store_true",
                     help="only time each pass kernel a few times (small command for ncu captures)")
@@ -629,8 +633,132 @@ def run_c3(args):
     print(json.dumps(line), flush=True)
 
 
+def make_c5_cell(n, seed):
+    """3-D two-phase cell: overlapping balls (odd seeds) or randomly oriented
+    ellipsoids (aspect <= 3, even seeds) of size n/27..n/13 to digital volume
+    fraction U[0.1, 0.5], contrast log-U[1e1, 1e4]."""
+    import numpy as np
+
+    from paper_1004_1122_gb300 import microstructure as micro
+
+    r = np.random.default_rng(seed)
+    vf = r.uniform(0.1, 0.5)
+    rho = float(10 ** r.uniform(1.0, 4.0))
+    ph = micro.random_ellipsoids(n, vf, n / 27.0, n / 13.0, 3.0, seed=seed, spheres=bool(seed % 2))
+    return ph, micro.isotropic_table([1.0, rho], 3), rho
+
+
+def run_c5(args):
+    """Learned warm start: train the network on solver-generated unit-load fields
+    of n^3 cells, then solve held-out cells for a random load from the warm start
+    and from e = E (FP32 + FP64 refinement, same tolerance) and count the CG
+    iterations and the time to solution."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1004_1122_gb300 import fh, warmstart
+    from paper_1004_1122_gb300 import microstructure as micro
+
+    n = args.c5_n
+    N3 = (n, n, n)
+    sync = torch.cuda.synchronize
+    # training fields
+    t0 = time.perf_counter()
+    pairs, gen_iters = [], []
+    for k in range(args.c5_train):
+        ph, L, _ = make_c5_cell(n, micro.config_seed(5, k))
+        phd = torch.from_numpy(ph).cuda()
+        s = fh.Solver(phd, L, precision="fp32_refined")
+        x, t, infos = warmstart.training_pair(s, phd, L, tol=TOL, max_iter=MAX_ITER)
+        gen_iters += [i["iters"] for i in infos]
+        pairs.append((x, t))
+        s.close()
+    sync()
+    gen_s = time.perf_counter() - t0
+    ws = warmstart.WarmStart(N3, d=3, seed=micro.config_seed(5, 99999))
+    steps = args.c5_epochs * len(pairs)
+    sync()
+    t0 = time.perf_counter()
+    l0 = ws.net.launches()
+    losses = ws.train(pairs, steps=steps, lr=3e-4)
+    sync()
+    train_s = time.perf_counter() - t0
+    train_launches = ws.net.launches() - l0
+    del pairs
+    # held-out evaluation
+    rng = np.random.default_rng(micro.config_seed(5, 77777))
+    clocks = Clocks(local)
+    clocks.start()
+    rows = []
+    launches = 0
+    for k in range(args.c5_eval):
+        ph, L, rho = make_c5_cell(n, micro.config_seed(5, 100000 + k))
+        phd = torch.from_numpy(ph).cuda()
+        s = fh.Solver(phd, L, precision="fp32_refined")
+        E = rng.normal(size=3)
+        E /= np.linalg.norm(E)
+        sync()
+        t0 = time.perf_counter()
+        _, col_c, ic = s.solve(E, tol=TOL, max_iter=MAX_ITER, want_field=False)
+        sync()
+        t_cold = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        l0 = ws.net.launches()
+        x = ws.features(phd, L, s)
+        pred = ws.predict(x)
+        _, col_w, iw = ws.solve(s, x, pred, E, tol=TOL, max_iter=MAX_ITER)
+        sync()
+        t_warm = time.perf_counter() - t0
+        launches += ic["launches"] + iw["launches"] + ws.net.launches() - l0
+        rows.append(dict(rho=rho, vf=float(micro.digital_fraction(ph)), cold=ic["iters"], warm=iw["iters"],
+                         start=iw["start"], t_cold=t_cold, t_warm=t_warm,
+                         res0=(iw["res0_cold"], iw["res0_warm"]),
+                         dcol=float(np.max(np.abs(col_w - col_c)) / np.max(np.abs(col_c))),
+                         ok=(ic["status"] == "FH_OK" and iw["status"] == "FH_OK")))
+        s.close()
+    clk = clocks.stop()
+    cold = np.array([r["cold"] for r in rows], dtype=float)
+    warm = np.array([r["warm"] for r in rows], dtype=float)
+    tc = sum(r["t_cold"] for r in rows)
+    tw = sum(r["t_warm"] for r in rows)
+    saved = 100.0 * (cold.sum() - warm.sum()) / cold.sum()
+    line = {
+        "metric": "learned warm start: CG iterations saved vs cold start e=E, to true rel.res 1e-6",
+        "value": saved, "unit": "% iterations saved", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": 1e3 * tw / len(rows), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 weights / f32 net; f32 CG (f64 refinement)", "data": "synthetic",
+        "config": {"workload": f"3-D N={n}^3 balls/ellipsoids vf U[0.1,0.5], rho log-U[1e1,1e4]; "
+                               f"{args.c5_train} training cells x 3 unit loads, {args.c5_eval} held-out cells "
+                               f"x 1 random unit load; net 4 levels (16,32,48,64) ch, 11 convs",
+                   "train_steps": steps, "generation_s": gen_s, "train_s": train_s,
+                   "train_ms_per_step": 1e3 * train_s / max(steps, 1), "train_launches": train_launches,
+                   "gen_iters_mean": float(np.mean(gen_iters))},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "warm_start": {"iters_cold_mean": float(cold.mean()), "iters_warm_mean": float(warm.mean()),
+                       "time_cold_ms_mean": 1e3 * tc / len(rows), "time_warm_ms_mean": 1e3 * tw / len(rows),
+                       "time_ratio_cold_over_warm": tc / tw,
+                       "warm_taken": sum(r["start"] == "warm" for r in rows),
+                       "all_converged": all(r["ok"] for r in rows),
+                       "max_rel_diff_Leff_col": max(r["dcol"] for r in rows),
+                       "loss_first": float(np.mean(losses[:len(losses) // 20 + 1])),
+                       "loss_last": float(np.mean(losses[-(len(losses) // 20 + 1):])),
+                       "per_cell": [(round(r["rho"]), r["cold"], r["warm"], r["start"]) for r in rows]},
+    }
+    ws.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "c5" and args.impl != "reference":
+        run_c5(args)
+        return
     if args.probe:
         run_probe()
         return

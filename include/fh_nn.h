@@ -9,14 +9,17 @@
  * with the cold start e = E as fallback.
  *
  * Network (all kernels hand-written, float32 activations, bfloat16-rounded
- * weights, float32 accumulation; levels N, N/3, N/9, N/27; channels c0..c3):
- *   a0 = leaky(conv(x))            a1 = leaky(conv(pool(a0)))
- *   a2 = leaky(conv(pool(a1)))     a3 = leaky(conv(pool(a2)))
- *   u2 = up(leaky(conv(a3))) + a2  u1 = up(leaky(conv(u2))) + a1
- *   u0 = up(leaky(conv(u1))) + a0  y  = conv(u0)
+ * weights, float32 accumulation; levels N, N/3, N/9, N/27; channels c0..c3;
+ * layers 0..10 in parameter order):
+ *   a0 = leaky(conv0(x))            a1 = leaky(conv1(pool(a0)))
+ *   a2 = leaky(conv2(pool(a1)))     a3 = leaky(conv3(pool(a2)))
+ *   v2 = up(leaky(conv4(a3))) + a2  u2 = leaky(conv5(v2))
+ *   v1 = up(leaky(conv6(u2))) + a1  u1 = leaky(conv7(v1))
+ *   v0 = up(leaky(conv8(u1))) + a0  u0 = leaky(conv9(v0))
+ *   y  = conv10(u0)
  * conv: 3x3x3, periodic padding, bias; pool: mean over 3x3x3 blocks; up:
  * nearest-neighbour upsampling by 3; leaky: max(x,0) + 0.1 min(x,0).
- * Parameters are one flat float32 vector: for each of the 8 layers in order,
+ * Parameters are one flat float32 vector: for each of the 11 layers in order,
  * its weights [out][in][27] (taps ordered dz, dy, dx in {-1,0,1}, dx fastest)
  * then its biases [out].
  * Fields are [channels][N0][N1][N2] float32 device arrays.
@@ -70,18 +73,31 @@ void fh_nn_destroy(fh_nn* nn);
 fh_status fh_nn_features(const uint8_t* phase, int nphase, const double* L, int d, long long nodes,
                          float* x, void* stream);
 
+/* First-order response of the cell: x[b*d + a] = (B e_b)_a for the d unit
+ * loads e_b, B = F^-1 Gamma0 F dL of Eq. (mtrx_B), i.e. the fluctuation of
+ * the first fixed-point iterate of Eq. (orig_fft) started at e = e_b (up to
+ * sign).  d products of ctx (float64 where ctx has that pipeline, else
+ * float32).  x: device float32 [d*d][nodes] (nodes = product of ctx's N).
+ * Synchronises the device.  Errors: FH_ERR_ARG, FH_ERR_OOM, FH_ERR_CUDA. */
+fh_status fh_nn_response_features(fh_ctx* ctx, int d, long long nodes, float* x);
+
 /* Training target from the d solved unit-load fields (host array of d device
- * float64 pointers, each [d][nodes]): target[b*d + a] = e^(b)_a - delta_ab,
- * device float32 [d*d][nodes].  Asynchronous. */
-fh_status fh_nn_targets(const double* const* fields, int d, long long nodes, float* target, void* stream);
+ * float64 pointers, each [d][nodes]): target[b*d + a] = e^(b)_a - delta_ab
+ * + base[b*d + a], device float32 [d*d][nodes].  base (device float32
+ * [d*d][nodes], or NULL for zero) is what the network's output is measured
+ * from; with base = fh_nn_response_features the network learns the
+ * correction to the first-order response.  Asynchronous. */
+fh_status fh_nn_targets(const double* const* fields, int d, long long nodes, const float* base, float* target,
+                        void* stream);
 
 /* Warm start for load E (host, d float64) from a prediction pred (device
- * float32 [d*d][nodes], as fh_nn_forward returns): x0 = E + Q(sum_b E_b
- * pred_b) with Q the compatible projection of ctx (fh_project_compatible), so
- * x0 - E lies in the space where CG is justified.  x0: device float64
- * [d][nodes].  Synchronises. */
-fh_status fh_nn_warm_start(fh_ctx* ctx, const float* pred, const double* E, int d, long long nodes,
-                           double* x0, void* stream);
+ * float32 [d*d][nodes], as fh_nn_forward returns) and the same base as the
+ * targets (or NULL): x0 = E + Q(sum_b E_b (pred_b - base_b)) with Q the
+ * compatible projection of ctx (fh_project_compatible), so x0 - E is a
+ * zero-mean compatible field.  x0: device float64 [d][nodes].  Synchronises
+ * the device. */
+fh_status fh_nn_warm_start(fh_ctx* ctx, const float* pred, const float* base, const double* E, int d,
+                           long long nodes, double* x0, void* stream);
 
 #ifdef __cplusplus
 }

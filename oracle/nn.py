@@ -16,15 +16,16 @@ checked element by element:
 * adam  : Kingma & Ba's Adam with bias correction
 * bf16  : round-to-nearest-even float32 -> bfloat16 (weights in the forward)
 
-Architecture (channels c = (16, 32, 48, 64), levels N, N/3, N/9, N/27):
+Architecture (channels c = (16, 32, 48, 64), levels N, N/3, N/9, N/27;
+layers numbered 0..10 in parameter order):
   a0 = leaky(conv3(x; W0))                     c0 at N
   a1 = leaky(conv3(pool3(a0); W1))             c1 at N/3
   a2 = leaky(conv3(pool3(a1); W2))             c2 at N/9
   a3 = leaky(conv3(pool3(a2); W3))             c3 at N/27
-  u2 = up3(leaky(conv3(a3; W4))) + a2          c2 at N/9
-  u1 = up3(leaky(conv3(u2; W5))) + a1          c1 at N/3
-  u0 = up3(leaky(conv3(u1; W6))) + a0          c0 at N
-  y  = conv3(u0; W7)                           cout at N
+  v2 = up3(leaky(conv3(a3; W4))) + a2 ; u2 = leaky(conv3(v2; W5))    c2 at N/9
+  v1 = up3(leaky(conv3(u2; W6))) + a1 ; u1 = leaky(conv3(v1; W7))    c1 at N/3
+  v0 = up3(leaky(conv3(u1; W8))) + a0 ; u0 = leaky(conv3(v0; W9))    c0 at N
+  y  = conv3(u0; W10)                                                cout at N
 
 Pinned by ``tests/test_oracle_nn.py``: the convolution against explicit index
 loops, every backward formula against central finite differences, the
@@ -124,7 +125,9 @@ def adam(param, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 # ---------------------------------------------------------------------------
 def layer_shapes(cin, cout, channels=CHANNELS):
     c0, c1, c2, c3 = channels
-    io = [(cin, c0), (c0, c1), (c1, c2), (c2, c3), (c3, c2), (c2, c1), (c1, c0), (c0, cout)]
+    io = [(cin, c0), (c0, c1), (c1, c2), (c2, c3),
+          (c3, c2), (c2, c2), (c2, c1), (c1, c1), (c1, c0), (c0, c0),
+          (c0, cout)]
     return [(o, i, 27) for (i, o) in io]
 
 
@@ -141,44 +144,42 @@ def init_params(cin, cout, seed, channels=CHANNELS):
 def forward(params, x, round_bf16=True):
     """Returns (y, cache).  Weights are rounded to bfloat16 when round_bf16."""
     W = [(bf16(w) if round_bf16 else w, b) for (w, b) in params]
-    cache = {"x": x, "W": W}
-    z0 = conv3(x, *W[0]); a0 = leaky(z0)
-    p0 = pool3(a0); z1 = conv3(p0, *W[1]); a1 = leaky(z1)
-    p1 = pool3(a1); z2 = conv3(p1, *W[2]); a2 = leaky(z2)
-    p2 = pool3(a2); z3 = conv3(p2, *W[3]); a3 = leaky(z3)
-    z4 = conv3(a3, *W[4]); u2 = up3(leaky(z4)) + a2
-    z5 = conv3(u2, *W[5]); u1 = up3(leaky(z5)) + a1
-    z6 = conv3(u1, *W[6]); u0 = up3(leaky(z6)) + a0
-    y = conv3(u0, *W[7])
-    cache.update(z0=z0, a0=a0, p0=p0, z1=z1, a1=a1, p1=p1, z2=z2, a2=a2, p2=p2, z3=z3, a3=a3,
-                 z4=z4, u2=u2, z5=z5, u1=u1, z6=z6, u0=u0)
-    return y, cache
+    c = {"x": x, "W": W}
+    c["z0"] = conv3(x, *W[0]); c["a0"] = leaky(c["z0"])
+    for l in (1, 2, 3):
+        c[f"p{l - 1}"] = pool3(c[f"a{l - 1}"])
+        c[f"z{l}"] = conv3(c[f"p{l - 1}"], *W[l])
+        c[f"a{l}"] = leaky(c[f"z{l}"])
+    u = c["a3"]
+    for l, (ku, kp) in zip((2, 1, 0), ((4, 5), (6, 7), (8, 9))):
+        c[f"u{l + 1}_in"] = u                      # input of the up convolution
+        c[f"z{ku}"] = conv3(u, *W[ku])
+        c[f"v{l}"] = up3(leaky(c[f"z{ku}"])) + c[f"a{l}"]
+        c[f"z{kp}"] = conv3(c[f"v{l}"], *W[kp])
+        u = leaky(c[f"z{kp}"])
+        c[f"u{l}"] = u
+    y = conv3(u, *W[10])
+    return y, c
 
 
 def backward(cache, gy):
     """Gradients of sum(gy * y) with respect to every (w, b), in layer order."""
     c, W = cache, cache["W"]
-    grads = [None] * 8
-    g_u0, grads[7] = _conv_grads(c["u0"], W[7], gy)
-    g_a0 = g_u0.copy()
-    g_z6 = leaky_backward(c["z6"], up3_backward(g_u0))
-    g_u1, grads[6] = _conv_grads(c["u1"], W[6], g_z6)
-    g_a1 = g_u1.copy()
-    g_z5 = leaky_backward(c["z5"], up3_backward(g_u1))
-    g_u2, grads[5] = _conv_grads(c["u2"], W[5], g_z5)
-    g_a2 = g_u2.copy()
-    g_z4 = leaky_backward(c["z4"], up3_backward(g_u2))
-    g_a3, grads[4] = _conv_grads(c["a3"], W[4], g_z4)
-    g_z3 = leaky_backward(c["z3"], g_a3)
-    g_p2, grads[3] = _conv_grads(c["p2"], W[3], g_z3)
-    g_a2 = g_a2 + pool3_backward(g_p2)
-    g_z2 = leaky_backward(c["z2"], g_a2)
-    g_p1, grads[2] = _conv_grads(c["p1"], W[2], g_z2)
-    g_a1 = g_a1 + pool3_backward(g_p1)
-    g_z1 = leaky_backward(c["z1"], g_a1)
-    g_p0, grads[1] = _conv_grads(c["p0"], W[1], g_z1)
-    g_a0 = g_a0 + pool3_backward(g_p0)
-    g_z0 = leaky_backward(c["z0"], g_a0)
+    grads = [None] * 11
+    g_u, grads[10] = _conv_grads(c["u0"], W[10], gy)
+    g_skip = {}
+    for l, (ku, kp) in zip((0, 1, 2), ((8, 9), (6, 7), (4, 5))):
+        g_zp = leaky_backward(c[f"z{kp}"], g_u)
+        g_v, grads[kp] = _conv_grads(c[f"v{l}"], W[kp], g_zp)
+        g_skip[l] = g_v                            # v_l = up(...) + a_l
+        g_zu = leaky_backward(c[f"z{ku}"], up3_backward(g_v))
+        g_u, grads[ku] = _conv_grads(c[f"u{l + 1}_in"], W[ku], g_zu)
+    g_a = g_u                                      # gradient at a3
+    for l in (3, 2, 1):
+        g_z = leaky_backward(c[f"z{l}"], g_a)
+        g_p, grads[l] = _conv_grads(c[f"p{l - 1}"], W[l], g_z)
+        g_a = g_skip[l - 1] + pool3_backward(g_p)
+    g_z0 = leaky_backward(c["z0"], g_a)
     _, grads[0] = _conv_grads(c["x"], W[0], g_z0)
     return grads
 

@@ -4,11 +4,13 @@
 // Activations are float32 [channels][N0][N1][N2]; weights are kept as float32
 // masters for Adam and rounded to bfloat16 (round to nearest even) for every
 // product; products accumulate in float32.  Architecture (levels N, N/3,
-// N/9, N/27; channels c0..c3):
-//   a0 = leaky(conv(x))            a1 = leaky(conv(pool(a0)))
-//   a2 = leaky(conv(pool(a1)))     a3 = leaky(conv(pool(a2)))
-//   u2 = up(leaky(conv(a3))) + a2  u1 = up(leaky(conv(u2))) + a1
-//   u0 = up(leaky(conv(u1))) + a0  y  = conv(u0)
+// N/9, N/27; channels c0..c3; layers 0..10 in parameter order):
+//   a0 = leaky(conv0(x))            a1 = leaky(conv1(pool(a0)))
+//   a2 = leaky(conv2(pool(a1)))     a3 = leaky(conv3(pool(a2)))
+//   v2 = up(leaky(conv4(a3))) + a2  u2 = leaky(conv5(v2))
+//   v1 = up(leaky(conv6(u2))) + a1  u1 = leaky(conv7(v1))
+//   v0 = up(leaky(conv8(u1))) + a0  u0 = leaky(conv9(v0))
+//   y  = conv10(u0)
 // conv = 3x3x3 with periodic padding (the unit cell is periodic), pool = mean
 // over 3x3x3 blocks, up = nearest-neighbour upsampling by 3.
 #include <cuda_bf16.h>
@@ -282,23 +284,35 @@ __global__ void k_features(const uint8_t* __restrict__ phase, const float* __res
   }
 }
 
-// target[b * d + a] = e^(b)_a - delta_ab  (fields: d loads, each [d][V] float64)
+// target[b * d + a] = e^(b)_a - delta_ab (+ base[b * d + a] if base)
+// (fields: d loads, each [d][V] float64)
 __global__ void k_targets(const double* __restrict__ f0, const double* __restrict__ f1,
-                          const double* __restrict__ f2, int d, float* __restrict__ t, long long V) {
+                          const double* __restrict__ f2, int d, const float* __restrict__ base,
+                          float* __restrict__ t, long long V) {
   const double* f[3] = {f0, f1, f2};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
     for (int b = 0; b < d; ++b)
-      for (int a = 0; a < d; ++a) t[(long long)(b * d + a) * V + i] = (float)(f[b][(long long)a * V + i] - (a == b ? 1.0 : 0.0));
+      for (int a = 0; a < d; ++a) {
+        const long long k = (long long)(b * d + a) * V + i;
+        float v = (float)(f[b][(long long)a * V + i] - (a == b ? 1.0 : 0.0));
+        if (base) v += base[k];
+        t[k] = v;
+      }
 }
 
-// g[a] = sum_b E_b pred[b * d + a]  (fluctuation of load E predicted by the network)
-__global__ void k_combine(const float* __restrict__ pred, int d, double E0, double E1, double E2,
-                          double* __restrict__ g, long long V) {
+// g[a] = sum_b E_b (pred[b * d + a] - base[b * d + a])  (fluctuation of load E
+// predicted by the network; base = the residual base the network was trained
+// against, or null)
+__global__ void k_combine(const float* __restrict__ pred, const float* __restrict__ base, int d, double E0,
+                          double E1, double E2, double* __restrict__ g, long long V) {
   const double E[3] = {E0, E1, E2};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
     for (int a = 0; a < d; ++a) {
       double s = 0.0;
-      for (int b = 0; b < d; ++b) s += E[b] * (double)pred[(long long)(b * d + a) * V + i];
+      for (int b = 0; b < d; ++b) {
+        const long long k = (long long)(b * d + a) * V + i;
+        s += E[b] * ((double)pred[k] - (base ? (double)base[k] : 0.0));
+      }
       g[(long long)a * V + i] = s;
     }
 }
@@ -310,6 +324,20 @@ __global__ void k_add_E(double* __restrict__ x, int d, double E0, double E1, dou
     x[i] += E[i / V];
 }
 
+// e[a][i] = delta_ab: the constant unit load b
+template <typename T>
+__global__ void k_unit_load(T* __restrict__ e, int b, int d, long long V) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)d * V; i += (long long)gridDim.x * blockDim.x)
+    e[i] = (i / V == b) ? T(1) : T(0);
+}
+
+// x[a][i] = y[a][i] - delta_ab  (B e_b from y = (I + B) e_b), as float32
+template <typename T>
+__global__ void k_response(const T* __restrict__ y, int b, int d, float* __restrict__ x, long long V) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)d * V; i += (long long)gridDim.x * blockDim.x)
+    x[i] = (float)(y[i] - ((i / V == b) ? T(1) : T(0)));
+}
+
 int grid1(long long n) {
   const long long g = (n + kThreads - 1) / kThreads;
   return (int)(g < 4096 ? (g < 1 ? 1 : g) : 4096);
@@ -317,19 +345,24 @@ int grid1(long long n) {
 
 }  // namespace
 
+constexpr int kLayers = 11;
+
 struct fh_nn {
   Dims lv[4];
   int cin = 0, cout = 0;
   int ch[4] = {16, 32, 48, 64};
-  int lo[8], li[8], ll[8];     // layer out / in channels, level
-  long long woff[8], boff[8];  // offsets in the flat parameter vector
+  int lo[kLayers], li[kLayers], ll[kLayers];  // layer out / in channels, level
+  long long woff[kLayers], boff[kLayers];      // offsets in the flat parameter vector
   long long nparam = 0;
   cudaStream_t st = nullptr;
   float *P = nullptr, *G = nullptr, *Mo = nullptr, *Ve = nullptr;
   __nv_bfloat16* Wb = nullptr;
-  // activations
-  float *x = nullptr, *z[8] = {}, *a[4] = {}, *pl[3] = {}, *u[3] = {}, *y = nullptr;
-  float *gtmp[2] = {}, *gy = nullptr, *gu[3] = {}, *ga[4] = {}, *gp[3] = {};
+  // forward: pre-activations z[k] (k < 10), encoder a[l], pooled pl[l],
+  // decoder sums v[l] and activations u[l], output y; tmp = leaky(up conv)
+  float *x = nullptr, *z[kLayers - 1] = {}, *a[4] = {}, *pl[3] = {}, *v[3] = {}, *u[3] = {}, *y = nullptr;
+  float* tmp = nullptr;
+  // backward
+  float *gy = nullptr, *gu[3] = {}, *gv[3] = {}, *ga3 = nullptr, *gp[3] = {}, *gt = nullptr;
   double* part = nullptr;
   double* h_part = nullptr;
   int npart = 0;
@@ -390,70 +423,65 @@ void up_bwd(fh_nn* n, const float* f, float* c, int C, Dims cd) {
   k_up_bwd<<<grid1(cd.v() * C), kThreads, 0, n->st>>>(f, c, C, cd);
 }
 
+// decoder level l: (up convolution, post convolution) layer indices
+constexpr int kUp[3] = {8, 6, 4};
+constexpr int kPost[3] = {9, 7, 5};
+
 cudaError_t forward(fh_nn* n) {
   cudaError_t e;
-  const long long V0 = n->lv[0].v(), V1 = n->lv[1].v(), V2 = n->lv[2].v(), V3 = n->lv[3].v();
   ++n->launches;
   k_to_bf16<<<grid1(n->nparam), kThreads, 0, n->st>>>(n->P, n->Wb, n->nparam);
   if ((e = conv(n, 0, n->x, n->z[0], false))) return e;
-  leaky(n, n->z[0], n->a[0], V0 * n->ch[0]);
-  pool(n, n->a[0], n->pl[0], n->ch[0], n->lv[1]);
-  if ((e = conv(n, 1, n->pl[0], n->z[1], false))) return e;
-  leaky(n, n->z[1], n->a[1], V1 * n->ch[1]);
-  pool(n, n->a[1], n->pl[1], n->ch[1], n->lv[2]);
-  if ((e = conv(n, 2, n->pl[1], n->z[2], false))) return e;
-  leaky(n, n->z[2], n->a[2], V2 * n->ch[2]);
-  pool(n, n->a[2], n->pl[2], n->ch[2], n->lv[3]);
-  if ((e = conv(n, 3, n->pl[2], n->z[3], false))) return e;
-  leaky(n, n->z[3], n->a[3], V3 * n->ch[3]);
-  // decoder: z4 at level 3, u2 = up(leaky(z4)) + a2 at level 2 (gtmp[0] holds leaky(z4))
-  if ((e = conv(n, 4, n->a[3], n->z[4], false))) return e;
-  leaky(n, n->z[4], n->gtmp[0], V3 * n->ch[2]);
-  up(n, n->gtmp[0], n->u[2], n->a[2], n->ch[2], n->lv[2], 1.0f, 0);
-  if ((e = conv(n, 5, n->u[2], n->z[5], false))) return e;
-  leaky(n, n->z[5], n->gtmp[0], V2 * n->ch[1]);
-  up(n, n->gtmp[0], n->u[1], n->a[1], n->ch[1], n->lv[1], 1.0f, 0);
-  if ((e = conv(n, 6, n->u[1], n->z[6], false))) return e;
-  leaky(n, n->z[6], n->gtmp[0], V1 * n->ch[0]);
-  up(n, n->gtmp[0], n->u[0], n->a[0], n->ch[0], n->lv[0], 1.0f, 0);
-  if ((e = conv(n, 7, n->u[0], n->y, false))) return e;
+  leaky(n, n->z[0], n->a[0], n->lv[0].v() * n->ch[0]);
+  for (int l = 1; l < 4; ++l) {
+    pool(n, n->a[l - 1], n->pl[l - 1], n->ch[l - 1], n->lv[l]);
+    if ((e = conv(n, l, n->pl[l - 1], n->z[l], false))) return e;
+    leaky(n, n->z[l], n->a[l], n->lv[l].v() * n->ch[l]);
+  }
+  const float* in = n->a[3];
+  for (int l = 2; l >= 0; --l) {
+    const int ku = kUp[l], kp = kPost[l];
+    // v_l = up(leaky(conv_ku(in))) + a_l ; u_l = leaky(conv_kp(v_l))
+    if ((e = conv(n, ku, in, n->z[ku], false))) return e;
+    leaky(n, n->z[ku], n->tmp, n->lv[l + 1].v() * n->ch[l]);
+    up(n, n->tmp, n->v[l], n->a[l], n->ch[l], n->lv[l], 1.0f, 0);
+    if ((e = conv(n, kp, n->v[l], n->z[kp], false))) return e;
+    leaky(n, n->z[kp], n->u[l], n->lv[l].v() * n->ch[l]);
+    in = n->u[l];
+  }
+  if ((e = conv(n, 10, n->u[0], n->y, false))) return e;
   return cudaGetLastError();
 }
 
 // gradients of sum(gy * y) (gy already in n->gy)
 cudaError_t backward(fh_nn* n) {
   cudaError_t e;
-  // layer 7
-  if ((e = wgrad(n, 7, n->u[0], n->gy))) return e;
-  if ((e = conv(n, 7, n->gy, n->gu[0], true))) return e;          // g_u0 (c0, level 0)
-  // u0 = up(leaky(z6)) + a0:  g_a0 = g_u0 ; g_z6 = leaky'(z6) * upT(g_u0)
-  up_bwd(n, n->gu[0], n->gtmp[1], n->ch[0], n->lv[1]);            // c0 at level 1
-  leaky_bwd(n, n->z[6], n->gtmp[1], n->lv[1].v() * n->ch[0]);
-  if ((e = wgrad(n, 6, n->u[1], n->gtmp[1]))) return e;
-  if ((e = conv(n, 6, n->gtmp[1], n->gu[1], true))) return e;      // g_u1 (c1, level 1)
-  up_bwd(n, n->gu[1], n->gtmp[1], n->ch[1], n->lv[2]);            // c1 at level 2
-  leaky_bwd(n, n->z[5], n->gtmp[1], n->lv[2].v() * n->ch[1]);
-  if ((e = wgrad(n, 5, n->u[2], n->gtmp[1]))) return e;
-  if ((e = conv(n, 5, n->gtmp[1], n->gu[2], true))) return e;      // g_u2 (c2, level 2)
-  up_bwd(n, n->gu[2], n->gtmp[1], n->ch[2], n->lv[3]);            // c2 at level 3
-  leaky_bwd(n, n->z[4], n->gtmp[1], n->lv[3].v() * n->ch[2]);
-  if ((e = wgrad(n, 4, n->a[3], n->gtmp[1]))) return e;
-  if ((e = conv(n, 4, n->gtmp[1], n->ga[3], true))) return e;      // g_a3
-  leaky_bwd(n, n->z[3], n->ga[3], n->lv[3].v() * n->ch[3]);        // -> g_z3
-  if ((e = wgrad(n, 3, n->pl[2], n->ga[3]))) return e;
-  if ((e = conv(n, 3, n->ga[3], n->gp[2], true))) return e;        // g_p2 (c2, level 3)
-  // g_a2 = g_u2 + poolT(g_p2)
-  up(n, n->gp[2], n->gu[2], nullptr, n->ch[2], n->lv[2], 1.0f / 27.0f, 1);
-  leaky_bwd(n, n->z[2], n->gu[2], n->lv[2].v() * n->ch[2]);        // -> g_z2
-  if ((e = wgrad(n, 2, n->pl[1], n->gu[2]))) return e;
-  if ((e = conv(n, 2, n->gu[2], n->gp[1], true))) return e;        // g_p1 (c1, level 2)
-  up(n, n->gp[1], n->gu[1], nullptr, n->ch[1], n->lv[1], 1.0f / 27.0f, 1);
-  leaky_bwd(n, n->z[1], n->gu[1], n->lv[1].v() * n->ch[1]);        // -> g_z1
-  if ((e = wgrad(n, 1, n->pl[0], n->gu[1]))) return e;
-  if ((e = conv(n, 1, n->gu[1], n->gp[0], true))) return e;        // g_p0 (c0, level 1)
-  up(n, n->gp[0], n->gu[0], nullptr, n->ch[0], n->lv[0], 1.0f / 27.0f, 1);
-  leaky_bwd(n, n->z[0], n->gu[0], n->lv[0].v() * n->ch[0]);        // -> g_z0
-  if ((e = wgrad(n, 0, n->x, n->gu[0]))) return e;
+  if ((e = wgrad(n, 10, n->u[0], n->gy))) return e;
+  if ((e = conv(n, 10, n->gy, n->gu[0], true))) return e;        // g_u0
+  for (int l = 0; l < 3; ++l) {
+    const int ku = kUp[l], kp = kPost[l];
+    const long long Vl = n->lv[l].v(), Vc = n->lv[l + 1].v();
+    leaky_bwd(n, n->z[kp], n->gu[l], Vl * n->ch[l]);               // -> g_z(post)
+    if ((e = wgrad(n, kp, n->v[l], n->gu[l]))) return e;
+    if ((e = conv(n, kp, n->gu[l], n->gv[l], true))) return e;     // g_v_l (= skip part of g_a_l)
+    up_bwd(n, n->gv[l], n->gt, n->ch[l], n->lv[l + 1]);             // c_l at level l+1
+    leaky_bwd(n, n->z[ku], n->gt, Vc * n->ch[l]);                   // -> g_z(up)
+    const float* up_in = l < 2 ? n->u[l + 1] : n->a[3];
+    if ((e = wgrad(n, ku, up_in, n->gt))) return e;
+    float* g_in = l < 2 ? n->gu[l + 1] : n->ga3;
+    if ((e = conv(n, ku, n->gt, g_in, true))) return e;            // g_u_{l+1} (or g_a3)
+  }
+  // encoder: g_a3 in ga3; g_a_l = g_v_l + poolT(g_p_l)
+  float* g_a = n->ga3;
+  for (int l = 3; l >= 1; --l) {
+    leaky_bwd(n, n->z[l], g_a, n->lv[l].v() * n->ch[l]);          // -> g_z_l
+    if ((e = wgrad(n, l, n->pl[l - 1], g_a))) return e;
+    if ((e = conv(n, l, g_a, n->gp[l - 1], true))) return e;      // g_p_{l-1}
+    up(n, n->gp[l - 1], n->gv[l - 1], nullptr, n->ch[l - 1], n->lv[l - 1], 1.0f / 27.0f, 1);
+    g_a = n->gv[l - 1];
+  }
+  leaky_bwd(n, n->z[0], g_a, n->lv[0].v() * n->ch[0]);            // -> g_z0
+  if ((e = wgrad(n, 0, n->x, g_a))) return e;
   return cudaGetLastError();
 }
 
@@ -505,11 +533,12 @@ fh_status fh_nn_create(fh_nn** out, const int* N, int cin, int cout, const int* 
     for (int k = 0; k < l; ++k) f *= 3;
     n->lv[l] = Dims{N[0] / f, N[1] / f, N[2] / f};
   }
-  const int io[8][3] = {{cin, n->ch[0], 0},        {n->ch[0], n->ch[1], 1}, {n->ch[1], n->ch[2], 2},
-                        {n->ch[2], n->ch[3], 3},   {n->ch[3], n->ch[2], 3}, {n->ch[2], n->ch[1], 2},
-                        {n->ch[1], n->ch[0], 1},   {n->ch[0], cout, 0}};
+  const int c0 = n->ch[0], c1 = n->ch[1], c2 = n->ch[2], c3 = n->ch[3];
+  const int io[kLayers][3] = {{cin, c0, 0}, {c0, c1, 1}, {c1, c2, 2}, {c2, c3, 3},
+                              {c3, c2, 3},  {c2, c2, 2}, {c2, c1, 2}, {c1, c1, 1},
+                              {c1, c0, 1},  {c0, c0, 0}, {c0, cout, 0}};
   long long off = 0;
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < kLayers; ++k) {
     n->li[k] = io[k][0];
     n->lo[k] = io[k][1];
     n->ll[k] = io[k][2];
@@ -522,27 +551,27 @@ fh_status fh_nn_create(fh_nn** out, const int* N, int cin, int cout, const int* 
   n->st = (cudaStream_t)stream;
   int rc = 0;
   const long long V[4] = {n->lv[0].v(), n->lv[1].v(), n->lv[2].v(), n->lv[3].v()};
-  int cmax = cout;
-  for (int k = 0; k < 4; ++k) cmax = std::max(cmax, n->ch[k]);
+  long long coarse_max = 0;  // largest c_l * |level l+1|
+  for (int l = 0; l < 3; ++l) coarse_max = std::max(coarse_max, (long long)n->ch[l] * V[l + 1]);
   rc |= nn_alloc(n, &n->P, off);
   rc |= nn_alloc(n, &n->G, off);
   rc |= nn_alloc(n, &n->Mo, off);
   rc |= nn_alloc(n, &n->Ve, off);
   rc |= nn_alloc(n, &n->Wb, off);
   rc |= nn_alloc(n, &n->x, V[0] * cin);
-  for (int k = 0; k < 4; ++k) rc |= nn_alloc(n, &n->z[k], V[k] * n->ch[k]);
-  rc |= nn_alloc(n, &n->z[4], V[3] * n->ch[2]);
-  rc |= nn_alloc(n, &n->z[5], V[2] * n->ch[1]);
-  rc |= nn_alloc(n, &n->z[6], V[1] * n->ch[0]);
+  for (int k = 0; k < kLayers - 1; ++k) rc |= nn_alloc(n, &n->z[k], V[n->ll[k]] * (long long)n->lo[k]);
   for (int k = 0; k < 4; ++k) rc |= nn_alloc(n, &n->a[k], V[k] * n->ch[k]);
   for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->pl[k], V[k + 1] * n->ch[k]);
+  for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->v[k], V[k] * n->ch[k]);
   for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->u[k], V[k] * n->ch[k]);
   rc |= nn_alloc(n, &n->y, V[0] * cout);
+  rc |= nn_alloc(n, &n->tmp, coarse_max);
   rc |= nn_alloc(n, &n->gy, V[0] * cout);
-  for (int k = 0; k < 2; ++k) rc |= nn_alloc(n, &n->gtmp[k], V[1] * cmax);
   for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->gu[k], V[k] * n->ch[k]);
-  for (int k = 0; k < 4; ++k) rc |= nn_alloc(n, &n->ga[k], V[k] * n->ch[k]);
+  for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->gv[k], V[k] * n->ch[k]);
+  rc |= nn_alloc(n, &n->ga3, V[3] * n->ch[3]);
   for (int k = 0; k < 3; ++k) rc |= nn_alloc(n, &n->gp[k], V[k + 1] * n->ch[k]);
+  rc |= nn_alloc(n, &n->gt, coarse_max);
   n->npart = 4096;
   rc |= nn_alloc(n, &n->part, n->npart);
   if (!rc && cudaMallocHost(&n->h_part, n->npart * sizeof(double)) != cudaSuccess) rc = FH_ERR_OOM;
@@ -643,24 +672,67 @@ fh_status fh_nn_features(const uint8_t* phase, int nphase, const double* L, int 
   return e == cudaSuccess ? FH_OK : FH_ERR_CUDA;
 }
 
-fh_status fh_nn_targets(const double* const* fields, int d, long long nodes, float* target, void* stream) {
+fh_status fh_nn_targets(const double* const* fields, int d, long long nodes, const float* base, float* target,
+                        void* stream) {
   if (!fields || !target || (d != 2 && d != 3)) return FH_ERR_ARG;
   for (int b = 0; b < d; ++b)
     if (!fields[b]) return FH_ERR_ARG;
   k_targets<<<grid1(nodes), kThreads, 0, (cudaStream_t)stream>>>(fields[0], fields[1], d > 2 ? fields[2] : fields[0], d,
-                                                                  target, nodes);
+                                                                  base, target, nodes);
   return cudaGetLastError() == cudaSuccess ? FH_OK : FH_ERR_CUDA;
 }
 
-fh_status fh_nn_warm_start(fh_ctx* ctx, const float* pred, const double* E, int d, long long nodes, double* x0,
-                           void* stream) {
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+fh_status response_features(fh_ctx* ctx, int dtype, int d, long long nodes, float* x) {
+  const long long len = (long long)d * nodes;
+  T* buf = nullptr;
+  if (cudaMalloc((void**)&buf, 2 * len * sizeof(T)) != cudaSuccess) return FH_ERR_OOM;
+  fh_status s = FH_OK;
+  for (int b = 0; b < d && s == FH_OK; ++b) {
+    k_unit_load<T><<<grid1(len), kThreads>>>(buf, b, d, len / d);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+      s = FH_ERR_CUDA;
+      break;
+    }
+    s = fh_apply(ctx, buf, buf + len, 0, dtype);
+    if (s != FH_OK) break;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      s = FH_ERR_CUDA;
+      break;
+    }
+    k_response<T><<<grid1(len), kThreads>>>(buf + len, b, d, x + (long long)b * len, len / d);
+    if (cudaGetLastError() != cudaSuccess) s = FH_ERR_CUDA;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess && s == FH_OK) s = FH_ERR_CUDA;
+  cudaFree(buf);
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+fh_status fh_nn_response_features(fh_ctx* ctx, int d, long long nodes, float* x) {
+  if (!ctx || !x || (d != 2 && d != 3) || nodes < 1) return FH_ERR_ARG;
+  // float64 products where the context has them, else the float32 pipeline
+  fh_status s = response_features<double>(ctx, FH_FP64, d, nodes, x);
+  if (s == FH_ERR_ARG) s = response_features<float>(ctx, FH_FP32, d, nodes, x);
+  return s;
+}
+
+fh_status fh_nn_warm_start(fh_ctx* ctx, const float* pred, const float* base, const double* E, int d,
+                           long long nodes, double* x0, void* stream) {
   if (!ctx || !pred || !E || !x0 || (d != 2 && d != 3)) return FH_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  k_combine<<<grid1(nodes), kThreads, 0, st>>>(pred, d, E[0], E[1], d > 2 ? E[2] : 0.0, x0, nodes);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return FH_ERR_CUDA;
+  k_combine<<<grid1(nodes), kThreads, 0, st>>>(pred, base, d, E[0], E[1], d > 2 ? E[2] : 0.0, x0, nodes);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return FH_ERR_CUDA;
   fh_status s = fh_project_compatible(ctx, x0, x0);
   if (s != FH_OK) return s;
-  cudaDeviceSynchronize();
+  if (cudaDeviceSynchronize() != cudaSuccess) return FH_ERR_CUDA;
   k_add_E<<<grid1((long long)d * nodes), kThreads, 0, st>>>(x0, d, E[0], E[1], d > 2 ? E[2] : 0.0, nodes);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return FH_ERR_CUDA;
   return FH_OK;

@@ -39,7 +39,7 @@ EXPORTS = (
     # fh_nn.h
     "fh_nn_create", "fh_nn_param_count", "fh_nn_launches", "fh_nn_set_params", "fh_nn_get_params",
     "fh_nn_forward", "fh_nn_gradients", "fh_nn_train_step", "fh_nn_destroy", "fh_nn_features",
-    "fh_nn_targets", "fh_nn_warm_start",
+    "fh_nn_targets", "fh_nn_warm_start", "fh_nn_response_features",
 )
 
 
@@ -130,9 +130,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fh_nn_destroy.restype = V
     lib.fh_nn_features.argtypes = [P, I, pD, I, LL, P, P]
     lib.fh_nn_features.restype = I
-    lib.fh_nn_targets.argtypes = [ctypes.POINTER(ctypes.c_void_p), I, LL, P, P]
+    lib.fh_nn_targets.argtypes = [ctypes.POINTER(ctypes.c_void_p), I, LL, P, P, P]
     lib.fh_nn_targets.restype = I
-    lib.fh_nn_warm_start.argtypes = [P, P, pD, I, LL, P, P]
+    lib.fh_nn_response_features.argtypes = [P, I, LL, P]
+    lib.fh_nn_response_features.restype = I
+    lib.fh_nn_warm_start.argtypes = [P, P, P, pD, I, LL, P, P]
     lib.fh_nn_warm_start.restype = I
     lib.fh_autotune.argtypes = [P, I, pD, pD]
     lib.fh_autotune.restype = I
@@ -477,25 +479,37 @@ def nn_features(phase_dev, L, out):
     return out
 
 
-def nn_targets(fields, out):
-    """Training target (d*d channels) from the d solved unit-load fields (float64, device)."""
+def nn_response_features(solver: "Solver", out):
+    """out[b*d + a] = (B e_b)_a, float32 [d*d][N...] on the device."""
+    lib = load_library()
+    rc = lib.fh_nn_response_features(solver.ctx, solver.d, int(np.prod(solver.N)), ctypes.c_void_p(out.data_ptr()))
+    if rc != FH_OK:
+        raise FhError(rc, "fh_nn_response_features")
+    return out
+
+
+def nn_targets(fields, out, base=None):
+    """Training target (d*d channels) from the d solved unit-load fields (float64,
+    device), measured from base (float32 [d*d][N...] or None)."""
     lib = load_library()
     d = len(fields)
     arr = (ctypes.c_void_p * d)(*[f.data_ptr() for f in fields])
     nodes = fields[0].numel() // d
-    rc = lib.fh_nn_targets(arr, d, nodes, ctypes.c_void_p(out.data_ptr()), None)
+    rc = lib.fh_nn_targets(arr, d, nodes, None if base is None else ctypes.c_void_p(base.data_ptr()),
+                           ctypes.c_void_p(out.data_ptr()), None)
     if rc != FH_OK:
         raise FhError(rc, "fh_nn_targets")
     return out
 
 
-def nn_warm_start(solver: "Solver", pred, E, out):
-    """x0 = E + Q(sum_b E_b pred_b): the projected warm start for load E."""
+def nn_warm_start(solver: "Solver", pred, E, out, base=None):
+    """x0 = E + Q(sum_b E_b (pred_b - base_b)): the projected warm start for load E."""
     lib = load_library()
     Eh = np.ascontiguousarray(E, dtype=np.float64)
     nodes = int(np.prod(solver.N))
-    rc = lib.fh_nn_warm_start(solver.ctx, ctypes.c_void_p(pred.data_ptr()), _dptr(Eh), solver.d, nodes,
-                              ctypes.c_void_p(out.data_ptr()), None)
+    rc = lib.fh_nn_warm_start(solver.ctx, ctypes.c_void_p(pred.data_ptr()),
+                              None if base is None else ctypes.c_void_p(base.data_ptr()), _dptr(Eh), solver.d,
+                              nodes, ctypes.c_void_p(out.data_ptr()), None)
     if rc != FH_OK:
         raise FhError(rc, "fh_nn_warm_start")
     return out

@@ -80,7 +80,7 @@ def test_network_backward_finite_differences():
     x = rng.normal(size=(2, 27, 27, 27))
     target = rng.normal(size=(3, 27, 27, 27))
     loss, grads, _ = nn.loss_and_grads(params, x, target, round_bf16=False)
-    for layer in (0, 3, 4, 7):
+    for layer in (0, 2, 3, 4, 5, 8, 9, 10):
         w, b = params[layer]
         f = lambda: nn.loss_and_grads(params, x, target, round_bf16=False)[0]
         idx = rng.choice(w.size, 4, replace=False)
