@@ -37,7 +37,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = glob.glob(os.path.join(CSRC, "*")) + [os.path.join(ROOT, "include", "fh.h"), __file__]
+    deps = glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(ROOT, "include", "*.h")) + [__file__]
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 

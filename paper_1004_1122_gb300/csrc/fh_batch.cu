@@ -284,6 +284,7 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
         if (done[gi]) continue;
         cudaError_t e = cudaStreamSynchronize((*groups[gi]).st);
         if (e != cudaSuccess) return FH_ERR_CUDA;
+        if ((*groups[gi]).p64->device_error()) return FH_ERR_TIMEOUT;
         done[gi] = (*groups[gi]).p64->solve_done();
         all = all && done[gi];
       }
@@ -400,6 +401,7 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
         for (int gi = 0; gi < ng; ++gi) {
           if (!active[gi]) continue;
           if (cudaStreamSynchronize((*groups[gi]).st) != cudaSuccess) return FH_ERR_CUDA;
+          if ((*groups[gi]).p32->device_error()) return FH_ERR_TIMEOUT;
           if ((*groups[gi]).p32->solve_done()) active[gi] = false;
           all = all && !active[gi];
         }

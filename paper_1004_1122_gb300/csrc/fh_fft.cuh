@@ -236,18 +236,38 @@ __device__ __forceinline__ void stockham_stage(cplx<T> (&v)[EM], cplx<T>* sm, in
   constexpr int BM = EM / R;
   static_assert(BM >= 1, "radix exceeds the register budget");
   const int nb = n / R;
-  const int S = n / (Ns * R);
+  const int S = nb / Ns;
+  const int in_step = nb * is, out_step = Ns * is;
+  // j = u + b * nthr = q * Ns + k, advanced without divisions
+  const int dq = nthr / Ns, dk = nthr - dq * Ns;
+  int q0 = u / Ns;
+  int k0 = u - q0 * Ns;
+  int kb[BM], ob[BM];
+  {
+    int q = q0, k = k0;
+#pragma unroll
+    for (int b = 0; b < BM; ++b) {
+      kb[b] = k;
+      ob[b] = (q * R * Ns + k) * is;
+      q += dq;
+      k += dk;
+      if (k >= Ns) { k -= Ns; ++q; }
+    }
+  }
 #pragma unroll
   for (int b = 0; b < BM; ++b) {
     const int j = u + b * nthr;
     if (j < nb) {
+      const C* src = sm + j * is;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b * R + r] = sm[(j + r * nb) * is];
+      for (int r = 0; r < R; ++r) v[b * R + r] = src[r * in_step];
       if (Ns > 1) {
-        const int k = j % Ns;
+        const int ks = kb[b] * S;
+        int ti = ks;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const C w = __ldg(&tw[r * k * S]);
+          const C w = __ldg(tw + ti);
+          ti += ks;
           v[b * R + r] = INV ? cmulc(v[b * R + r], w) : cmul(v[b * R + r], w);
         }
       }
@@ -259,10 +279,9 @@ __device__ __forceinline__ void stockham_stage(cplx<T> (&v)[EM], cplx<T>* sm, in
   for (int b = 0; b < BM; ++b) {
     const int j = u + b * nthr;
     if (j < nb) {
-      const int k = j % Ns;
-      const int base = (j - k) * R + k;
+      C* dst = sm + ob[b];
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[(base + r * Ns) * is] = v[b * R + r];
+      for (int r = 0; r < R; ++r) dst[r * out_step] = v[b * R + r];
     }
   }
   __syncthreads();

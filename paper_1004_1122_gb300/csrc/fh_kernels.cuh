@@ -32,6 +32,7 @@
 #pragma once
 
 #include "fh_fft.cuh"
+#include "fh_tma.cuh"
 
 namespace fh {
 
@@ -41,6 +42,7 @@ constexpr int kMaxChannels = kMaxLoads * kMaxD;
 constexpr int kRedThreads = 256;
 constexpr int kRowMaxThreads = 512;   // row passes: <= 128 registers per thread
 constexpr int kColMaxThreads = 768;   // column passes: <= 85 registers per thread
+constexpr int kColPipeMaxThreads = 512;  // persistent Green pass: <= 128 registers per thread
 
 // ----------------------------------------------------------------------------
 // device scalars of one Krylov solve (one per load)
@@ -147,6 +149,7 @@ template <typename T> struct ColArgs {
   Scal* scal;
   double* part;
   const double* L0cell;  // per-cell reference medium [ncell][9], or nullptr for g.L0
+  int* err;              // device error word (bounded waits that expired), or nullptr
 };
 
 // ----------------------------------------------------------------------------
@@ -162,24 +165,25 @@ __device__ __forceinline__ bool all_done(const Scal* s, int nloads) {
 __device__ __forceinline__ int signed_freq(int j, int n) { return j <= (n - 1) / 2 ? j : j - n; }
 
 // Dot-product accumulator.  float64 work accumulates directly; float32 work
-// sums short runs (at most kRun terms) in float32 and folds each run into a
-// float64 total, so the per-element cost stays on the float32 pipe (float64
-// throughput is ~60x lower on this part) while the total is float64.
+// uses compensated (Kahan) summation in float32, whose error is a few float32
+// ulps of the sum of |terms| whatever the count, and converts to float64 once
+// at the end.  Keeping float64 arithmetic and float32->float64 conversions out
+// of the per-element loop matters on this part: a float64 fold every 32 terms
+// cost the row-inverse pass 35 % and the CG update 25 % (measured, 2187^2).
 template <typename T> struct DotAcc {
   double total = 0.0;
   __device__ __forceinline__ void add(T x) { total += (double)x; }
   __device__ __forceinline__ double get() const { return total; }
 };
 template <> struct DotAcc<float> {
-  static constexpr int kRun = 32;
-  double total = 0.0;
-  float run = 0.0f;
-  int cnt = 0;
+  float s = 0.0f, c = 0.0f;
   __device__ __forceinline__ void add(float x) {
-    run += x;
-    if (++cnt == kRun) { total += (double)run; run = 0.0f; cnt = 0; }
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
   }
-  __device__ __forceinline__ double get() const { return total + (double)run; }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
 
 // Block-wide float64 sum of up to kMaxLoads values; thread 0 writes
@@ -371,6 +375,84 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
 // ----------------------------------------------------------------------------
 enum : int { kColFwd = 0, kColInv = 1, kColGreen = 2, kColEta = 3 };
 
+// Green projection of one column tile held in shared memory (after the
+// forward FFT along axis 0): y^(k) = xi (xi . tau^(k)) / (xi . L0 . xi) / |N|,
+// zero at k = 0 and on padded frequencies (kColGreen), or the equilibrium-norm
+// sums of Eq. (errE_def) (kColEta, into acc).
+template <typename T, int D, int CM_>
+__device__ __forceinline__ void green_tile(const ColArgs<T>& a, cplx<T>* sm, int t, int blk_inner, int cell_idx,
+                                           double (&acc)[2]) {
+  using C = cplx<T>;
+  const ColArgsBase& b = a.b;
+  const Geom& g = b.g;
+  const int n = b.plan.n, Q = b.Q;
+  const int M = g.M;
+  const int ngrp = Q / D;  // groups of D components sharing one frequency
+  T invY[D], L0[D * D];
+#pragma unroll
+  for (int p = 0; p < D; ++p) invY[p] = T(g.invY[p]);
+  const double* L0src = a.L0cell ? a.L0cell + 9 * cell_idx : g.L0;
+#pragma unroll
+  for (int p = 0; p < D; ++p)
+#pragma unroll
+    for (int r = 0; r < D; ++r) L0[p * D + r] = T(L0src[p * 3 + r]);
+  const T inv_nodes = T(g.inv_nodes);
+  for (int idx = threadIdx.x; idx < n * ngrp; idx += blockDim.x) {
+    const int i = idx / ngrp, grp = idx - i * ngrp;
+    const int q0 = grp * D;
+    const int gl = q0 / (g.C * M);
+    const int c = (q0 / M) % g.C;
+    const int kl = t * g.C + c;
+    const int k0 = signed_freq(i, n);
+    const int k1 = D == 2 ? kl : signed_freq(blk_inner * b.G + gl, g.n[1]);
+    T xi[D];
+    xi[0] = T(k0) * invY[0];
+    xi[1] = T(k1) * invY[1];
+    if (D == 3) xi[D - 1] = T(kl) * invY[D - 1];
+    C* v = sm + (size_t)i * Q + q0;
+    const bool pad = kl >= g.H;
+    if (CM_ == kColGreen) {
+      T den = T(0);
+#pragma unroll
+      for (int p = 0; p < D; ++p) {
+        T row = T(0);
+#pragma unroll
+        for (int r = 0; r < D; ++r) row += L0[p * D + r] * xi[r];
+        den += xi[p] * row;
+      }
+      T sre = T(0), sim = T(0);
+#pragma unroll
+      for (int p = 0; p < D; ++p) {
+        sre += xi[p] * v[p].x;
+        sim += xi[p] * v[p].y;
+      }
+      const bool zero = pad || (k0 == 0 && k1 == 0 && kl == 0);
+      const T f = zero ? T(0) : inv_nodes / den;
+#pragma unroll
+      for (int p = 0; p < D; ++p) {
+        v[p].x = xi[p] * sre * f;
+        v[p].y = xi[p] * sim * f;
+      }
+    } else {
+      if (!pad) {
+        double dre = 0.0, dim = 0.0;
+#pragma unroll
+        for (int p = 0; p < D; ++p) {
+          dre += (double)xi[p] * (double)v[p].x;
+          dim += (double)xi[p] * (double)v[p].y;
+        }
+        const double w = kl == 0 ? 1.0 : 2.0;  // half spectrum: k and -k
+        acc[0] += w * (dre * dre + dim * dim);
+        if (k0 == 0 && k1 == 0 && kl == 0) {
+#pragma unroll
+          for (int p = 0; p < D; ++p)
+            acc[1] += (double)v[p].x * v[p].x + (double)v[p].y * v[p].y;
+        }
+      }
+    }
+  }
+}
+
 template <typename T, int D, int CM_>
 __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
   using C = cplx<T>;
@@ -440,73 +522,8 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
     run_fft<true, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
 
   if (CM_ == kColGreen || CM_ == kColEta) {
-    const int M = g.M;
-    const int t = blk_outer;
-    const int ngrp = Q / D;  // groups of D components sharing one frequency
-    T invY[D], L0[D * D];
-#pragma unroll
-    for (int p = 0; p < D; ++p) invY[p] = T(g.invY[p]);
-    const double* L0src = a.L0cell ? a.L0cell + 9 * cell : g.L0;
-#pragma unroll
-    for (int p = 0; p < D; ++p)
-#pragma unroll
-      for (int r = 0; r < D; ++r) L0[p * D + r] = T(L0src[p * 3 + r]);
-    const T inv_nodes = T(g.inv_nodes);
     double acc[2] = {0.0, 0.0};
-    for (int idx = threadIdx.x; idx < n * ngrp; idx += blockDim.x) {
-      const int i = idx / ngrp, grp = idx - i * ngrp;
-      const int q0 = grp * D;
-      const int gl = q0 / (g.C * M);
-      const int c = (q0 / M) % g.C;
-      const int kl = t * g.C + c;
-      const int k0 = signed_freq(i, n);
-      const int k1 = D == 2 ? kl : signed_freq(blk_inner * b.G + gl, g.n[1]);
-      T xi[D];
-      xi[0] = T(k0) * invY[0];
-      xi[1] = T(k1) * invY[1];
-      if (D == 3) xi[D - 1] = T(kl) * invY[D - 1];
-      C* cell = sm + (size_t)i * Q + q0;
-      const bool pad = kl >= g.H;
-      if (CM_ == kColGreen) {
-        T den = T(0);
-#pragma unroll
-        for (int p = 0; p < D; ++p) {
-          T row = T(0);
-#pragma unroll
-          for (int r = 0; r < D; ++r) row += L0[p * D + r] * xi[r];
-          den += xi[p] * row;
-        }
-        T sre = T(0), sim = T(0);
-#pragma unroll
-        for (int p = 0; p < D; ++p) {
-          sre += xi[p] * cell[p].x;
-          sim += xi[p] * cell[p].y;
-        }
-        const bool zero = pad || (k0 == 0 && k1 == 0 && kl == 0);
-        const T f = zero ? T(0) : inv_nodes / den;
-#pragma unroll
-        for (int p = 0; p < D; ++p) {
-          cell[p].x = xi[p] * sre * f;
-          cell[p].y = xi[p] * sim * f;
-        }
-      } else {
-        if (!pad) {
-          double dre = 0.0, dim = 0.0;
-#pragma unroll
-          for (int p = 0; p < D; ++p) {
-            dre += (double)xi[p] * (double)cell[p].x;
-            dim += (double)xi[p] * (double)cell[p].y;
-          }
-          const double w = kl == 0 ? 1.0 : 2.0;  // half spectrum: k and -k
-          acc[0] += w * (dre * dre + dim * dim);
-          if (k0 == 0 && k1 == 0 && kl == 0) {
-#pragma unroll
-            for (int p = 0; p < D; ++p)
-              acc[1] += (double)cell[p].x * cell[p].x + (double)cell[p].y * cell[p].y;
-          }
-        }
-      }
-    }
+    green_tile<T, D, CM_>(a, sm, blk_outer, blk_inner, cell, acc);
     if (CM_ == kColEta) {
       block_reduce_store<2>(acc, 2, a.part, gridDim.x, blockIdx.x);
       return;
@@ -526,6 +543,82 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
       const int i = idx / Q, qq = idx - i * Q;
       if (qq < qvalid) a.S[base + i * b.stride_i + qq] = sm[idx];
     }
+  }
+}
+
+// Persistent, double-buffered Green pass for 2-D grids.  A work item is the
+// spectrum block of one (tile, cell): n rows of Q = C*M complex values, one
+// contiguous, 16-byte aligned range.  One thread moves each block into shared
+// memory with a bulk copy while the CTA transforms the previous block, and
+// writes the result back with a bulk store, so HBM traffic overlaps the FFTs
+// and the grid (one CTA per SM) has no wave tail.
+template <typename T, int D>
+__global__ void __launch_bounds__(kColPipeMaxThreads) k_col_pipe(ColArgs<T> a) {
+  using C = cplx<T>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int s_fail;
+  const ColArgsBase& b = a.b;
+  const Geom& g = b.g;
+  const int n = b.plan.n, Q = b.Q;
+  const uint32_t bytes = (uint32_t)((size_t)n * Q * sizeof(C));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  C* const buf0 = reinterpret_cast<C*>(smem_raw + 128);
+  const size_t bstride = (size_t)n * Q;  // buffer j starts at buf0 + j * bstride
+  const int nitems = g.Tt * b.nb_inner;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    tma::mbar_init(&bar[0], 1);
+    tma::mbar_init(&bar[1], 1);
+    tma::fence_barrier_init();
+    s_fail = 0;
+  }
+  __syncthreads();
+  auto base_of = [&](int w) -> long long {
+    const int t = w / b.nb_inner;
+    return (long long)t * b.base_outer + (long long)(w - t * b.nb_inner) * b.base_inner;
+  };
+  auto issue = [&](int w, int k) {
+    tma::mbar_arrive_expect_tx(&bar[k & 1], bytes);
+    tma::bulk_load(buf0 + (k & 1) * bstride, a.S + base_of(w), bytes, &bar[k & 1]);
+  };
+  const int q = tid % Q;
+  const int u0 = tid / Q;
+  const int u = u0 < b.tpc ? u0 : n;
+  int w = blockIdx.x;
+  if (tid == 0 && w < nitems) issue(w, 0);
+  int k = 0;
+  for (; w < nitems; ++k, w += gridDim.x) {
+    const int wn = w + gridDim.x;
+    if (tid == 0 && wn < nitems) {
+      tma::bulk_wait_read();  // the store of item k-1 has read buffer (k+1)&1
+      issue(wn, k + 1);
+    }
+    if (!tma::mbar_wait(&bar[k & 1], (k >> 1) & 1)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    C* sm = buf0 + (k & 1) * bstride;
+    const int t = w / b.nb_inner, blk_inner = w - t * b.nb_inner;
+    const int cell = g.ncell > 1 ? blk_inner : 0;
+    if (all_done(a.scal ? a.scal + cell * g.nloads : nullptr, g.nloads)) continue;
+    run_fft<false, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+    double acc[2] = {0.0, 0.0};
+    green_tile<T, D, kColGreen>(a, sm, t, blk_inner, cell, acc);
+    __syncthreads();
+    run_fft<true, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+    tma::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tma::bulk_store(a.S + base_of(w), sm, bytes);
+      tma::bulk_commit();
+    }
+  }
+  if (tid == 0) {
+    if (s_fail) {
+      // a load is still owed to the other buffer when the next item existed
+      if (w + gridDim.x < nitems) tma::mbar_wait(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1);
+      if (a.err) atomicExch(a.err, 1);
+    }
+    tma::bulk_wait_all();
   }
 }
 

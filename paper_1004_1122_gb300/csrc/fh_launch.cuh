@@ -20,6 +20,10 @@ struct LaunchTable {
   cudaError_t (*row_fwd)(int pro, const Launch&, const RowArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*row_inv)(int epi, const Launch&, const RowArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*col)(int mode, const Launch&, const ColArgs<T>&, cudaStream_t) = nullptr;
+  // persistent bulk-copy Green pass (2-D only; nullptr otherwise)
+  cudaError_t (*col_pipe)(const Launch&, const ColArgs<T>&, cudaStream_t) = nullptr;
+  cudaError_t (*set_smem_pipe)(size_t bytes) = nullptr;
+  cudaError_t (*occupancy_pipe)(int block, size_t smem, int* per_sm) = nullptr;
   cudaError_t (*cg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*bicg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*current_sum)(const Launch&, const T*, const uint8_t*, const double*, long long nodes,

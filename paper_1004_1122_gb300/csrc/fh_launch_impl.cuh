@@ -80,6 +80,21 @@ struct Launchers {
     }
     return cudaGetLastError();
   }
+  static cudaError_t col_pipe(const Launch& L, const ColArgs<T>& a, cudaStream_t st) {
+    if constexpr (D == 2) {
+      k_col_pipe<T, D><<<L.grid, L.block, L.smem, st>>>(a);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t set_smem_pipe(size_t bytes) {
+    if constexpr (D == 2) return opt_in_smem(k_col_pipe<T, D>, bytes);
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t occupancy_pipe(int block, size_t smem, int* per_sm) {
+    if constexpr (D == 2) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_col_pipe<T, D>, block, smem);
+    return cudaErrorInvalidValue;
+  }
   static cudaError_t cg_update(const Launch& L, const VecArgs<T>& v, cudaStream_t st) {
     k_cg_update<T, NL><<<L.grid, L.block, 0, st>>>(v);
     return cudaGetLastError();
@@ -107,6 +122,11 @@ struct Launchers {
     t.row_fwd = &row_fwd;
     t.row_inv = &row_inv;
     t.col = &col;
+    if (D == 2) {
+      t.col_pipe = &col_pipe;
+      t.set_smem_pipe = &set_smem_pipe;
+      t.occupancy_pipe = &occupancy_pipe;
+    }
     t.cg_update = &cg_update;
     t.bicg_update = &bicg_update;
     t.current_sum = &current_sum;

@@ -310,7 +310,7 @@ extern "C" fh_status fh_apply_noalloc(int d, const int* N, const double* Y, cons
     a.in[l] = e_in;
     a.out[l] = e_out;
   }
-  ColArgs<double> c0, c1;
+  ColArgs<double> c0{}, c1{};
   c0.b = cb0;
   c0.tw = sym.tw + offs[1];
   c0.S = a.S;

@@ -69,6 +69,10 @@ struct Pipeline {
   FFTPlan prow{}, pcol0{}, pcol1{};
   int lpc = 0, tpl = 0, nseq = 0;
   Launch row{}, col0{}, col1{};
+  Launch colp{};              // persistent bulk-copy Green pass (when green_pipe)
+  bool green_pipe = false;
+  int* dev_err = nullptr;     // set by kernels whose bounded waits expired
+  int* h_err = nullptr;       // pinned host mirror, refreshed with the scalars
   ColArgsBase cb0{}, cb1{};
   C* tw_last = nullptr;
   C* tw0 = nullptr;
@@ -120,6 +124,7 @@ struct Pipeline {
   static int autotune(const Problem& pb, int nloads, cudaStream_t stream, Tuning& best, double& ms,
                       std::string& err, int max_candidates = 64);
   void release();
+  bool device_error() const { return h_err != nullptr && *h_err != 0; }
   void set_phase(const uint8_t* d_phase) { phase = d_phase; }
 
   // ---- one application of the operator passes --------------------------
