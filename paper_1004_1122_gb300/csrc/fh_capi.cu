@@ -170,7 +170,8 @@ int to_status(int done) {
 
 // ---- autotuning cache ---------------------------------------------------
 // A plain text file named by the environment variable FH_TUNE_CACHE, one line
-// per problem shape:  <key> C lpc tpl tpc0 tpc1 ms_per_iteration
+// per problem shape:  <key> C lpc tpl tpc0 tpc1 pipe ms_per_iteration
+// (lines without the pipe field read as pipe = 0).
 std::mutex g_cache_mu;
 
 std::string tune_key(const Problem& pb, int nloads, bool f64) {
@@ -190,12 +191,20 @@ bool cache_lookup(const std::string& key, Tuning& t) {
   while (std::getline(f, line)) {
     std::istringstream ls(line);
     std::string k;
+    std::vector<double> v;
+    double x;
+    if (!(ls >> k) || k != key) continue;
+    while (ls >> x) v.push_back(x);
+    if (v.size() != 6 && v.size() != 7) continue;
     Tuning c;
-    double ms;
-    if (ls >> k >> c.C >> c.lpc >> c.tpl >> c.tpc0 >> c.tpc1 >> ms && k == key) {
-      t = c;
-      found = true;  // the last entry for a key wins
-    }
+    c.C = (int)v[0];
+    c.lpc = (int)v[1];
+    c.tpl = (int)v[2];
+    c.tpc0 = (int)v[3];
+    c.tpc1 = (int)v[4];
+    c.pipe = v.size() == 7 ? (int)v[5] : 0;
+    t = c;
+    found = true;  // the last entry for a key wins
   }
   return found;
 }
@@ -205,8 +214,8 @@ void cache_store(const std::string& key, const Tuning& t, double ms) {
   if (!path || !*path) return;
   std::lock_guard<std::mutex> lock(g_cache_mu);
   std::ofstream f(path, std::ios::app);
-  f << key << " " << t.C << " " << t.lpc << " " << t.tpl << " " << t.tpc0 << " " << t.tpc1 << " "
-    << ms << "\n";
+  f << key << " " << t.C << " " << t.lpc << " " << t.tpl << " " << t.tpc0 << " " << t.tpc1 << " " << t.pipe
+    << " " << ms << "\n";
 }
 
 template <typename T>

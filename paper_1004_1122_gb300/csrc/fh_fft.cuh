@@ -321,4 +321,101 @@ __device__ __forceinline__ void run_fft(cplx<T>* sm, int is, const FFTPlan& pl, 
   }
 }
 
+// Forward FFT, a pointwise operation in the frequency domain, and the inverse
+// FFT, with the last forward stage and the first inverse stage fused in
+// registers.  The inverse runs the forward radices in reverse order, so its
+// first stage (Ns = 1) reads exactly the positions j + r n/R the last forward
+// stage produced (Ns = n/R) and no shared-memory round trip or barrier pair is
+// needed in between.  mid(v, i, active) maps the spectrum value at row i; it
+// is called by every thread of the CTA for the same (b, r) sequence, so it may
+// use warp shuffles (inactive threads pass active = false and garbage values).
+template <int R, typename T, int EM, typename F>
+__device__ __forceinline__ void fused_middle(cplx<T> (&v)[EM], cplx<T>* sm, int is, int n, int u, int nthr,
+                                             const cplx<T>* __restrict__ tw, F& mid) {
+  using C = cplx<T>;
+  constexpr int BM = EM / R;
+  const int nb = n / R;  // = Ns of the last forward stage
+  const int in_step = nb * is;
+#pragma unroll
+  for (int b = 0; b < BM; ++b) {
+    const int j = u + b * nthr;
+    if (j < nb) {
+      const C* src = sm + j * is;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b * R + r] = src[r * in_step];
+      if (nb > 1) {
+        int ti = j;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          v[b * R + r] = cmul(v[b * R + r], __ldg(tw + ti));
+          ti += j;
+        }
+      }
+      RegDFT<R, 1, false, T>::run(&v[b * R]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < BM; ++b) {
+    const int j = u + b * nthr;
+    const bool act = j < nb;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b * R + r] = mid(v[b * R + r], j + r * nb, act);
+    if (act) RegDFT<R, 1, true, T>::run(&v[b * R]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BM; ++b) {
+    const int j = u + b * nthr;
+    if (j < nb) {
+      C* dst = sm + j * R * is;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r * is] = v[b * R + r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ void run_fft_fused(cplx<T>* sm, int is, const FFTPlan& pl, int u, int nthr,
+                                              const cplx<T>* __restrict__ tw, F& mid) {
+  constexpr int EM = RegBudget<T>::value;
+  cplx<T> v[EM];
+  const int S = pl.nstages;
+  int Ns = 1;
+  for (int s = 0; s + 1 < S; ++s) {
+    switch (pl.radix[s]) {
+#define FH_STAGE_CASE(RR)                                                                          \
+  case RR:                                                                                         \
+    if constexpr (RR <= EM) stockham_stage<RR, false, T, EM>(v, sm, is, pl.n, Ns, u, nthr, tw); \
+    break;
+      FH_FOR_EACH_RADIX(FH_STAGE_CASE)
+#undef FH_STAGE_CASE
+      default: break;
+    }
+    Ns *= pl.radix[s];
+  }
+  switch (pl.radix[S - 1]) {
+#define FH_MID_CASE(RR)                                                              \
+  case RR:                                                                           \
+    if constexpr (RR <= EM) fused_middle<RR, T, EM>(v, sm, is, pl.n, u, nthr, tw, mid); \
+    break;
+    FH_FOR_EACH_RADIX(FH_MID_CASE)
+#undef FH_MID_CASE
+    default: break;
+  }
+  Ns = pl.radix[S - 1];
+  for (int s = S - 2; s >= 0; --s) {
+    switch (pl.radix[s]) {
+#define FH_STAGE_CASE(RR)                                                                         \
+  case RR:                                                                                        \
+    if constexpr (RR <= EM) stockham_stage<RR, true, T, EM>(v, sm, is, pl.n, Ns, u, nthr, tw); \
+    break;
+      FH_FOR_EACH_RADIX(FH_STAGE_CASE)
+#undef FH_STAGE_CASE
+      default: break;
+    }
+    Ns *= pl.radix[s];
+  }
+}
+
 }  // namespace fh

@@ -375,6 +375,52 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
 // ----------------------------------------------------------------------------
 enum : int { kColFwd = 0, kColInv = 1, kColGreen = 2, kColEta = 3 };
 
+// Green projection of one value of a 2-D spectrum in registers:
+// y_a = xi_a (xi . v) / (xi . L0 . xi) / |N| at (k0, k_last), zero at k = 0 and
+// on padded frequencies.  The caller holds component a = q % 2 of the value;
+// the other component comes from the neighbouring lane (q ^ 1).
+template <typename T>
+struct GreenPoint2 {
+  T invY0, invY1, L00, L01, L10, L11, inv_nodes, xi1;
+  int n, a;
+  bool pad, kl0;
+  __device__ __forceinline__ void init(const Geom& g, const double* L0src, int t, int q, int n_) {
+    const int c = (q / g.M) % g.C;
+    const int kl = t * g.C + c;
+    invY0 = T(g.invY[0]);
+    invY1 = T(g.invY[1]);
+    L00 = T(L0src[0]);
+    L01 = T(L0src[1]);
+    L10 = T(L0src[3]);
+    L11 = T(L0src[4]);
+    inv_nodes = T(g.inv_nodes);
+    xi1 = T(kl) * invY1;
+    n = n_;
+    a = q & 1;
+    pad = kl >= g.H;
+    kl0 = kl == 0;
+  }
+  __device__ __forceinline__ cplx<T> operator()(cplx<T> v, int i, bool act) const {
+    cplx<T> o;
+    o.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
+    o.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
+    const int k0 = i <= (n - 1) / 2 ? i : i - n;
+    const T xi0 = T(k0) * invY0;
+    const cplx<T> v0 = a == 0 ? v : o;
+    const cplx<T> v1 = a == 0 ? o : v;
+    const T den = xi0 * (L00 * xi0 + L01 * xi1) + xi1 * (L10 * xi0 + L11 * xi1);
+    const bool zero = !act || pad || (k0 == 0 && kl0);
+    const T f = zero ? T(0) : inv_nodes / den;
+    const T sre = xi0 * v0.x + xi1 * v1.x;
+    const T sim = xi0 * v0.y + xi1 * v1.y;
+    const T xa = a == 0 ? xi0 : xi1;
+    cplx<T> y;
+    y.x = xa * sre * f;
+    y.y = xa * sim * f;
+    return y;
+  }
+};
+
 // Green projection of one column tile held in shared memory (after the
 // forward FFT along axis 0): y^(k) = xi (xi . tau^(k)) / (xi . L0 . xi) / |N|,
 // zero at k = 0 and on padded frequencies (kColGreen), or the equilibrium-norm
@@ -516,6 +562,16 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
   const int q = threadIdx.x % Q;
   const int u0 = threadIdx.x / Q;
   const int u = u0 < b.tpc ? u0 : n;
+  if constexpr (CM_ == kColGreen && D == 2) {
+    // 2-D: the Green projection runs in registers between the forward and
+    // inverse FFTs.  Q = C * M is even and the two components of a frequency
+    // sit in columns q and q ^ 1, i.e. adjacent lanes of one warp.
+    const int t = blk_outer;
+    const double* L0src = a.L0cell ? a.L0cell + 9 * cell : g.L0;
+    GreenPoint2<T> gp;
+    gp.init(g, L0src, t, q, n);
+    run_fft_fused<T>(sm + q, Q, b.plan, u, b.tpc, a.tw, gp);
+  } else {
   if (CM_ == kColFwd || CM_ == kColGreen || CM_ == kColEta)
     run_fft<false, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
   else
@@ -530,6 +586,7 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
     }
     __syncthreads();
     run_fft<true, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+  }
   }
 
   if (vec) {
@@ -554,6 +611,7 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
 // and the grid (one CTA per SM) has no wave tail.
 template <typename T, int D>
 __global__ void __launch_bounds__(kColPipeMaxThreads) k_col_pipe(ColArgs<T> a) {
+  static_assert(D == 2, "the persistent Green pass is 2-D only");
   using C = cplx<T>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_fail;
@@ -600,11 +658,9 @@ __global__ void __launch_bounds__(kColPipeMaxThreads) k_col_pipe(ColArgs<T> a) {
     const int t = w / b.nb_inner, blk_inner = w - t * b.nb_inner;
     const int cell = g.ncell > 1 ? blk_inner : 0;
     if (all_done(a.scal ? a.scal + cell * g.nloads : nullptr, g.nloads)) continue;
-    run_fft<false, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
-    double acc[2] = {0.0, 0.0};
-    green_tile<T, D, kColGreen>(a, sm, t, blk_inner, cell, acc);
-    __syncthreads();
-    run_fft<true, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+    GreenPoint2<T> gp;
+    gp.init(g, a.L0cell ? a.L0cell + 9 * cell : g.L0, t, q, n);
+    run_fft_fused<T>(sm + q, Q, b.plan, u, b.tpc, a.tw, gp);
     tma::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {

@@ -50,8 +50,9 @@ struct Tuning {
   int tpl = 0;   // threads per line FFT (selects the radix plan)
   int tpc0 = 0;  // threads per column FFT along axis 0
   int tpc1 = 0;  // threads per column FFT along axis 1 (3-D)
+  int pipe = 0;  // 2-D Green pass: 1 = persistent double-buffered bulk-copy kernel
   bool operator==(const Tuning& o) const {
-    return C == o.C && lpc == o.lpc && tpl == o.tpl && tpc0 == o.tpc0 && tpc1 == o.tpc1;
+    return C == o.C && lpc == o.lpc && tpl == o.tpl && tpc0 == o.tpc0 && tpc1 == o.tpc1 && pipe == o.pipe;
   }
 };
 
@@ -122,7 +123,7 @@ struct Pipeline {
   // Time the CG-iteration pass kernels for candidate tunings (temporary
   // pipelines) and return the fastest; `ms` receives its time per iteration.
   static int autotune(const Problem& pb, int nloads, cudaStream_t stream, Tuning& best, double& ms,
-                      std::string& err, int max_candidates = 64);
+                      std::string& err, int max_candidates = 256);
   void release();
   bool device_error() const { return h_err != nullptr && *h_err != 0; }
   void set_phase(const uint8_t* d_phase) { phase = d_phase; }

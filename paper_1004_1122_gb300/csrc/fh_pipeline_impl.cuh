@@ -215,15 +215,14 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
 
   FH_CKS(lt.set_smem(row.smem, col0.smem, d == 3 ? col1.smem : 0));
 
-  // Persistent bulk-copy Green pass (2-D): two tile buffers per CTA, one CTA
-  // per SM slot.  Needs 16-byte aligned, 16-byte multiple blocks.  Selected
-  // by the environment variable FH_GREEN_PIPE=1; the default is the
-  // one-tile-per-CTA kernel, measured faster on 2187^2 (0.076 vs 0.095 ms):
-  // with two 70 KB tiles per CTA only ten warps per SM run the FFTs.
+  // Persistent bulk-copy Green pass (2-D): two tile buffers per CTA, CTAs
+  // sized to the SMs.  Needs 16-byte aligned, 16-byte multiple blocks.  It is
+  // a tuning choice (Tuning::pipe, picked by the autotuner); without a
+  // requested tuning the environment variable FH_GREEN_PIPE=1 selects it.
   green_pipe = false;
   {
     const char* env = std::getenv("FH_GREEN_PIPE");
-    const bool allow = env && env[0] == '1';
+    const bool allow = want ? want->pipe != 0 : (env && env[0] == '1');
     const size_t bytes = (size_t)pb.N[0] * cb0.Q * esz;
     const size_t smem = 128 + 2 * bytes;
     const bool aligned = bytes % 16 == 0 && (cb0.base_outer * esz) % 16 == 0 && (cb0.base_inner * esz) % 16 == 0;
@@ -240,6 +239,7 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     }
     cudaGetLastError();  // clear a refused opt-in
   }
+  tuning.pipe = green_pipe ? 1 : 0;
 
   // device buffers
   int rc;
@@ -837,19 +837,22 @@ int Pipeline<T>::autotune(const Problem& pb, int nloads_, cudaStream_t stream, T
   std::vector<int> tpc0s = plan_tpls(pb.N[0], kColMaxThreads);
   std::vector<int> tpc1s = d == 3 ? plan_tpls(pb.N[1], kColMaxThreads) : std::vector<int>{0};
   std::vector<Tuning> cands;
+  const std::vector<int> pipes = d == 2 ? std::vector<int>{0, 1} : std::vector<int>{0};
   for (int C : {16, 8, 4, 2, 1})
     for (int lpc : {1, 2, 3, 4, 6, 8})
       for (int tp : tpls)
         for (int t0 : tpc0s)
-          for (int t1 : tpc1s) {
-            Tuning c;
-            c.C = C;
-            c.lpc = lpc;
-            c.tpl = tp;
-            c.tpc0 = t0;
-            c.tpc1 = t1;
-            cands.push_back(c);
-          }
+          for (int t1 : tpc1s)
+            for (int pp : pipes) {
+              Tuning c;
+              c.C = C;
+              c.lpc = lpc;
+              c.tpl = tp;
+              c.tpc0 = t0;
+              c.tpc1 = t1;
+              c.pipe = pp;
+              cands.push_back(c);
+            }
   best_ms = 1e30;
   int tried = 0;
   std::string e2;
