@@ -418,4 +418,88 @@ __device__ __forceinline__ void run_fft_fused(cplx<T>* sm, int is, const FFTPlan
   }
 }
 
+// ----------------------------------------------------------------------------
+// compile-time plans
+// ----------------------------------------------------------------------------
+// A plan fixed at compile time: the stage loop is unrolled, every stage size
+// (n, Ns, n/R) is a constant, and only the radices of this plan are compiled
+// into the kernel (the run-time dispatcher above instantiates every radix for
+// both directions, which overflows the instruction cache of a busy SM).
+struct DynPlan {};
+
+template <int... Rs> struct CPlan {
+  static constexpr int S = sizeof...(Rs);
+  static constexpr int r[S] = {Rs...};
+  static constexpr int n = (Rs * ... * 1);
+};
+
+template <typename P> __host__ __device__ constexpr int cplan_prefix(int s) {
+  int p = 1;
+  for (int i = 0; i < s; ++i) p *= P::r[i];
+  return p;
+}
+template <typename P> __host__ __device__ constexpr int cplan_suffix(int s) {
+  int p = 1;
+  for (int i = s; i < P::S; ++i) p *= P::r[i];
+  return p;
+}
+
+// Does the run-time plan pl equal the compile-time plan P?
+template <typename P> inline bool cplan_is(const FFTPlan& pl) {
+  if (pl.n != P::n || pl.nstages != P::S) return false;
+  for (int i = 0; i < P::S; ++i)
+    if (pl.radix[i] != P::r[i]) return false;
+  return true;
+}
+
+template <bool INV, typename T, typename P>
+__device__ __forceinline__ void run_fft_ct(cplx<T>* sm, int is, int u, int nthr, const cplx<T>* __restrict__ tw) {
+  constexpr int EM = RegBudget<T>::value;
+  cplx<T> v[EM];
+  static_for<P::S>([&](auto I) {
+    constexpr int st = decltype(I)::value;
+    constexpr int R = P::r[st];
+    static_assert(R <= EM, "radix exceeds the register budget");
+    stockham_stage<R, INV, T, EM>(v, sm, is, P::n, cplan_prefix<P>(st), u, nthr, tw);
+  });
+}
+
+template <typename T, typename P, typename F>
+__device__ __forceinline__ void run_fft_fused_ct(cplx<T>* sm, int is, int u, int nthr,
+                                                 const cplx<T>* __restrict__ tw, F& mid) {
+  constexpr int EM = RegBudget<T>::value;
+  cplx<T> v[EM];
+  static_for<P::S - 1>([&](auto I) {
+    constexpr int st = decltype(I)::value;
+    stockham_stage<P::r[st], false, T, EM>(v, sm, is, P::n, cplan_prefix<P>(st), u, nthr, tw);
+  });
+  fused_middle<P::r[P::S - 1], T, EM>(v, sm, is, P::n, u, nthr, tw, mid);
+  static_for<P::S - 1>([&](auto I) {
+    constexpr int st = P::S - 2 - decltype(I)::value;
+    stockham_stage<P::r[st], true, T, EM>(v, sm, is, P::n, cplan_suffix<P>(st + 1), u, nthr, tw);
+  });
+}
+
+// Dispatch on the plan kind: DynPlan uses the run-time plan pl.
+template <bool INV, typename T, typename P>
+__device__ __forceinline__ void fft_plan(cplx<T>* sm, int is, const FFTPlan& pl, int u, int nthr,
+                                         const cplx<T>* __restrict__ tw) {
+  if constexpr (std::is_same<P, DynPlan>::value)
+    run_fft<INV, T>(sm, is, pl, u, nthr, tw);
+  else
+    run_fft_ct<INV, T, P>(sm, is, u, nthr, tw);
+}
+
+template <typename T, typename P, typename F>
+__device__ __forceinline__ void fft_fused_plan(cplx<T>* sm, int is, const FFTPlan& pl, int u, int nthr,
+                                               const cplx<T>* __restrict__ tw, F& mid) {
+  if constexpr (std::is_same<P, DynPlan>::value)
+    run_fft_fused<T>(sm, is, pl, u, nthr, tw, mid);
+  else
+    run_fft_fused_ct<T, P>(sm, is, u, nthr, tw, mid);
+}
+
+// The plan of the 3^7 = 2187 axis that the planner picks for 81 threads.
+using Plan2187 = CPlan<27, 27, 3>;
+
 }  // namespace fh

@@ -223,7 +223,7 @@ enum : int {
   kProDirPlain = 3   // p = r + beta p; tau = p
 };
 
-template <typename T, int D, int NL, int PRO>
+template <typename T, int D, int NL, int PRO, typename PS = DynPlan>
 __global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
   {
     const int s = threadIdx.x / a.tpl;
     const int u = s < a.nseq ? threadIdx.x - s * a.tpl : n;  // idle threads never touch smem
-    run_fft<false, T>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
+    fft_plan<false, T, PS>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
   }
 
   // 3. unpack two real spectra per sequence and store the half spectrum:
@@ -499,7 +499,7 @@ __device__ __forceinline__ void green_tile(const ColArgs<T>& a, cplx<T>* sm, int
   }
 }
 
-template <typename T, int D, int CM_>
+template <typename T, int D, int CM_, typename PS = DynPlan>
 __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
     const double* L0src = a.L0cell ? a.L0cell + 9 * cell : g.L0;
     GreenPoint2<T> gp;
     gp.init(g, L0src, t, q, n);
-    run_fft_fused<T>(sm + q, Q, b.plan, u, b.tpc, a.tw, gp);
+    fft_fused_plan<T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw, gp);
   } else {
   if (CM_ == kColFwd || CM_ == kColGreen || CM_ == kColEta)
     run_fft<false, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
 // memory with a bulk copy while the CTA transforms the previous block, and
 // writes the result back with a bulk store, so HBM traffic overlaps the FFTs
 // and the grid (one CTA per SM) has no wave tail.
-template <typename T, int D>
+template <typename T, int D, typename PS = DynPlan>
 __global__ void __launch_bounds__(kColPipeMaxThreads) k_col_pipe(ColArgs<T> a) {
   static_assert(D == 2, "the persistent Green pass is 2-D only");
   using C = cplx<T>;
@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(kColPipeMaxThreads) k_col_pipe(ColArgs<T> a) {
     if (all_done(a.scal ? a.scal + cell * g.nloads : nullptr, g.nloads)) continue;
     GreenPoint2<T> gp;
     gp.init(g, a.L0cell ? a.L0cell + 9 * cell : g.L0, t, q, n);
-    run_fft_fused<T>(sm + q, Q, b.plan, u, b.tpc, a.tw, gp);
+    fft_fused_plan<T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw, gp);
     tma::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
@@ -690,7 +690,7 @@ enum : int {
   kEpiResid = 5     // out = rhs - in - y, dot |out|^2     [residual]
 };
 
-template <typename T, int D, int NL, int EPI>
+template <typename T, int D, int NL, int EPI, typename PS = DynPlan>
 __global__ void __launch_bounds__(kRowMaxThreads) k_row_inv(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -759,7 +759,7 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_inv(RowArgs<T> a) {
   {
     const int s = threadIdx.x / a.tpl;
     const int u = s < a.nseq ? threadIdx.x - s * a.tpl : n;
-    run_fft<true, T>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
+    fft_plan<true, T, PS>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
   }
 
   // 3. epilogue

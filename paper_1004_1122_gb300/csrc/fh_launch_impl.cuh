@@ -2,6 +2,8 @@
 // four fh_launch_*.cu translation units only.
 #pragma once
 
+#include <type_traits>
+
 #include "fh_launch.cuh"
 
 namespace fh {
@@ -25,10 +27,22 @@ static cudaError_t opt_in_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
 }
 
+// Kernels with a compile-time FFT plan are built for float, 2-D, one load
+// per launch and the 2187-point plan: the hot kernels of one CG iteration
+// (direction pass, A p pass, Green pass).  Launches whose run-time plan
+// matches use them; everything else runs the run-time-plan kernels.
+template <typename T, int D, int NL>
+constexpr bool kHasCt = std::is_same<T, float>::value && D == 2 && NL == 1;
+
 template <typename T, int D, int NL>
 struct Launchers {
   static cudaError_t set_smem(size_t rs, size_t c0, size_t c1) {
     cudaError_t e;
+    if constexpr (kHasCt<T, D, NL>) {
+      if ((e = opt_in_smem(k_row_fwd<T, D, NL, kProDir, Plan2187>, rs)) != cudaSuccess) return e;
+      if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, Plan2187>, rs)) != cudaSuccess) return e;
+      if ((e = opt_in_smem(k_col<T, D, kColGreen, Plan2187>, c0)) != cudaSuccess) return e;
+    }
 #define FH_SM(K, B) \
   if ((e = opt_in_smem(K, B)) != cudaSuccess) return e;
     FH_SM((k_row_fwd<T, D, NL, kProApply>), rs)
@@ -49,6 +63,12 @@ struct Launchers {
     return cudaSuccess;
   }
   static cudaError_t row_fwd(int pro, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
+    if constexpr (kHasCt<T, D, NL>) {
+      if (pro == kProDir && cplan_is<Plan2187>(a.plan)) {
+        k_row_fwd<T, D, NL, kProDir, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
+        return cudaGetLastError();
+      }
+    }
     switch (pro) {
       case kProApply: k_row_fwd<T, D, NL, kProApply><<<L.grid, L.block, L.smem, st>>>(a); break;
       case kProPlain: k_row_fwd<T, D, NL, kProPlain><<<L.grid, L.block, L.smem, st>>>(a); break;
@@ -59,6 +79,12 @@ struct Launchers {
     return cudaGetLastError();
   }
   static cudaError_t row_inv(int epi, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
+    if constexpr (kHasCt<T, D, NL>) {
+      if (epi == kEpiDir && cplan_is<Plan2187>(a.plan)) {
+        k_row_inv<T, D, NL, kEpiDir, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
+        return cudaGetLastError();
+      }
+    }
     switch (epi) {
       case kEpiApply: k_row_inv<T, D, NL, kEpiApply><<<L.grid, L.block, L.smem, st>>>(a); break;
       case kEpiApplyT: k_row_inv<T, D, NL, kEpiApplyT><<<L.grid, L.block, L.smem, st>>>(a); break;
@@ -71,6 +97,12 @@ struct Launchers {
     return cudaGetLastError();
   }
   static cudaError_t col(int mode, const Launch& L, const ColArgs<T>& a, cudaStream_t st) {
+    if constexpr (kHasCt<T, D, NL>) {
+      if (mode == kColGreen && cplan_is<Plan2187>(a.b.plan)) {
+        k_col<T, D, kColGreen, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
+        return cudaGetLastError();
+      }
+    }
     switch (mode) {
       case kColFwd: k_col<T, D, kColFwd><<<L.grid, L.block, L.smem, st>>>(a); break;
       case kColInv: k_col<T, D, kColInv><<<L.grid, L.block, L.smem, st>>>(a); break;
@@ -81,6 +113,12 @@ struct Launchers {
     return cudaGetLastError();
   }
   static cudaError_t col_pipe(const Launch& L, const ColArgs<T>& a, cudaStream_t st) {
+    if constexpr (kHasCt<T, D, NL>) {
+      if (cplan_is<Plan2187>(a.b.plan)) {
+        k_col_pipe<T, D, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
+        return cudaGetLastError();
+      }
+    }
     if constexpr (D == 2) {
       k_col_pipe<T, D><<<L.grid, L.block, L.smem, st>>>(a);
       return cudaGetLastError();
@@ -88,6 +126,10 @@ struct Launchers {
     return cudaErrorInvalidValue;
   }
   static cudaError_t set_smem_pipe(size_t bytes) {
+    if constexpr (kHasCt<T, D, NL>) {
+      cudaError_t e = opt_in_smem(k_col_pipe<T, D, Plan2187>, bytes);
+      if (e != cudaSuccess) return e;
+    }
     if constexpr (D == 2) return opt_in_smem(k_col_pipe<T, D>, bytes);
     return cudaErrorInvalidValue;
   }
