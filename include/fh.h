@@ -81,12 +81,17 @@ typedef struct {
                              FH_FP64 and FH_FP32_REFINED, float32 pipeline for FH_FP32) */
   double rel_res;         /* last recursive relative residual of the inner solver */
   double eta_r;           /* Eq. (errR_def) as printed: ||L0 (e_{m+1} - e_m)|| / ||e0|| */
-  double eta_e;           /* Eq. (errE_def) of the returned field (float64) */
+  double eta_e;           /* Eq. (errE_def) of the returned field (float64), when
+                             flags has FH_INFO_ETA_E; NaN otherwise */
   double* history;        /* in: host buffer or NULL */
   int history_cap;        /* in: its capacity */
   int history_len;        /* out: entries written */
   long long launches;     /* out: CUDA kernels this call launched (graph replays included) */
+  int flags;              /* in: FH_INFO_ETA_E requests eta_e (one float64 operator pass) */
 } fh_info;
+
+/* fh_info.flags bits */
+#define FH_INFO_ETA_E 1
 
 /* fh_create -- build a solver context for one microstructure.
  *

@@ -582,7 +582,30 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
     double prev_rel = INFINITY;
     SolveResult res;
     double last_alpha = 0.0, last_inner_b = 0.0;
-    for (;;) {
+    bool done_first = false;
+    if (!e_init) {
+      // From e = E the first correction solves A d = -B E, whose complement
+      // part is zero (B maps into the compatible fields): that is the float32
+      // solve of A x = E from x = E itself, with no float64 residual before it.
+      double eta = 0.3 * tol;
+      if (eta < 2e-6) eta = 2e-6;
+      if (eta > 0.1) eta = 0.1;
+      rc = P->solve(method, Ev, false, fh::kX0Const, nullptr, eta, max_iter, &res, err, nullptr,
+                    kInnerStallWindow);
+      if (rc) return from_rc(c, rc, err);
+      total = res.iters;
+      hist_len = res.iters + 1;
+      last_alpha = res.alpha;
+      ++c->own_launches;
+      k_widen_vec<float><<<vec_grid(len), 256, 0, c->st>>>(P->x[0], c->d_x64, len);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "widen");
+      outer = 1;
+      if (res.status == fh::kBreakdown && res.iters == 0) {
+        status = fh::kBreakdown;
+        done_first = true;
+      }
+    }
+    for (; !done_first;) {
       double rr;
       const double* xin[fh::kMaxLoads] = {c->d_x64};
       double* rout[fh::kMaxLoads] = {c->d_r64};
@@ -666,7 +689,7 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
     info->eta_r = eta_r;
     info->status = st;
     double eta;
-    if (fh_eta_e(c, xfinal, &eta) == FH_OK) info->eta_e = eta;
+    if ((info->flags & FH_INFO_ETA_E) && fh_eta_e(c, xfinal, &eta) == FH_OK) info->eta_e = eta;
     info->matvecs = info->iters * (method == FH_BICG ? 2 : 1) + 1 + info->outer_iters;
     info->launches = c->own_launches + (c->p32 ? c->p32->launches : 0) +
                      (c->p64 ? c->p64->launches : 0) - launches0;

@@ -57,6 +57,7 @@ class FhInfo(ctypes.Structure):
         ("history_cap", ctypes.c_int),
         ("history_len", ctypes.c_int),
         ("launches", ctypes.c_longlong),
+        ("flags", ctypes.c_int),
     ]
 
 
@@ -266,14 +267,17 @@ class Solver:
         return out
 
     def solve(self, E: Sequence[float], tol: float = 1e-8, method: str = "cg", max_iter: int = 10000,
-              e_init=None, out=None, history: int = 0, want_field: bool = True, check: bool = False):
-        """Solve for the load E.  Returns (field or None, L_eff column, info dict)."""
+              e_init=None, out=None, history: int = 0, want_field: bool = True, check: bool = False,
+              eta_e: bool = False):
+        """Solve for the load E.  Returns (field or None, L_eff column, info dict);
+        info["eta_e"] is computed (one float64 pass) only when eta_e is true."""
         torch = self._torch
         Eh = np.ascontiguousarray(E, dtype=np.float64)
         if want_field and out is None:
             out = torch.empty((self.d,) + self.N, dtype=torch.float64, device=self.dev)
         col = np.zeros(self.d)
         info = FhInfo()
+        info.flags = 1 if eta_e else 0
         hist = None
         if history > 0:
             hist = np.zeros(history)

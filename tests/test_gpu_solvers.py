@@ -204,9 +204,11 @@ def test_eta_e_matches_oracle():
     e = rng.normal(size=(2, 45, 45))
     with fh.Solver(phase, L, precision="fp64") as s:
         got = s.eta_e(torch.from_numpy(e).cuda())
-        x, _, info = s.solve([1.0, 0.0], tol=1e-12)
+        x, _, info = s.solve([1.0, 0.0], tol=1e-12, eta_e=True)
+        _, _, info_plain = s.solve([1.0, 0.0], tol=1e-12)
     assert abs(got - oracle.eta_e(e, phase, L)) < 1e-12 * oracle.eta_e(e, phase, L)
     assert info["eta_e"] < 1e-9
+    assert np.isnan(info_plain["eta_e"])
 
 
 def test_invalid_inputs_rejected():
