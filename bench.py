@@ -279,6 +279,39 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+def csrc_digest() -> str:
+    """sha256 over the CUDA sources and public headers (identifies the kernels a
+    recorded ncu capture belongs to)."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1004_1122_gb300", "csrc", "*")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for p in files:
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch (read + write) of `kernel` from the committed ncu
+    summary, or None when the summary was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic_c2_2187_fp32.md")
+    if not os.path.exists(path):
+        return None
+    digest = csrc_digest()
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) == 3 and cells[0] == kernel and cells[1] == digest:
+            try:
+                return int(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
 def spectrum_bytes(n0, n1, d, s):
     return 2 * s * d * ((n1 + 1) // 2) * n0  # half spectrum, complex
 
@@ -396,12 +429,7 @@ def run_fh(args):
     achieved = kern[dom][1] / (times[dom] * 1e-3) / 1e9
     b_min = (2 * d * s4 + 1) * nodes
     b_apply = (d * s4 + 1) * nodes + spec + 2 * spec + spec + 2 * d * s4 * nodes
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tj = json.load(f)
-        traffic = tj.get(dom)
+    traffic = recorded_traffic(dom)
 
     # ---- plain float64 CG on cuFFT (baseline, measured once) ---------------
     base = None
