@@ -42,6 +42,29 @@ constexpr int kMaxChannels = kMaxLoads * kMaxD;
 constexpr int kRedThreads = 256;
 constexpr int kRowMaxThreads = 512;   // row passes: <= 128 registers per thread
 constexpr int kColMaxThreads = 768;   // column passes: <= 85 registers per thread
+// Row kernels with a compile-time plan run one line per 96-thread CTA; their
+// register cap is set for kRowCtBlocks resident CTAs per SM (measured on
+// 2187^2: 7 CTAs beat 6, 8 and 10 -- 49.7 / 43.2 us for the direction and
+// A p passes against 59.6 / 49.6 us at 6 and spills at 10).
+constexpr int kRowCtThreads = 96;
+constexpr int kRowCtBlocks = 7;
+template <typename PS> struct RowBounds {
+  static constexpr int threads = kRowCtThreads, blocks = kRowCtBlocks;
+};
+template <> struct RowBounds<DynPlan> {
+  static constexpr int threads = kRowMaxThreads, blocks = 1;
+};
+// Green-pass kernels with a compile-time plan: kColCtBlocks resident CTAs of
+// at most kColCtThreads threads (measured on 2187^2: a cap for 2 x 352 threads
+// or 3 x 352 threads is slower than the 80-register cap of 768 threads).
+constexpr int kColCtThreads = 768;
+constexpr int kColCtBlocks = 1;
+template <typename PS> struct ColBounds {
+  static constexpr int threads = kColCtThreads, blocks = kColCtBlocks;
+};
+template <> struct ColBounds<DynPlan> {
+  static constexpr int threads = kColMaxThreads, blocks = 1;
+};
 constexpr int kColPipeMaxThreads = 512;  // persistent Green pass: <= 128 registers per thread
 
 // ----------------------------------------------------------------------------
@@ -224,7 +247,7 @@ enum : int {
 };
 
 template <typename T, int D, int NL, int PRO, typename PS = DynPlan>
-__global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
+__global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks) k_row_fwd(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
@@ -260,7 +283,7 @@ __global__ void __launch_bounds__(kRowMaxThreads) k_row_fwd(RowArgs<T> a) {
   // elements per thread are issued before any of them is used, so each thread
   // keeps several global loads in flight (the row pass is latency-bound
   // otherwise).
-  constexpr int kUnroll = 8;
+  constexpr int kUnroll = 4;
   for (int ll = 0; ll < a.lpc; ++ll) {
     const int line = line0 + ll;
     const bool valid = line < g.nlines;
@@ -500,7 +523,7 @@ __device__ __forceinline__ void green_tile(const ColArgs<T>& a, cplx<T>* sm, int
 }
 
 template <typename T, int D, int CM_, typename PS = DynPlan>
-__global__ void __launch_bounds__(kColMaxThreads) k_col(ColArgs<T> a) {
+__global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks) k_col(ColArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
@@ -691,7 +714,7 @@ enum : int {
 };
 
 template <typename T, int D, int NL, int EPI, typename PS = DynPlan>
-__global__ void __launch_bounds__(kRowMaxThreads) k_row_inv(RowArgs<T> a) {
+__global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks) k_row_inv(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);

@@ -64,7 +64,7 @@ struct Launchers {
   }
   static cudaError_t row_fwd(int pro, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
     if constexpr (kHasCt<T, D, NL>) {
-      if (pro == kProDir && cplan_is<Plan2187>(a.plan)) {
+      if (pro == kProDir && L.block <= kRowCtThreads && cplan_is<Plan2187>(a.plan)) {
         k_row_fwd<T, D, NL, kProDir, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
       }
@@ -80,7 +80,7 @@ struct Launchers {
   }
   static cudaError_t row_inv(int epi, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
     if constexpr (kHasCt<T, D, NL>) {
-      if (epi == kEpiDir && cplan_is<Plan2187>(a.plan)) {
+      if (epi == kEpiDir && L.block <= kRowCtThreads && cplan_is<Plan2187>(a.plan)) {
         k_row_inv<T, D, NL, kEpiDir, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
       }
@@ -98,7 +98,7 @@ struct Launchers {
   }
   static cudaError_t col(int mode, const Launch& L, const ColArgs<T>& a, cudaStream_t st) {
     if constexpr (kHasCt<T, D, NL>) {
-      if (mode == kColGreen && cplan_is<Plan2187>(a.b.plan)) {
+      if (mode == kColGreen && L.block <= kColCtThreads && cplan_is<Plan2187>(a.b.plan)) {
         k_col<T, D, kColGreen, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
       }
