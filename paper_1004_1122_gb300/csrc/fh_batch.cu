@@ -47,6 +47,9 @@ __global__ void kb_add(double* x, const float* dx, long long len) {
 // Inner float32 solves stop as stalled after this many iterations without
 // halving their residual (see the single-cell driver).
 constexpr int kInnerStallWindow = 100;
+// absolute residual (relative to |E|) at which the first float32 step hands
+// over to the float64 outer residual
+constexpr double kFirstEta = 1e-3;
 
 int grid_for(long long len) {
   const long long g = (len + 255) / 256;
@@ -356,7 +359,11 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
           } else if (its[gi][it] >= max_iter || (outer > 0 && !(r < 0.9 * prev[gi][it]))) {
             st[gi][it] = fh::kCap;
           } else {
+            // the first step stops at an absolute residual of kFirstEta |E|
+            // (float32 CG tracks float64 CG that far), later steps aim a little
+            // past tol
             double e = 0.3 * tol / r;
+            if (outer == 0) e = std::max(e, kFirstEta / r);
             eta[gi][it] = std::min(0.1, std::max(2e-6, e));
             any = true;
           }

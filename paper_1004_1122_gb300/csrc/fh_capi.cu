@@ -1,6 +1,7 @@
 // fh_capi.cu -- the C ABI of include/fh.h: context creation and validation,
 // the matrix-free product, and the solve drivers (float64, float32, and
 // float32 inner solves with float64 refinement).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -233,6 +234,10 @@ int init_tuned(Pipeline<T>* P, const Problem& pb, bool krylov, cudaStream_t st, 
 // iterations has reached float32's noise floor for its right-hand side; the
 // float64 outer residual then decides whether another refinement step helps.
 constexpr int kInnerStallWindow = 100;
+
+// Relative residual at which the first float32 solve of a refined solve hands
+// over to the float64 outer residual.
+constexpr double kFirstEta = 1e-3;
 
 bool l0_isotropic(const Problem& pb, double& l0) {
   const int d = pb.d;
@@ -587,8 +592,11 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
       // From e = E the first correction solves A d = -B E, whose complement
       // part is zero (B maps into the compatible fields): that is the float32
       // solve of A x = E from x = E itself, with no float64 residual before it.
-      double eta = 0.3 * tol;
-      if (eta < 2e-6) eta = 2e-6;
+      // It stops at kFirstEta (or 0.3 tol if that is looser): float32 CG
+      // tracks float64 CG closely that far, and restarting from the float64
+      // residual there took fewer iterations in total than pushing float32 to
+      // its limit first (2187^2, contrast 1e4: 395 instead of 446).
+      double eta = std::max(0.3 * tol, kFirstEta);
       if (eta > 0.1) eta = 0.1;
       rc = P->solve(method, Ev, false, fh::kX0Const, nullptr, eta, max_iter, &res, err, nullptr,
                     kInnerStallWindow);
