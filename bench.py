@@ -77,6 +77,26 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """Largest x over the ranks of the initialised process group (all_reduce MAX);
+    x itself when there is one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(t_ms_max: float, steps: int, units_per_rank: int, world: int) -> float:
+    """Whole-job time per unit: the slowest rank's time over every unit of every
+    rank (replicas process independent units, no exchange)."""
+    return t_ms_max / (steps * units_per_rank * world)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -372,14 +392,11 @@ def run_fh(args):
     ev1.synchronize()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_ms = ev0.elapsed_time(ev1)
+    t_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     if world > 1:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
         dist.barrier()
     ms_per_step = t_ms / args.steps
-    value = t_ms / (args.steps * nsolve * world)
+    value = replica_value(t_ms, args.steps, nsolve, world)
     launches = sum(i["launches"] for i in infos)
     iters = [i["iters"] for i in infos[:nsolve]]
     outer = [i["outer_iters"] for i in infos[:nsolve]]
@@ -404,12 +421,8 @@ def run_fh(args):
                 d2h += out_host.numel() * 8 + 16
     e1.record(stream)
     e1.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = e2e_ms / (args.steps * nsolve * world)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_value = replica_value(e2e_ms, args.steps, nsolve, world)
 
     # ---- matvec and per-kernel roofline (float32 pipeline, rho = 1e2 context)
     prof = solvers[1]
