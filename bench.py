@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--c5-train", type=int, default=200, help="training cells of the warm-start workload")
     ap.add_argument("--c5-eval", type=int, default=32, help="held-out cells of the warm-start workload")
     ap.add_argument("--c5-epochs", type=int, default=20, help="training epochs of the warm-start workload")
+    ap.add_argument("--c5-lr", type=float, default=3e-4, help="peak Adam learning rate of the warm-start workload")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: 2187^2 contrast sweep (default); c3: 243^3 full tensor; c4: 512-cell sweep")
     ap.add_argument("--probe", action="store_true",
@@ -726,7 +727,7 @@ def run_c5(args):
     sync()
     t0 = time.perf_counter()
     l0 = ws.net.launches()
-    losses = ws.train(pairs, steps=steps, lr=3e-4)
+    losses = ws.train(pairs, steps=steps, lr=args.c5_lr)
     sync()
     train_s = time.perf_counter() - t0
     train_launches = ws.net.launches() - l0
@@ -776,7 +777,7 @@ def run_c5(args):
         "config": {"workload": f"3-D N={n}^3 balls/ellipsoids vf U[0.1,0.5], rho log-U[1e1,1e4]; "
                                f"{args.c5_train} training cells x 3 unit loads, {args.c5_eval} held-out cells "
                                f"x 1 random unit load; net 4 levels (16,32,48,64) ch, 11 convs",
-                   "train_steps": steps, "generation_s": gen_s, "train_s": train_s,
+                   "train_steps": steps, "lr": args.c5_lr, "generation_s": gen_s, "train_s": train_s,
                    "train_ms_per_step": 1e3 * train_s / max(steps, 1), "train_launches": train_launches,
                    "gen_iters_mean": float(np.mean(gen_iters))},
         "clocks": clk,

@@ -632,6 +632,9 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
       // inner tolerance relative to the current residual: aim a little past
       // the target, never below what float32 can resolve
       double eta = 0.3 * tol / rel_true;
+      // a first step from a given initial field far from the solution hands
+      // over at kFirstEta |E| too, as the direct first step from e = E does
+      if (outer == 0 && rel_true > 10.0 * kFirstEta) eta = std::max(eta, kFirstEta / rel_true);
       if (eta < 2e-6) eta = 2e-6;
       if (eta > 0.1) eta = 0.1;
       ++c->own_launches;
