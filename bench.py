@@ -59,11 +59,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
-    ap.add_argument("--c5-n", type=int, default=81, help="grid of the warm-start workload (a multiple of 27)")
+    ap.add_argument("--c5-n", type=int, default=135, help="grid of the warm-start workload (a multiple of 27)")
     ap.add_argument("--c5-train", type=int, default=200, help="training cells of the warm-start workload")
     ap.add_argument("--c5-eval", type=int, default=32, help="held-out cells of the warm-start workload")
     ap.add_argument("--c5-epochs", type=int, default=20, help="training epochs of the warm-start workload")
-    ap.add_argument("--c5-lr", type=float, default=3e-4, help="peak Adam learning rate of the warm-start workload")
+    ap.add_argument("--c5-lr", type=float, default=1e-3, help="peak Adam learning rate of the warm-start workload")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: 2187^2 contrast sweep (default); c3: 243^3 full tensor; c4: 512-cell sweep")
     ap.add_argument("--probe", action="store_true",

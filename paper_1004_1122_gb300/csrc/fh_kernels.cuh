@@ -49,10 +49,10 @@ constexpr int kColMaxThreads = 768;   // column passes: <= 85 registers per thre
 constexpr int kRowCtThreads = 96;
 constexpr int kRowCtBlocks = 7;
 template <typename PS> struct RowBounds {
-  static constexpr int threads = kRowCtThreads, blocks = kRowCtBlocks;
-};
-template <> struct RowBounds<DynPlan> {
   static constexpr int threads = kRowMaxThreads, blocks = 1;
+};
+template <> struct RowBounds<Plan2187> {
+  static constexpr int threads = kRowCtThreads, blocks = kRowCtBlocks;
 };
 // Green-pass kernels with a compile-time plan: kColCtBlocks resident CTAs of
 // at most kColCtThreads threads (measured on 2187^2: a cap for 2 x 352 threads
@@ -596,9 +596,9 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
     fft_fused_plan<T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw, gp);
   } else {
   if (CM_ == kColFwd || CM_ == kColGreen || CM_ == kColEta)
-    run_fft<false, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+    fft_plan<false, T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw);
   else
-    run_fft<true, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+    fft_plan<true, T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw);
 
   if (CM_ == kColGreen || CM_ == kColEta) {
     double acc[2] = {0.0, 0.0};
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
       return;
     }
     __syncthreads();
-    run_fft<true, T>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+    fft_plan<true, T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw);
   }
   }
 

@@ -27,21 +27,29 @@ static cudaError_t opt_in_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
 }
 
-// Kernels with a compile-time FFT plan are built for float, 2-D, one load
-// per launch and the 2187-point plan: the hot kernels of one CG iteration
-// (direction pass, A p pass, Green pass).  Launches whose run-time plan
-// matches use them; everything else runs the run-time-plan kernels.
+// Kernels with a compile-time FFT plan are built for float: 2-D with one load
+// per launch and the 2187-point plan, 3-D (one or three loads) with the
+// 243-point plan.  They are the hot kernels of one CG iteration (direction
+// pass, A p pass, Green pass and, in 3-D, the middle-axis passes).  Launches
+// whose run-time plan matches use them; everything else runs the
+// run-time-plan kernels.
 template <typename T, int D, int NL>
-constexpr bool kHasCt = std::is_same<T, float>::value && D == 2 && NL == 1;
+constexpr bool kHasCt = std::is_same<T, float>::value && ((D == 2 && NL == 1) || D == 3);
+template <int D> using CtPlan = typename std::conditional<D == 2, Plan2187, Plan243>::type;
 
 template <typename T, int D, int NL>
 struct Launchers {
   static cudaError_t set_smem(size_t rs, size_t c0, size_t c1) {
     cudaError_t e;
     if constexpr (kHasCt<T, D, NL>) {
-      if ((e = opt_in_smem(k_row_fwd<T, D, NL, kProDir, Plan2187>, rs)) != cudaSuccess) return e;
-      if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, Plan2187>, rs)) != cudaSuccess) return e;
-      if ((e = opt_in_smem(k_col<T, D, kColGreen, Plan2187>, c0)) != cudaSuccess) return e;
+      using P = CtPlan<D>;
+      if ((e = opt_in_smem(k_row_fwd<T, D, NL, kProDir, P>, rs)) != cudaSuccess) return e;
+      if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, P>, rs)) != cudaSuccess) return e;
+      if ((e = opt_in_smem(k_col<T, D, kColGreen, P>, c0)) != cudaSuccess) return e;
+      if constexpr (D == 3) {
+        if ((e = opt_in_smem(k_col<T, D, kColFwd, P>, c1)) != cudaSuccess) return e;
+        if ((e = opt_in_smem(k_col<T, D, kColInv, P>, c1)) != cudaSuccess) return e;
+      }
     }
 #define FH_SM(K, B) \
   if ((e = opt_in_smem(K, B)) != cudaSuccess) return e;
@@ -64,8 +72,9 @@ struct Launchers {
   }
   static cudaError_t row_fwd(int pro, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
     if constexpr (kHasCt<T, D, NL>) {
-      if (pro == kProDir && L.block <= kRowCtThreads && cplan_is<Plan2187>(a.plan)) {
-        k_row_fwd<T, D, NL, kProDir, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
+      using P = CtPlan<D>;
+      if (pro == kProDir && L.block <= RowBounds<P>::threads && cplan_is<P>(a.plan)) {
+        k_row_fwd<T, D, NL, kProDir, P><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
       }
     }
@@ -80,8 +89,9 @@ struct Launchers {
   }
   static cudaError_t row_inv(int epi, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
     if constexpr (kHasCt<T, D, NL>) {
-      if (epi == kEpiDir && L.block <= kRowCtThreads && cplan_is<Plan2187>(a.plan)) {
-        k_row_inv<T, D, NL, kEpiDir, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
+      using P = CtPlan<D>;
+      if (epi == kEpiDir && L.block <= RowBounds<P>::threads && cplan_is<P>(a.plan)) {
+        k_row_inv<T, D, NL, kEpiDir, P><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
       }
     }
@@ -98,9 +108,22 @@ struct Launchers {
   }
   static cudaError_t col(int mode, const Launch& L, const ColArgs<T>& a, cudaStream_t st) {
     if constexpr (kHasCt<T, D, NL>) {
-      if (mode == kColGreen && L.block <= kColCtThreads && cplan_is<Plan2187>(a.b.plan)) {
-        k_col<T, D, kColGreen, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
-        return cudaGetLastError();
+      using P = CtPlan<D>;
+      if (L.block <= ColBounds<P>::threads && cplan_is<P>(a.b.plan)) {
+        if (mode == kColGreen) {
+          k_col<T, D, kColGreen, P><<<L.grid, L.block, L.smem, st>>>(a);
+          return cudaGetLastError();
+        }
+        if constexpr (D == 3) {
+          if (mode == kColFwd) {
+            k_col<T, D, kColFwd, P><<<L.grid, L.block, L.smem, st>>>(a);
+            return cudaGetLastError();
+          }
+          if (mode == kColInv) {
+            k_col<T, D, kColInv, P><<<L.grid, L.block, L.smem, st>>>(a);
+            return cudaGetLastError();
+          }
+        }
       }
     }
     switch (mode) {
@@ -113,7 +136,7 @@ struct Launchers {
     return cudaGetLastError();
   }
   static cudaError_t col_pipe(const Launch& L, const ColArgs<T>& a, cudaStream_t st) {
-    if constexpr (kHasCt<T, D, NL>) {
+    if constexpr (kHasCt<T, D, NL> && D == 2) {
       if (cplan_is<Plan2187>(a.b.plan)) {
         k_col_pipe<T, D, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
@@ -126,7 +149,7 @@ struct Launchers {
     return cudaErrorInvalidValue;
   }
   static cudaError_t set_smem_pipe(size_t bytes) {
-    if constexpr (kHasCt<T, D, NL>) {
+    if constexpr (kHasCt<T, D, NL> && D == 2) {
       cudaError_t e = opt_in_smem(k_col_pipe<T, D, Plan2187>, bytes);
       if (e != cudaSuccess) return e;
     }
