@@ -30,11 +30,15 @@ CASES_2D = [
     ((15, 15), (1.0, 1.0)),
     ((25, 9), (1.0, 1.0)),
     ((5, 7), (1.0, 1.0)),
+    ((3, 3), (1.0, 1.0)),          # smallest odd grid: one radix-3 stage per axis
+    ((3, 2187), (1.0, 1.0)),       # a single row of tiles along axis 0, long lines
 ]
 CASES_3D = [
     ((9, 15, 27), (1.0, 1.0, 1.0)),
     ((27, 27, 27), (1.0, 0.5, 2.0)),
     ((5, 21, 45), (1.0, 1.0, 1.0)),
+    ((3, 5, 7), (1.0, 1.0, 1.0)),  # smallest mixed-radix 3-D grid
+    ((243, 3, 9), (1.0, 1.0, 1.0)),
 ]
 
 
@@ -153,3 +157,17 @@ def test_autotune_keeps_parity():
     tol = 64 * U["fp32"] * 4 * (1.0 + np.max(np.abs(L - L0[None]))) * np.max(np.abs(e))
     for got in (before, after, again):
         assert np.max(np.abs(got - ref)) <= tol
+
+
+def test_one_node_axis_is_refused():
+    """An axis of one node (a 1-D problem embedded in 2-D) is outside the
+    contract (every axis odd and >= 3): fh_create returns FH_ERR_ARG before any
+    allocation or launch."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = np.zeros((1, 15), dtype=np.uint8)
+    L = micro.isotropic_table([1.0], 2)
+    with pytest.raises(fh.FhError) as ex:
+        fh.Solver(phase, L, precision="fp64")
+    assert ex.value.status == 1  # FH_ERR_ARG
