@@ -10,7 +10,10 @@
  *
  * Network (all kernels hand-written, float32 activations, bfloat16-rounded
  * weights, float32 accumulation; levels N, N/3, N/9, N/27; channels c0..c3;
- * layers 0..10 in parameter order):
+ * layers 0..10 in parameter order).  The forward convolutions and the data
+ * gradients run on the tensor cores (tcgen05, each float32 activation or
+ * gradient split into two bfloat16 halves), the weight gradients on the CUDA
+ * cores:
  *   a0 = leaky(conv0(x))            a1 = leaky(conv1(pool(a0)))
  *   a2 = leaky(conv2(pool(a1)))     a3 = leaky(conv3(pool(a2)))
  *   v2 = up(leaky(conv4(a3))) + a2  u2 = leaky(conv5(v2))
@@ -36,10 +39,11 @@ extern "C" {
 typedef struct fh_nn fh_nn;
 
 /* Create a network for grids N (3 ints, each a multiple of 27), cin input and
- * cout output channels, channels[4] = (c0, c1, c2, c3) or NULL for
- * (16, 32, 48, 64).  Parameters start at zero (set them with
- * fh_nn_set_params).  stream: cudaStream_t or NULL.
- * Errors: FH_ERR_ARG, FH_ERR_OOM, FH_ERR_CUDA. */
+ * cout output channels (each <= 64), channels[4] = (c0, c1, c2, c3), each
+ * <= 64, or NULL for (16, 32, 48, 64).  Parameters start at zero (set them
+ * with fh_nn_set_params).  stream: cudaStream_t or NULL.
+ * Errors: FH_ERR_ARG, FH_ERR_OOM, FH_ERR_CUDA (FH_ERR_TIMEOUT from the
+ * synchronising calls if a tensor-core kernel's bounded wait expired). */
 fh_status fh_nn_create(fh_nn** out, const int* N, int cin, int cout, const int* channels, void* stream);
 
 /* Number of float32 parameters. */

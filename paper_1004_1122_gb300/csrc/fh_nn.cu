@@ -13,6 +13,10 @@
 //   y  = conv10(u0)
 // conv = 3x3x3 with periodic padding (the unit cell is periodic), pool = mean
 // over 3x3x3 blocks, up = nearest-neighbour upsampling by 3.
+// The forward convolutions run on the tensor cores (fh_conv_tc.cuh: tcgen05
+// implicit GEMM, bfloat16 weights, float32 activations split into two
+// bfloat16 halves); the backward ones (data and weight gradients) on the
+// CUDA cores in float32.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -23,6 +27,7 @@
 #include <vector>
 
 #include "../../include/fh_nn.h"
+#include "fh_conv_tc.cuh"
 
 namespace {
 
@@ -269,6 +274,35 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
   }
 }
 
+// Tensor-core weight layout of one layer: wt[o][t * Cp + c] = bf16(w[o][c][t]),
+// zero for o >= O or c >= C (NT rows, 27 * Cp columns).
+__global__ void k_to_bf16_tc(const float* __restrict__ w, int O, int C, int Cp, int NT,
+                             __nv_bfloat16* __restrict__ wt) {
+  const long long n = (long long)NT * 27 * Cp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)(i / (27 * Cp));
+    const int k = (int)(i - (long long)o * 27 * Cp);
+    const int t = k / Cp, c = k - t * Cp;
+    const float v = (o < O && c < C) ? w[((long long)o * C + c) * 27 + t] : 0.0f;
+    wt[i] = __float2bfloat16_rn(v);
+  }
+}
+
+// Transposed layout for the data gradient gx[c] = sum_o sum_t w[o][c][t] gy[o](. - t):
+// wt[c][t * Op + o] = bf16(w[o][c][26 - t]), zero for c >= C or o >= O (NT rows
+// = C padded to 16, 27 * Op columns).
+__global__ void k_to_bf16_tc_t(const float* __restrict__ w, int O, int C, int Op, int NT,
+                               __nv_bfloat16* __restrict__ wt) {
+  const long long n = (long long)NT * 27 * Op;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / (27 * Op));
+    const int k = (int)(i - (long long)c * 27 * Op);
+    const int t = k / Op, o = k - t * Op;
+    const float v = (o < O && c < C) ? w[((long long)o * C + c) * 27 + (26 - t)] : 0.0f;
+    wt[i] = __float2bfloat16_rn(v);
+  }
+}
+
 __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ q, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     q[i] = __float2bfloat16_rn(p[i]);
@@ -357,6 +391,12 @@ struct fh_nn {
   cudaStream_t st = nullptr;
   float *P = nullptr, *G = nullptr, *Mo = nullptr, *Ve = nullptr;
   __nv_bfloat16* Wb = nullptr;
+  __nv_bfloat16* Wtc = nullptr;                 // tensor-core weight layout, all layers
+  __nv_bfloat16* WtcT = nullptr;                // transposed (data-gradient) layout
+  long long wtc_off[kLayers], wtct_off[kLayers];// offsets (multiples of 8 elements)
+  int cpad[kLayers], ntile[kLayers];             // forward: in channels padded to 8, N tile
+  int opad[kLayers], ntile_t[kLayers];           // data gradient: out channels padded to 8, N tile
+  int* dev_err = nullptr;                        // bounded waits that expired
   // forward: pre-activations z[k] (k < 10), encoder a[l], pooled pl[l],
   // decoder sums v[l] and activations u[l], output y; tmp = leaky(up conv)
   float *x = nullptr, *z[kLayers - 1] = {}, *a[4] = {}, *pl[3] = {}, *v[3] = {}, *u[3] = {}, *y = nullptr;
@@ -387,10 +427,26 @@ cudaError_t conv(fh_nn* n, int layer, const float* in, float* out, bool trans) {
   const Dims d = n->lv[n->ll[layer]];
   dim3 grid((unsigned)((d.v() + kThreads - 1) / kThreads), (unsigned)((O + kOC - 1) / kOC));
   ++n->launches;
-  if (trans)
-    k_conv<true><<<grid, kThreads, 0, n->st>>>(in, C, out, O, n->Wb + n->woff[layer], nullptr, d);
-  else
-    k_conv<false><<<grid, kThreads, 0, n->st>>>(in, C, out, O, n->Wb + n->woff[layer], n->P + n->boff[layer], d);
+  (void)grid;
+  {
+    // forward: y = conv(x; W) + b;  data gradient: gx = conv(gy; W^T, taps
+    // reversed), the same implicit GEMM with the transposed weight layout
+    fh::tc::ConvTcArgs ta;
+    ta.x = in;
+    ta.C = C;
+    ta.Cp = trans ? n->opad[layer] : n->cpad[layer];
+    ta.y = out;
+    ta.O = O;
+    ta.NT = trans ? n->ntile_t[layer] : n->ntile[layer];
+    ta.w = trans ? n->WtcT + n->wtct_off[layer] : n->Wtc + n->wtc_off[layer];
+    ta.b = trans ? nullptr : n->P + n->boff[layer];
+    ta.n0 = d.n0;
+    ta.n1 = d.n1;
+    ta.n2 = d.n2;
+    ta.err = n->dev_err;
+    const unsigned g = (unsigned)((d.v() + fh::tc::kM - 1) / fh::tc::kM);
+    fh::tc::k_conv_tc<<<g, fh::tc::kThreads, fh::tc::kSmemBytes, n->st>>>(ta);
+  }
   return cudaGetLastError();
 }
 
@@ -431,6 +487,13 @@ cudaError_t forward(fh_nn* n) {
   cudaError_t e;
   ++n->launches;
   k_to_bf16<<<grid1(n->nparam), kThreads, 0, n->st>>>(n->P, n->Wb, n->nparam);
+  for (int k = 0; k < kLayers; ++k) {
+    n->launches += 2;
+    k_to_bf16_tc<<<grid1((long long)n->ntile[k] * 27 * n->cpad[k]), kThreads, 0, n->st>>>(
+        n->P + n->woff[k], n->lo[k], n->li[k], n->cpad[k], n->ntile[k], n->Wtc + n->wtc_off[k]);
+    k_to_bf16_tc_t<<<grid1((long long)n->ntile_t[k] * 27 * n->opad[k]), kThreads, 0, n->st>>>(
+        n->P + n->woff[k], n->lo[k], n->li[k], n->opad[k], n->ntile_t[k], n->WtcT + n->wtct_off[k]);
+  }
   if ((e = conv(n, 0, n->x, n->z[0], false))) return e;
   leaky(n, n->z[0], n->a[0], n->lv[0].v() * n->ch[0]);
   for (int l = 1; l < 4; ++l) {
@@ -485,6 +548,15 @@ cudaError_t backward(fh_nn* n) {
   return cudaGetLastError();
 }
 
+// true when a kernel's bounded wait expired (synchronises the stream)
+bool device_error(fh_nn* n) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, n->dev_err, sizeof(int), cudaMemcpyDeviceToHost, n->st) != cudaSuccess ||
+      cudaStreamSynchronize(n->st) != cudaSuccess)
+    return true;
+  return h != 0;
+}
+
 int loss_grad(fh_nn* n, const float* target, double* loss) {
   const long long cnt = n->lv[0].v() * n->cout;
   const int g = std::min(n->npart, grid1(cnt));
@@ -496,7 +568,7 @@ int loss_grad(fh_nn* n, const float* target, double* loss) {
   double s = 0.0;
   for (int i = 0; i < g; ++i) s += n->h_part[i];
   if (loss) *loss = s / (double)cnt;
-  return 0;
+  return device_error(n) ? FH_ERR_TIMEOUT : 0;
 }
 
 }  // namespace
@@ -548,6 +620,21 @@ fh_status fh_nn_create(fh_nn** out, const int* N, int cin, int cout, const int* 
     off += n->lo[k];
   }
   n->nparam = off;
+  long long toff = 0, ttoff = 0;
+  for (int k = 0; k < kLayers; ++k) {
+    n->cpad[k] = (n->li[k] + 7) / 8 * 8;
+    n->ntile[k] = (n->lo[k] + 15) / 16 * 16;
+    n->opad[k] = (n->lo[k] + 7) / 8 * 8;
+    n->ntile_t[k] = (n->li[k] + 15) / 16 * 16;
+    n->wtc_off[k] = toff;
+    toff += (long long)n->ntile[k] * 27 * n->cpad[k];
+    n->wtct_off[k] = ttoff;
+    ttoff += (long long)n->ntile_t[k] * 27 * n->opad[k];
+    if (n->ntile[k] > fh::tc::kNmax || n->ntile_t[k] > fh::tc::kNmax) {
+      delete n;
+      return FH_ERR_ARG;  // more than 64 channels on one side of a layer
+    }
+  }
   n->st = (cudaStream_t)stream;
   int rc = 0;
   const long long V[4] = {n->lv[0].v(), n->lv[1].v(), n->lv[2].v(), n->lv[3].v()};
@@ -558,6 +645,9 @@ fh_status fh_nn_create(fh_nn** out, const int* N, int cin, int cout, const int* 
   rc |= nn_alloc(n, &n->Mo, off);
   rc |= nn_alloc(n, &n->Ve, off);
   rc |= nn_alloc(n, &n->Wb, off);
+  rc |= nn_alloc(n, &n->Wtc, toff);
+  rc |= nn_alloc(n, &n->WtcT, ttoff);
+  rc |= nn_alloc(n, &n->dev_err, 1);
   rc |= nn_alloc(n, &n->x, V[0] * cin);
   for (int k = 0; k < kLayers - 1; ++k) rc |= nn_alloc(n, &n->z[k], V[n->ll[k]] * (long long)n->lo[k]);
   for (int k = 0; k < 4; ++k) rc |= nn_alloc(n, &n->a[k], V[k] * n->ch[k]);
@@ -575,7 +665,8 @@ fh_status fh_nn_create(fh_nn** out, const int* N, int cin, int cout, const int* 
   n->npart = 4096;
   rc |= nn_alloc(n, &n->part, n->npart);
   if (!rc && cudaMallocHost(&n->h_part, n->npart * sizeof(double)) != cudaSuccess) rc = FH_ERR_OOM;
-  if (!rc && (cudaMemsetAsync(n->Mo, 0, off * sizeof(float), n->st) != cudaSuccess ||
+  if (!rc && (cudaMemsetAsync(n->dev_err, 0, sizeof(int), n->st) != cudaSuccess ||
+              cudaMemsetAsync(n->Mo, 0, off * sizeof(float), n->st) != cudaSuccess ||
               cudaMemsetAsync(n->Ve, 0, off * sizeof(float), n->st) != cudaSuccess ||
               cudaMemsetAsync(n->P, 0, off * sizeof(float), n->st) != cudaSuccess))
     rc = FH_ERR_CUDA;

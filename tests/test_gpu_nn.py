@@ -1,9 +1,13 @@
 """The warm-start network's kernels against the numpy oracle (oracle/nn.py),
 and the learned warm start against a cold start e = E.
 
-Forward: float32 accumulation against float64 with the same bfloat16-rounded
-weights, max error <= 1e-4 of max |y|.  Gradients: per layer, max error
-<= 2e-3 of the layer's max |g| (two float32 sweeps through eight layers).
+Forward: tensor-core products of the bfloat16 weights with each float32
+activation split into two bfloat16 halves (about 16 mantissa bits kept, error
+<= 2^-17 relative per product) and float32 accumulation, against float64 with
+the same bfloat16-rounded weights: max error <= 1e-4 of max |y| (eleven
+layers of ~2^-17 each), loss within 1e-4 relative.  Gradients: per layer, max
+error <= 2e-3 of the layer's max |g| (float32 backward sweeps through eleven
+layers).
 Features and targets are exact conversions and compared bit for bit.
 """
 import numpy as np
@@ -105,7 +109,7 @@ def test_gradient_parity():
     net.set_params(_flat(params))
     loss, g = net.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(target).cuda())
     ref_loss, ref_grads, _ = onn.loss_and_grads(params, x.astype(np.float64), target.astype(np.float64))
-    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    assert abs(loss - ref_loss) <= 1e-4 * ref_loss
     shapes = onn.layer_shapes(2, 9)
     for layer, ((gw, gb), (rw, rb)) in enumerate(zip(_unflat(g, shapes), ref_grads)):
         scale = max(np.max(np.abs(rw)), np.max(np.abs(rb)))
