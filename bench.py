@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--c5-lr", type=float, default=1e-3, help="peak Adam learning rate of the warm-start workload")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: 2187^2 contrast sweep (default); c3: 243^3 full tensor; c4: 512-cell sweep")
+    ap.add_argument("--probe-nn", action="store_true",
+                    help="a few forward passes and one training step of the warm-start network at 81^3 "
+                         "(for profiler captures)")
     ap.add_argument("--probe", action="store_true",
                     help="only time each pass kernel a few times (small command for ncu captures)")
     return ap.parse_args()
@@ -796,8 +799,41 @@ def run_c5(args):
     print(json.dumps(line), flush=True)
 
 
+def run_probe_nn():
+    """Three forward passes and one training step of the warm-start network
+    (11 input channels, 9 outputs, default channels) on an 81^3 grid."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1004_1122_gb300 import fh, warmstart
+
+    n = 81
+    net = fh.Net((n, n, n), 11, 9)
+    net.set_params(warmstart.init_params(11, 3, seed=1))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((11, n, n, n), device="cuda", generator=g)
+    t = torch.randn((9, n, n, n), device="cuda", generator=g)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    for _ in range(3):
+        net.forward(x)
+    ev[1].record()
+    net.train_step(x, t, 1e-3)
+    ev[2].record()
+    ev[2].synchronize()
+    print(json.dumps({"probe_nn_ms": {"forward": ev[0].elapsed_time(ev[1]) / 3,
+                                      "train_step": ev[1].elapsed_time(ev[2])},
+                      "launches": net.launches()}))
+    net.close()
+
+
 def main():
     args = parse()
+    if args.probe_nn:
+        run_probe_nn()
+        return
     if args.workload == "c5" and args.impl != "reference":
         run_c5(args)
         return
