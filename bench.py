@@ -648,6 +648,10 @@ def run_c3(args):
     gen_s = time.perf_counter() - t0
     L = micro.isotropic_table([1.0, 1e3], 3)
     s = fh.Solver(phase, L, precision="fp32_refined")
+    tune = None
+    if not args.no_tune:
+        before, after = s.autotune(loads=True)
+        tune = {"ms_per_iter_before": before, "ms_per_iter_after": after}
     for _ in range(args.warmup):
         s.solve_all(tol=TOL, max_iter=MAX_ITER)
     clocks = Clocks(local)
@@ -669,6 +673,7 @@ def run_c3(args):
         "vs_baseline": None, "dtype": "f32 (f64 refinement)", "data": "synthetic",
         "config": {"workload": "3-D N=243^3 Boolean spheres r=12 vf>=0.25, rho=1e3, loads e1,e2,e3 batched",
                    "vf": float(micro.digital_fraction(phase)), "generation_s": gen_s},
+        "autotune": tune,
         "clocks": clk,
         "gpu_launches": sum(i["launches"] for i in infos[:1]) * args.steps,
         "solver": {"iters": [i["iters"] for i in infos], "outer_iters": infos[0]["outer_iters"],

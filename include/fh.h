@@ -199,6 +199,15 @@ fh_status fh_profile(fh_ctx* ctx, int dtype, int what, int reps, double* ms);
  * Synchronises.  Errors: FH_ERR_ARG, FH_ERR_OOM, FH_ERR_CUDA, FH_ERR_UNSUPPORTED. */
 fh_status fh_autotune(fh_ctx* ctx, int dtype, double* ms_before, double* ms_after);
 
+/* fh_autotune_loads -- the same search for the pipeline of fh_solve_all,
+ * which carries all d unit loads in every launch (float32; FH_FP32 and
+ * FH_FP32_REFINED contexts).  The best shapes are appended to the tuning
+ * cache under this grid with d loads, and the next fh_solve_all uses them.
+ * ms_before / ms_after (host, or NULL): float32 CG-iteration time of the
+ * default and of the chosen shapes.  Errors: FH_ERR_ARG (FH_FP64 context),
+ * FH_ERR_OOM, FH_ERR_CUDA. */
+fh_status fh_autotune_loads(fh_ctx* ctx, double* ms_before, double* ms_after);
+
 /* ---- Batches of independent 2-D cells (serving-style sweeps) ------------
  *
  * fh_batch_create -- many independent 2-D cells, possibly of different odd

@@ -556,7 +556,21 @@ int solve_all_loads(const Problem& pb, int precision, double tol, int method, in
     }
     if (!rc && precision != FH_FP64) {
       g->p32 = new (std::nothrow) Pipeline<float>();
-      rc = g->p32 ? g->p32->init(pb, d, true, g->st, err) : FH_ERR_OOM;
+      if (!g->p32) {
+        rc = FH_ERR_OOM;
+      } else {
+        // launch shapes tuned for d loads per launch (fh_autotune_loads), else the defaults
+        Tuning t;
+        rc = -1;
+        if (tuning_from_cache(pb, d, false, t)) {
+          rc = g->p32->init(pb, d, true, g->st, err, &t);
+          if (rc) {
+            g->p32->release();
+            *g->p32 = Pipeline<float>();
+          }
+        }
+        if (rc) rc = g->p32->init(pb, d, true, g->st, err);
+      }
     }
     for (int l = 0; l < d && !rc; ++l)
       if (cudaMalloc(&g->x64[l], (size_t)d * pb.nodes * sizeof(double)) != cudaSuccess ||

@@ -219,6 +219,16 @@ void cache_store(const std::string& key, const Tuning& t, double ms) {
     << " " << ms << "\n";
 }
 
+}  // namespace
+
+namespace fh {
+bool tuning_from_cache(const Problem& pb, int nloads, bool f64, Tuning& t) {
+  return cache_lookup(tune_key(pb, nloads, f64), t);
+}
+}  // namespace fh
+
+namespace {
+
 template <typename T>
 int init_tuned(Pipeline<T>* P, const Problem& pb, bool krylov, cudaStream_t st, std::string& err) {
   Tuning t;
@@ -846,6 +856,36 @@ fh_status fh_autotune(fh_ctx* c, int dtype, double* ms_before, double* ms_after)
   if (dtype == FH_FP64 && c->p64 && c->p64->x[0])
     return autotune_one<double>(c, c->p64, true, ms_before, ms_after);
   return fail(c, FH_ERR_ARG, "no Krylov pipeline of that precision in this context");
+}
+
+fh_status fh_autotune_loads(fh_ctx* c, double* ms_before, double* ms_after) {
+  if (!c) return FH_ERR_ARG;
+  if (c->precision == FH_FP64) return fail(c, FH_ERR_ARG, "the all-loads float32 pipeline needs FH_FP32 or FH_FP32_REFINED");
+  const int d = c->pb.d;
+  std::string err;
+  // the default shapes' time, from a temporary pipeline
+  double before = 0.0, t;
+  {
+    fh::Pipeline<float> P;
+    int rc = P.init(c->pb, d, true, c->st, err);
+    for (int what = 0; what < 4 && !rc; ++what) {
+      rc = P.profile(what, 10, &t, err);
+      before += t;
+    }
+    P.release();
+    if (rc) return from_rc(c, rc, err);
+  }
+  Tuning best;
+  double best_ms;
+  int rc = fh::Pipeline<float>::autotune(c->pb, d, c->st, best, best_ms, err);
+  if (rc) return from_rc(c, rc, err);
+  cache_store(tune_key(c->pb, d, false), best, best_ms);
+  // the next fh_solve_all rebuilds its pipelines with the tuned shapes
+  fh::release_loads_group(c->loads_group);
+  c->loads_group = nullptr;
+  if (ms_before) *ms_before = before;
+  if (ms_after) *ms_after = best_ms;
+  return FH_OK;
 }
 
 fh_status fh_effective_column(fh_ctx* c, const double* e, double* col) {

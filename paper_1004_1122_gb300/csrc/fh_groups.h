@@ -25,4 +25,8 @@ int solve_all_loads(const Problem& pb, int precision, double tol, int method, in
                     double* Leff, LoadsResult& res, void** cache, std::string& err);
 void release_loads_group(void* cache);
 
+// The launch shapes recorded in the tuning cache (FH_TUNE_CACHE) for this
+// problem with nloads loads per launch, if any.
+bool tuning_from_cache(const Problem& pb, int nloads, bool f64, Tuning& t);
+
 }  // namespace fh

@@ -34,7 +34,7 @@ DT_FP64, DT_FP32 = 0, 1
 EXPORTS = (
     "fh_create", "fh_set_phase", "fh_apply", "fh_solve", "fh_solve_all", "fh_effective_column",
     "fh_eta_e", "fh_profile", "fh_autotune", "fh_apply_noalloc", "fh_batch_create", "fh_batch_solve",
-    "fh_batch_last_error", "fh_batch_destroy", "fh_project_compatible", "fh_destroy", "fh_status_string", "fh_last_error",
+    "fh_batch_last_error", "fh_batch_destroy", "fh_project_compatible", "fh_autotune_loads", "fh_destroy", "fh_status_string", "fh_last_error",
     "fh_version",
     # fh_nn.h
     "fh_nn_create", "fh_nn_param_count", "fh_nn_launches", "fh_nn_set_params", "fh_nn_get_params",
@@ -137,6 +137,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fh_nn_response_features.restype = I
     lib.fh_nn_warm_start.argtypes = [P, P, P, pD, I, LL, P, P]
     lib.fh_nn_warm_start.restype = I
+    lib.fh_autotune_loads.argtypes = [P, pD, pD]
+    lib.fh_autotune_loads.restype = I
     lib.fh_autotune.argtypes = [P, I, pD, pD]
     lib.fh_autotune.restype = I
     lib.fh_apply_noalloc.argtypes = [I, pI, pD, P, I, pD, pD, P, P, I, P, ctypes.c_char_p, ctypes.c_size_t]
@@ -308,11 +310,15 @@ class Solver:
                                         int(reps), _dptr(v)), "fh_profile")
         return float(v[0])
 
-    def autotune(self, dtype: str = "fp32"):
-        """Pick the fastest launch shapes (fh_autotune); returns (ms_before, ms_after)."""
+    def autotune(self, dtype: str = "fp32", loads: bool = False):
+        """Pick the fastest launch shapes (fh_autotune, or fh_autotune_loads for the
+        all-loads pipeline of solve_all); returns (ms_before, ms_after)."""
         b, a = np.zeros(1), np.zeros(1)
-        self._check(self.lib.fh_autotune(self.ctx, DT_FP64 if dtype == "fp64" else DT_FP32, _dptr(b), _dptr(a)),
-                    "fh_autotune")
+        if loads:
+            self._check(self.lib.fh_autotune_loads(self.ctx, _dptr(b), _dptr(a)), "fh_autotune_loads")
+        else:
+            self._check(self.lib.fh_autotune(self.ctx, DT_FP64 if dtype == "fp64" else DT_FP32, _dptr(b),
+                                             _dptr(a)), "fh_autotune")
         return float(b[0]), float(a[0])
 
     def project_compatible(self, f, out=None):

@@ -245,10 +245,12 @@ def test_fp32_refined_reaches_tight_tolerance_on_noise_dominated_corrections(N, 
 
 
 @pytest.mark.parametrize("prec,tol,bar", [("fp64", 1e-12, 1e-10), ("fp32_refined", 1e-10, 1e-6)])
-def test_3d_full_tensor_loads_batched(prec, tol, bar):
+def test_3d_full_tensor_loads_batched(prec, tol, bar, tmp_path, monkeypatch):
     """Config-3 path at a small size: all three unit loads in every launch
-    (fh_solve_all), Boolean spheres, against three oracle solves."""
+    (fh_solve_all), Boolean spheres, against three oracle solves; for float32
+    + refinement also after tuning the all-loads pipeline (fh_autotune_loads)."""
     torch = cuda_or_skip()
+    monkeypatch.setenv("FH_TUNE_CACHE", str(tmp_path / "tune.txt"))
     from paper_1004_1122_gb300 import fh
 
     phase = micro.boolean_spheres(27, 3.0, 0.25, seed=micro.config_seed(3, 2))
@@ -258,6 +260,15 @@ def test_3d_full_tensor_loads_batched(prec, tol, bar):
     Lo = oracle.effective_tensor(xs, phase, L)
     with fh.Solver(phase, L, precision=prec) as s:
         Le, infos = s.solve_all(tol=tol, max_iter=20000)
+        tuned = None
+        if prec == "fp32_refined":
+            # tune the all-loads pipeline (tuning cache in a temporary file), solve again
+            before, after = s.autotune(loads=True)
+            assert after <= before * 1.05
+            tuned, tinfos = s.solve_all(tol=tol, max_iter=20000)
+            assert all(i["status"] == "FH_OK" for i in tinfos), tinfos
     assert all(i["status"] == "FH_OK" for i in infos), infos
     assert np.max(np.abs(Le - Lo)) / np.max(np.abs(Lo)) < bar
     assert np.max(np.abs(Le - Le.T)) < 10 * bar * np.max(np.abs(Lo))
+    if tuned is not None:
+        assert np.max(np.abs(tuned - Lo)) / np.max(np.abs(Lo)) < bar
