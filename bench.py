@@ -589,6 +589,11 @@ def run_c4(args):
     gen_s = time.perf_counter() - t0
     nodes = sum(c[2] * c[2] for c in cells)
     b = fh.Batch([c[0] for c in cells], [c[1] for c in cells], nloads=2, precision="fp32_refined")
+    tune = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        before, after = b.autotune()
+        tune = {"ms_per_iter_before": before, "ms_per_iter_after": after, "s": time.perf_counter() - t0}
     E = np.eye(2)
     for _ in range(args.warmup):
         b.solve(E, tol=TOL, method="cg", max_iter=MAX_ITER)
@@ -616,6 +621,7 @@ def run_c4(args):
         "config": {"workload": f"{len(cells)} 2-D cells, N in {C4_SIZES}, disks/ellipses/laminates vf 0.3, "
                                f"rho log-U[1e1,1e4], 2 loads, CG fp32 + fp64 refinement to {TOL:g}",
                    "total_nodes": nodes, "generation_s": gen_s},
+        "autotune": tune,
         "clocks": clk,
         "dof_iter_per_s": float(np.sum(iters * np.repeat([c[2] * c[2] * 2 for c in cells], 2)))
                           / (t_ms / args.steps * 1e-3),

@@ -249,6 +249,14 @@ fh_status fh_batch_create(fh_batch** out, int ncells, const int* N, const uint8_
 fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, int max_iter,
                          double* Leff, int* status, int* iters, fh_info* summary);
 
+/* fh_batch_autotune -- pick the launch shapes of every size group's float32
+ * pipeline (FH_FP32_REFINED batches) by timing a bounded set of candidates
+ * on the group itself, as fh_autotune does for one cell.  ms_before /
+ * ms_after (host, or NULL): the summed float32 CG-iteration time of all
+ * groups before and after.  Synchronises.  Errors: FH_ERR_ARG, FH_ERR_OOM,
+ * FH_ERR_CUDA. */
+fh_status fh_batch_autotune(fh_batch* b, double* ms_before, double* ms_after);
+
 /* Last error message of a batch (never NULL). */
 const char* fh_batch_last_error(const fh_batch* b);
 

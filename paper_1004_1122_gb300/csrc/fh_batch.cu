@@ -44,6 +44,10 @@ __global__ void kb_add(double* x, const float* dx, long long len) {
        i += (long long)gridDim.x * blockDim.x)
     x[i] += (double)dx[i];
 }
+// Candidate launch shapes timed per size group by fh_batch_autotune (each
+// candidate builds a full pipeline for the group, so the search is bounded).
+constexpr int kBatchTuneCandidates = 48;
+
 // Inner float32 solves stop as stalled after this many iterations without
 // halving their residual (see the single-cell driver).
 constexpr int kInnerStallWindow = 100;
@@ -235,6 +239,55 @@ fh_status fh_batch_create(fh_batch** out, int ncells, const int* N, const uint8_
     }
   }
   *out = b;
+  return FH_OK;
+}
+
+fh_status fh_batch_autotune(fh_batch* b, double* ms_before, double* ms_after) {
+  if (!b) return FH_ERR_ARG;
+  double before = 0.0, after = 0.0;
+  for (Group& g : b->groups) {
+    if (!g.p32) continue;  // float64 batches keep their default shapes
+    std::string err;
+    double t, cur = 0.0;
+    for (int what = 0; what < 4; ++what) {
+      int rc = g.p32->profile(what, 10, &t, err);
+      if (rc) {
+        b->err = err;
+        return (fh_status)rc;
+      }
+      cur += t;
+    }
+    fh::Tuning best;
+    double best_ms;
+    int rc = Pipeline<float>::autotune(g.pb, b->nloads, g.st, best, best_ms, err, kBatchTuneCandidates);
+    if (rc) {
+      b->err = err;
+      return (fh_status)rc;
+    }
+    before += cur;
+    if (best_ms < cur && !(best == g.p32->tuning)) {
+      cudaStreamSynchronize(g.st);
+      g.p32->release();
+      *g.p32 = Pipeline<float>();
+      rc = g.p32->init(g.pb, b->nloads, true, g.st, err, &best);
+      if (rc) {
+        // fall back to the default shapes
+        g.p32->release();
+        *g.p32 = Pipeline<float>();
+        rc = g.p32->init(g.pb, b->nloads, true, g.st, err);
+        if (rc) {
+          b->err = err;
+          return (fh_status)rc;
+        }
+        best_ms = cur;
+      }
+      after += best_ms;
+    } else {
+      after += cur;
+    }
+  }
+  if (ms_before) *ms_before = before;
+  if (ms_after) *ms_after = after;
   return FH_OK;
 }
 

@@ -34,7 +34,8 @@ DT_FP64, DT_FP32 = 0, 1
 EXPORTS = (
     "fh_create", "fh_set_phase", "fh_apply", "fh_solve", "fh_solve_all", "fh_effective_column",
     "fh_eta_e", "fh_profile", "fh_autotune", "fh_apply_noalloc", "fh_batch_create", "fh_batch_solve",
-    "fh_batch_last_error", "fh_batch_destroy", "fh_project_compatible", "fh_autotune_loads", "fh_destroy", "fh_status_string", "fh_last_error",
+    "fh_batch_last_error", "fh_batch_destroy", "fh_project_compatible", "fh_autotune_loads",
+    "fh_batch_autotune", "fh_destroy", "fh_status_string", "fh_last_error",
     "fh_version",
     # fh_nn.h
     "fh_nn_create", "fh_nn_param_count", "fh_nn_launches", "fh_nn_set_params", "fh_nn_get_params",
@@ -137,6 +138,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fh_nn_response_features.restype = I
     lib.fh_nn_warm_start.argtypes = [P, P, P, pD, I, LL, P, P]
     lib.fh_nn_warm_start.restype = I
+    lib.fh_batch_autotune.argtypes = [P, pD, pD]
+    lib.fh_batch_autotune.restype = I
     lib.fh_autotune_loads.argtypes = [P, pD, pD]
     lib.fh_autotune_loads.restype = I
     lib.fh_autotune.argtypes = [P, I, pD, pD]
@@ -366,6 +369,15 @@ class Batch:
         if rc != FH_OK:
             raise FhError(rc, "fh_batch_create failed")
         self.b = b
+
+    def autotune(self):
+        """Tune every size group's launch shapes (fh_batch_autotune); returns
+        (ms_before, ms_after), the summed CG-iteration time of all groups."""
+        bf, af = np.zeros(1), np.zeros(1)
+        rc = self.lib.fh_batch_autotune(self.b, _dptr(bf), _dptr(af))
+        if rc != FH_OK:
+            raise FhError(rc, "fh_batch_autotune: " + self.lib.fh_batch_last_error(self.b).decode())
+        return float(bf[0]), float(af[0])
 
     def solve(self, E, tol: float = 1e-6, method: str = "cg", max_iter: int = 20000):
         """Returns (Leff [ncells, 2, nloads], status [ncells, nloads], iters, summary)."""

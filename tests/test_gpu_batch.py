@@ -61,6 +61,22 @@ def test_batch_matches_oracle_per_cell(prec, tol, bar):
     assert info["launches"] > 0
 
 
+def test_batch_autotune_keeps_parity():
+    """fh_batch_autotune re-plans every size group; the results stay those of the oracle."""
+    cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    cells = _cells()
+    ref = _oracle_cols(cells, 1e-13)
+    with fh.Batch([c[0] for c in cells], [c[1] for c in cells], nloads=2, precision="fp32_refined") as b:
+        before, after = b.autotune()
+        assert 0.0 < after <= before * 1.05
+        Leff, st, it, info = b.solve(np.eye(2), tol=1e-10, method="cg", max_iter=20000)
+    assert np.all(st == 0), st
+    err = np.max(np.abs(Leff - ref), axis=(1, 2)) / np.max(np.abs(ref), axis=(1, 2))
+    assert np.all(err < 1e-6), err
+
+
 @pytest.mark.parametrize("method", ["bicg", "fixed_point"])
 def test_batch_other_methods_fp64(method):
     cuda_or_skip()
