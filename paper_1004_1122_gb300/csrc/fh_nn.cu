@@ -32,8 +32,6 @@
 namespace {
 
 constexpr float kSlope = 0.1f;
-constexpr int kOC = 16;      // output channels per conv CTA
-constexpr int kCC = 8;       // input channels staged per step
 constexpr int kThreads = 256;
 
 struct Dims {
@@ -41,110 +39,48 @@ struct Dims {
   __host__ __device__ long long v() const { return (long long)n0 * n1 * n2; }
 };
 
-// y[o] = b[o] + sum_c sum_t w(o, c, t) x[c](. + t), periodic.
-// TRANS: backward data, y = gradient wrt the input: y[c] = sum_o sum_t
-// w[o][c][t] x[o](. - t), i.e. the same loop with w(c_out, c_in, t) =
-// W[c_in][c_out][26 - t].
-template <bool TRANS>
-__global__ void __launch_bounds__(kThreads) k_conv(const float* __restrict__ x, int C,
-                                                   float* __restrict__ y, int O,
-                                                   const __nv_bfloat16* __restrict__ W,
-                                                   const float* __restrict__ b, Dims dm) {
-  __shared__ float ws[kOC][kCC][27];
-  const long long V = dm.v();
-  const long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int o0 = blockIdx.y * kOC;
-  const bool live = vox < V;
-  int off[27];
-  if (live) {
-    const int z = (int)(vox / ((long long)dm.n1 * dm.n2));
-    const int rem = (int)(vox - (long long)z * dm.n1 * dm.n2);
-    const int yy = rem / dm.n2, xx = rem - yy * dm.n2;
-    int t = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int zz = (z + dz + dm.n0) % dm.n0;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int y2 = (yy + dy + dm.n1) % dm.n1;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int x2 = (xx + dx + dm.n2) % dm.n2;
-          off[t++] = (zz * dm.n1 + y2) * dm.n2 + x2;
-        }
-      }
-    }
-  }
-  float acc[kOC];
-#pragma unroll
-  for (int k = 0; k < kOC; ++k) acc[k] = 0.0f;
-  for (int c0 = 0; c0 < C; c0 += kCC) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < kOC * kCC * 27; i += blockDim.x) {
-      const int oo = i / (kCC * 27), rem = i - oo * kCC * 27;
-      const int cc = rem / 27, t = rem - cc * 27;
-      const int o = o0 + oo, c = c0 + cc;
-      float w = 0.0f;
-      if (o < O && c < C) {
-        w = TRANS ? __bfloat162float(W[((long long)c * O + o) * 27 + (26 - t)])
-                  : __bfloat162float(W[((long long)o * C + c) * 27 + t]);
-      }
-      ws[oo][cc][t] = w;
-    }
-    __syncthreads();
-    if (!live) continue;
-    const int cn = min(kCC, C - c0);
-    for (int cc = 0; cc < cn; ++cc) {
-      const float* xc = x + (long long)(c0 + cc) * V;
-      float v[27];
-#pragma unroll
-      for (int t = 0; t < 27; ++t) v[t] = __ldg(xc + off[t]);
-#pragma unroll
-      for (int k = 0; k < kOC; ++k) {
-        float s = acc[k];
-#pragma unroll
-        for (int t = 0; t < 27; ++t) s = fmaf(ws[k][cc][t], v[t], s);
-        acc[k] = s;
-      }
-    }
-  }
-  if (!live) return;
-#pragma unroll
-  for (int k = 0; k < kOC; ++k) {
-    const int o = o0 + k;
-    if (o < O) y[(long long)o * V + vox] = acc[k] + (b ? b[o] : 0.0f);
-  }
-}
-
 // dW[o][c][t] = sum_z gy[o](z) x[c](z + t);  db[o] = sum_z gy[o](z).
-// One CTA per (o, c): 27 tap sums reduced over the voxels, no atomics.
+// CTA (o, c, s) sums the 27 taps and the bias over voxel slice s of S; the
+// partials go to part[((s * O + o) * C + c) * 28 + t] and k_wgrad_reduce adds
+// the slices in a fixed order (no atomics, deterministic).
 __global__ void __launch_bounds__(kThreads) k_conv_wgrad(const float* __restrict__ x, int C,
-                                                         const float* __restrict__ gy, int O,
-                                                         float* __restrict__ gW, float* __restrict__ gb,
-                                                         Dims dm) {
-  const int o = blockIdx.x / C, c = blockIdx.x - (blockIdx.x / C) * C;
+                                                         const float* __restrict__ gy, int O, int S,
+                                                         float* __restrict__ part, Dims dm) {
+  const int pair = blockIdx.x % (O * C), sl = blockIdx.x / (O * C);
+  const int o = pair / C, c = pair - (pair / C) * C;
   const long long V = dm.v();
+  const long long v0 = V * sl / S, v1 = V * (sl + 1) / S;
   const float* xc = x + (long long)c * V;
   const float* go = gy + (long long)o * V;
+  const int plane = dm.n1 * dm.n2;
   float acc[27];
 #pragma unroll
   for (int t = 0; t < 27; ++t) acc[t] = 0.0f;
   float accb = 0.0f;
-  for (long long vox = threadIdx.x; vox < V; vox += blockDim.x) {
-    const int z = (int)(vox / ((long long)dm.n1 * dm.n2));
-    const int rem = (int)(vox - (long long)z * dm.n1 * dm.n2);
+  for (long long vox = v0 + threadIdx.x; vox < v1; vox += blockDim.x) {
+    const int z = (int)(vox / plane);
+    const int rem = (int)(vox - (long long)z * plane);
     const int yy = rem / dm.n2, xx = rem - yy * dm.n2;
     const float g = __ldg(go + vox);
     accb += g;
-    int t = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int zz = (z + dz + dm.n0) % dm.n0;
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int y2 = (yy + dy + dm.n1) % dm.n1;
-        const int rowo = (zz * dm.n1 + y2) * dm.n2;
+    int xs[3];
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int x2 = (xx + dx + dm.n2) % dm.n2;
-          acc[t] = fmaf(g, __ldg(xc + rowo + x2), acc[t]);
-          ++t;
-        }
+    for (int k = 0; k < 3; ++k) {
+      int x2 = xx + k - 1;
+      x2 += x2 < 0 ? dm.n2 : (x2 >= dm.n2 ? -dm.n2 : 0);
+      xs[k] = x2;
+    }
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+      int zz = z + dz - 1;
+      zz += zz < 0 ? dm.n0 : (zz >= dm.n0 ? -dm.n0 : 0);
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        int y2 = yy + dy - 1;
+        y2 += y2 < 0 ? dm.n1 : (y2 >= dm.n1 ? -dm.n1 : 0);
+        const float* row = xc + (long long)(zz * dm.n1 + y2) * dm.n2;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[dz * 9 + dy * 3 + k] = fmaf(g, __ldg(row + xs[k]), acc[dz * 9 + dy * 3 + k]);
       }
     }
   }
@@ -152,17 +88,33 @@ __global__ void __launch_bounds__(kThreads) k_conv_wgrad(const float* __restrict
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int t = 0; t < 28; ++t) {
-    float s = t < 27 ? acc[t] : accb;
+    float v = t < 27 ? acc[t] : accb;
 #pragma unroll
-    for (int k = 16; k > 0; k >>= 1) s += __shfl_down_sync(0xffffffffu, s, k);
-    if (lane == 0) red[warp][t] = s;
+    for (int k = 16; k > 0; k >>= 1) v += __shfl_down_sync(0xffffffffu, v, k);
+    if (lane == 0) red[warp][t] = v;
   }
   __syncthreads();
   if (threadIdx.x < 28) {
-    float s = 0.0f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-    if (threadIdx.x < 27) gW[((long long)o * C + c) * 27 + threadIdx.x] = s;
-    else if (c == 0) gb[o] = s;
+    float v = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+    part[((long long)(sl * O + o) * C + c) * 28 + threadIdx.x] = v;
+  }
+}
+
+// gW[o][c][t] = sum_s part[s][o][c][t];  gb[o] = sum_s part[s][o][0][27]
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int O, int C, int S, float* __restrict__ gW,
+                               float* __restrict__ gb) {
+  const long long n = (long long)O * C * 28;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(i % 28);
+    const long long oc = i / 28;
+    float v = 0.0f;
+    for (int sl = 0; sl < S; ++sl) v += part[((long long)sl * O * C + oc) * 28 + t];
+    if (t < 27) {
+      gW[oc * 27 + t] = v;
+    } else if (oc % C == 0) {
+      gb[oc / C] = v;
+    }
   }
 }
 
@@ -303,11 +255,6 @@ __global__ void k_to_bf16_tc_t(const float* __restrict__ w, int O, int C, int Op
   }
 }
 
-__global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ q, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    q[i] = __float2bfloat16_rn(p[i]);
-}
-
 // x[0] = tab0[phase], x[1] = tab1[phase]  (input features from the phase image)
 __global__ void k_features(const uint8_t* __restrict__ phase, const float* __restrict__ t0,
                            const float* __restrict__ t1, float* __restrict__ x, long long V) {
@@ -390,13 +337,13 @@ struct fh_nn {
   long long nparam = 0;
   cudaStream_t st = nullptr;
   float *P = nullptr, *G = nullptr, *Mo = nullptr, *Ve = nullptr;
-  __nv_bfloat16* Wb = nullptr;
   __nv_bfloat16* Wtc = nullptr;                 // tensor-core weight layout, all layers
   __nv_bfloat16* WtcT = nullptr;                // transposed (data-gradient) layout
   long long wtc_off[kLayers], wtct_off[kLayers];// offsets (multiples of 8 elements)
   int cpad[kLayers], ntile[kLayers];             // forward: in channels padded to 8, N tile
   int opad[kLayers], ntile_t[kLayers];           // data gradient: out channels padded to 8, N tile
   int* dev_err = nullptr;                        // bounded waits that expired
+  float* wpart = nullptr;                        // weight-gradient partials per voxel slice
   // forward: pre-activations z[k] (k < 10), encoder a[l], pooled pl[l],
   // decoder sums v[l] and activations u[l], output y; tmp = leaky(up conv)
   float *x = nullptr, *z[kLayers - 1] = {}, *a[4] = {}, *pl[3] = {}, *v[3] = {}, *u[3] = {}, *y = nullptr;
@@ -425,9 +372,7 @@ cudaError_t conv(fh_nn* n, int layer, const float* in, float* out, bool trans) {
   const int O = trans ? n->li[layer] : n->lo[layer];
   const int C = trans ? n->lo[layer] : n->li[layer];
   const Dims d = n->lv[n->ll[layer]];
-  dim3 grid((unsigned)((d.v() + kThreads - 1) / kThreads), (unsigned)((O + kOC - 1) / kOC));
   ++n->launches;
-  (void)grid;
   {
     // forward: y = conv(x; W) + b;  data gradient: gx = conv(gy; W^T, taps
     // reversed), the same implicit GEMM with the transposed weight layout
@@ -450,11 +395,21 @@ cudaError_t conv(fh_nn* n, int layer, const float* in, float* out, bool trans) {
   return cudaGetLastError();
 }
 
+// voxel slices per (o, c) pair: enough CTAs for ~4 per SM, at least 2048 voxels a slice
+int wgrad_slices(int O, int C, long long V) {
+  long long s = (608 + (long long)O * C - 1) / ((long long)O * C);
+  s = std::min<long long>(s, std::max<long long>(1, V / 2048));
+  return (int)std::max<long long>(1, std::min<long long>(s, 64));
+}
+
 cudaError_t wgrad(fh_nn* n, int layer, const float* in, const float* gy) {
   const Dims d = n->lv[n->ll[layer]];
-  ++n->launches;
-  k_conv_wgrad<<<n->lo[layer] * n->li[layer], kThreads, 0, n->st>>>(in, n->li[layer], gy, n->lo[layer],
-                                                                     n->G + n->woff[layer], n->G + n->boff[layer], d);
+  const int O = n->lo[layer], C = n->li[layer];
+  const int S = wgrad_slices(O, C, d.v());
+  n->launches += 2;
+  k_conv_wgrad<<<O * C * S, kThreads, 0, n->st>>>(in, C, gy, O, S, n->wpart, d);
+  k_wgrad_reduce<<<grid1((long long)O * C * 28), kThreads, 0, n->st>>>(n->wpart, O, C, S, n->G + n->woff[layer],
+                                                                       n->G + n->boff[layer]);
   return cudaGetLastError();
 }
 
@@ -485,8 +440,6 @@ constexpr int kPost[3] = {9, 7, 5};
 
 cudaError_t forward(fh_nn* n) {
   cudaError_t e;
-  ++n->launches;
-  k_to_bf16<<<grid1(n->nparam), kThreads, 0, n->st>>>(n->P, n->Wb, n->nparam);
   for (int k = 0; k < kLayers; ++k) {
     n->launches += 2;
     k_to_bf16_tc<<<grid1((long long)n->ntile[k] * 27 * n->cpad[k]), kThreads, 0, n->st>>>(
@@ -644,9 +597,14 @@ fh_status fh_nn_create(fh_nn** out, const int* N, int cin, int cout, const int* 
   rc |= nn_alloc(n, &n->G, off);
   rc |= nn_alloc(n, &n->Mo, off);
   rc |= nn_alloc(n, &n->Ve, off);
-  rc |= nn_alloc(n, &n->Wb, off);
   rc |= nn_alloc(n, &n->Wtc, toff);
   rc |= nn_alloc(n, &n->WtcT, ttoff);
+  {
+    long long wp = 0;
+    for (int k = 0; k < kLayers; ++k)
+      wp = std::max(wp, (long long)wgrad_slices(n->lo[k], n->li[k], V[n->ll[k]]) * n->lo[k] * n->li[k] * 28);
+    rc |= nn_alloc(n, &n->wpart, wp);
+  }
   rc |= nn_alloc(n, &n->dev_err, 1);
   rc |= nn_alloc(n, &n->x, V[0] * cin);
   for (int k = 0; k < kLayers - 1; ++k) rc |= nn_alloc(n, &n->z[k], V[n->ll[k]] * (long long)n->lo[k]);
