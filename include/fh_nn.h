@@ -80,8 +80,8 @@ fh_status fh_nn_features(const uint8_t* phase, int nphase, const double* L, int 
 /* First-order response of the cell: x[b*d + a] = (B e_b)_a for the d unit
  * loads e_b, B = F^-1 Gamma0 F dL of Eq. (mtrx_B), i.e. the fluctuation of
  * the first fixed-point iterate of Eq. (orig_fft) started at e = e_b (up to
- * sign).  d products of ctx (float64 where ctx has that pipeline, else
- * float32).  x: device float32 [d*d][nodes] (nodes = product of ctx's N).
+ * sign).  d products of ctx (float32 where ctx has that pipeline, else
+ * float64).  x: device float32 [d*d][nodes] (nodes = product of ctx's N).
  * Synchronises the device.  Errors: FH_ERR_ARG, FH_ERR_OOM, FH_ERR_CUDA. */
 fh_status fh_nn_response_features(fh_ctx* ctx, int d, long long nodes, float* x);
 

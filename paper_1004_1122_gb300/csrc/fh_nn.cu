@@ -767,9 +767,10 @@ extern "C" {
 
 fh_status fh_nn_response_features(fh_ctx* ctx, int d, long long nodes, float* x) {
   if (!ctx || !x || (d != 2 && d != 3) || nodes < 1) return FH_ERR_ARG;
-  // float64 products where the context has them, else the float32 pipeline
-  fh_status s = response_features<double>(ctx, FH_FP64, d, nodes, x);
-  if (s == FH_ERR_ARG) s = response_features<float>(ctx, FH_FP32, d, nodes, x);
+  // float32 products where the context has them (the features are float32),
+  // else the float64 pipeline
+  fh_status s = response_features<float>(ctx, FH_FP32, d, nodes, x);
+  if (s == FH_ERR_ARG) s = response_features<double>(ctx, FH_FP64, d, nodes, x);
   return s;
 }
 
