@@ -236,6 +236,16 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], int nv, doub
   }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+// Prefetch [p, p + bytes) into L2, one request per 128-byte line, spread over the CTA.
+__device__ __forceinline__ void prefetch_range(const void* p, long long bytes) {
+  const char* b = reinterpret_cast<const char*>((reinterpret_cast<uintptr_t>(p)) & ~(uintptr_t)127);
+  const long long nl = (reinterpret_cast<const char*>(p) + bytes - b + 127) / 128;
+  for (long long i = threadIdx.x; i < nl; i += blockDim.x) prefetch_l2(b + i * 128);
+}
+
 // ----------------------------------------------------------------------------
 // row forward pass
 // ----------------------------------------------------------------------------
@@ -273,6 +283,22 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
     lbeta[l] = kDir ? T(sc[l].beta) : T(0);
     pin[l] = a.in[l];
     pout[l] = a.out[l];
+  }
+  // ask L2 for the CTA's input lines before the table load and the barrier:
+  // the gather below then waits on L2 rather than on HBM (direction pass on
+  // 2187^2: 50.0 -> 47.2 us; the same hint in the A p pass measured slower)
+  for (int ll = 0; ll < a.lpc; ++ll) {
+    const int line = line0 + ll;
+    if (line >= g.nlines) break;
+    const long long lo = (long long)line * n;
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        prefetch_range(pin[l] + c * g.nodes + lo, (long long)n * sizeof(T));
+        if (kDir) prefetch_range(pout[l] + c * g.nodes + lo, (long long)n * sizeof(T));
+      }
+    if (kUseTab) prefetch_range(a.phase + lo, n);
   }
   if (kUseTab) {
     for (int i = threadIdx.x; i < a.nphase * d * d; i += blockDim.x) stab[i] = tabc[i];
