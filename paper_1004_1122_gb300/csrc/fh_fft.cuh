@@ -499,9 +499,10 @@ __device__ __forceinline__ void fft_fused_plan(cplx<T>* sm, int is, const FFTPla
     run_fft_fused_ct<T, P>(sm, is, u, nthr, tw, mid);
 }
 
-// The plan of the 3^7 = 2187 axis that the planner picks for 81 threads, and
-// of the 3^5 = 243 axis (9 threads).
+// The plans the planner picks for the 3^7 = 2187 axis (81 threads), the
+// 3^5 = 243 axis (9 threads) and the 3^6 = 729 axis (27 threads).
 using Plan2187 = CPlan<27, 27, 3>;
 using Plan243 = CPlan<27, 9>;
+using Plan729 = CPlan<27, 27>;
 
 }  // namespace fh

@@ -34,15 +34,19 @@ static cudaError_t opt_in_smem(K kernel, size_t bytes) {
 // whose run-time plan matches use them; everything else runs the
 // run-time-plan kernels.
 template <typename T, int D, int NL>
-constexpr bool kHasCt = std::is_same<T, float>::value && ((D == 2 && NL == 1) || D == 3);
-template <int D> using CtPlan = typename std::conditional<D == 2, Plan2187, Plan243>::type;
+constexpr bool kHasCt = std::is_same<T, float>::value && (D == 2 || D == 3);
+// 2-D one load: the 2187-point plan; 2-D two loads (the batched sweep's
+// largest cells): the 729-point plan; 3-D: the 243-point plan.
+template <int D, int NL>
+using CtPlan = typename std::conditional<D == 2, typename std::conditional<NL == 1, Plan2187, Plan729>::type,
+                                         Plan243>::type;
 
 template <typename T, int D, int NL>
 struct Launchers {
   static cudaError_t set_smem(size_t rs, size_t c0, size_t c1) {
     cudaError_t e;
     if constexpr (kHasCt<T, D, NL>) {
-      using P = CtPlan<D>;
+      using P = CtPlan<D, NL>;
       if ((e = opt_in_smem(k_row_fwd<T, D, NL, kProDir, P>, rs)) != cudaSuccess) return e;
       if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, P>, rs)) != cudaSuccess) return e;
       if ((e = opt_in_smem(k_col<T, D, kColGreen, P>, c0)) != cudaSuccess) return e;
@@ -72,7 +76,7 @@ struct Launchers {
   }
   static cudaError_t row_fwd(int pro, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
     if constexpr (kHasCt<T, D, NL>) {
-      using P = CtPlan<D>;
+      using P = CtPlan<D, NL>;
       if (pro == kProDir && L.block <= RowBounds<P>::threads && cplan_is<P>(a.plan)) {
         k_row_fwd<T, D, NL, kProDir, P><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
@@ -89,7 +93,7 @@ struct Launchers {
   }
   static cudaError_t row_inv(int epi, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
     if constexpr (kHasCt<T, D, NL>) {
-      using P = CtPlan<D>;
+      using P = CtPlan<D, NL>;
       if (epi == kEpiDir && L.block <= RowBounds<P>::threads && cplan_is<P>(a.plan)) {
         k_row_inv<T, D, NL, kEpiDir, P><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
@@ -108,7 +112,7 @@ struct Launchers {
   }
   static cudaError_t col(int mode, const Launch& L, const ColArgs<T>& a, cudaStream_t st) {
     if constexpr (kHasCt<T, D, NL>) {
-      using P = CtPlan<D>;
+      using P = CtPlan<D, NL>;
       if (L.block <= ColBounds<P>::threads && cplan_is<P>(a.b.plan)) {
         if (mode == kColGreen) {
           k_col<T, D, kColGreen, P><<<L.grid, L.block, L.smem, st>>>(a);
@@ -136,7 +140,7 @@ struct Launchers {
     return cudaGetLastError();
   }
   static cudaError_t col_pipe(const Launch& L, const ColArgs<T>& a, cudaStream_t st) {
-    if constexpr (kHasCt<T, D, NL> && D == 2) {
+    if constexpr (kHasCt<T, D, NL> && D == 2 && NL == 1) {
       if (cplan_is<Plan2187>(a.b.plan)) {
         k_col_pipe<T, D, Plan2187><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
@@ -149,7 +153,7 @@ struct Launchers {
     return cudaErrorInvalidValue;
   }
   static cudaError_t set_smem_pipe(size_t bytes) {
-    if constexpr (kHasCt<T, D, NL> && D == 2) {
+    if constexpr (kHasCt<T, D, NL> && D == 2 && NL == 1) {
       cudaError_t e = opt_in_smem(k_col_pipe<T, D, Plan2187>, bytes);
       if (e != cudaSuccess) return e;
     }
