@@ -1108,17 +1108,37 @@ __global__ void k_bicg_update(VecArgs<T> a) {
 }
 
 // ----------------------------------------------------------------------------
-// scalar control kernels: one CTA of kRedThreads threads
+// scalar control kernels: one CTA of kRedThreads threads per item
 // ----------------------------------------------------------------------------
-// One warp per item (cell, load): the item's partials are the bpc = np / ncell
-// consecutive slots of its cell in row l of the partial array.
-__device__ __forceinline__ double warp_sum(const double* p, int n) {
-  const int lane = threadIdx.x & 31;
-  double x = 0.0;
-  for (int i = lane; i < n; i += 32) x += p[i];
+// One CTA of kRedThreads threads per item (cell, load): the item's partials are
+// the bpc = np / ncell consecutive slots of its cell in row l of the partial
+// array.  Four independent accumulators per thread keep several L2 loads in
+// flight (a single-cell 2187^2 CG item has 2187 slots; one warp walking them in
+// a dependent chain took ~10 us per scalar launch).
+__device__ __forceinline__ double block_sum(const double* p, int n) {
+  __shared__ double red[kRedThreads / 32];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int i = threadIdx.x;
+  for (; i + 3 * kRedThreads < n; i += 4 * kRedThreads) {
+    a0 += p[i];
+    a1 += p[i + kRedThreads];
+    a2 += p[i + 2 * kRedThreads];
+    a3 += p[i + 3 * kRedThreads];
+  }
+  for (; i < n; i += kRedThreads) a0 += p[i];
+  double x = (a0 + a1) + (a2 + a3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-  return __shfl_sync(0xffffffffu, x, 0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    x = lane < kRedThreads / 32 ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  }
+  __syncthreads();  // red[] may be reused by a second sum in the same kernel
+  return x;         // valid in thread 0
 }
 
 struct ItemRef {
@@ -1128,7 +1148,7 @@ struct ItemRef {
 
 __device__ __forceinline__ ItemRef item_ref(int np, int ncell, int nl) {
   ItemRef r;
-  r.item = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  r.item = (int)blockIdx.x;
   r.valid = r.item < ncell * nl;
   r.cell = r.item / nl;
   r.l = r.item - r.cell * nl;
@@ -1151,8 +1171,8 @@ __device__ __forceinline__ void record_hist(Scal& s) {
 static __global__ void k_scal_start(Scal* scal, const double* part, int np, int ncell, int nl) {
   const ItemRef r = item_ref(np, ncell, nl);
   if (!r.valid) return;
-  const double rr = warp_sum(item_part(part, r.l, np, r), r.bpc);
-  if ((threadIdx.x & 31) == 0) {
+  const double rr = block_sum(item_part(part, r.l, np, r), r.bpc);
+  if (threadIdx.x == 0) {
     Scal& s = scal[r.item];
     s.rr = rr;
     s.rho = rr;  // r0* = r0
@@ -1175,8 +1195,8 @@ static __global__ void k_scal_start(Scal* scal, const double* part, int np, int 
 static __global__ void k_scal_alpha(Scal* scal, const double* part, int np, int ncell, int nl, int bicg) {
   const ItemRef r = item_ref(np, ncell, nl);
   if (!r.valid) return;
-  const double den = warp_sum(item_part(part, r.l, np, r), r.bpc);
-  if ((threadIdx.x & 31) == 0) {
+  const double den = block_sum(item_part(part, r.l, np, r), r.bpc);
+  if (threadIdx.x == 0) {
     Scal& s = scal[r.item];
     if (s.done != kRunning) return;
     s.den = den;
@@ -1193,12 +1213,12 @@ static __global__ void k_scal_beta(Scal* scal, const double* part, int np, int n
   if (!r.valid) return;
   double rho_new = 0.0, rr_new;
   if (bicg) {
-    rho_new = warp_sum(item_part(part, r.l, np, r), r.bpc);
-    rr_new = warp_sum(item_part(part, kMaxLoads + r.l, np, r), r.bpc);
+    rho_new = block_sum(item_part(part, r.l, np, r), r.bpc);
+    rr_new = block_sum(item_part(part, kMaxLoads + r.l, np, r), r.bpc);
   } else {
-    rr_new = warp_sum(item_part(part, r.l, np, r), r.bpc);
+    rr_new = block_sum(item_part(part, r.l, np, r), r.bpc);
   }
-  if ((threadIdx.x & 31) == 0) {
+  if (threadIdx.x == 0) {
     Scal& s = scal[r.item];
     if (s.done != kRunning) return;
     s.iter += 1;
@@ -1224,8 +1244,8 @@ static __global__ void k_scal_beta(Scal* scal, const double* part, int np, int n
 static __global__ void k_scal_fixed(Scal* scal, const double* part, int np, int ncell, int nl) {
   const ItemRef r = item_ref(np, ncell, nl);
   if (!r.valid) return;
-  const double rr = warp_sum(item_part(part, r.l, np, r), r.bpc);
-  if ((threadIdx.x & 31) == 0) {
+  const double rr = block_sum(item_part(part, r.l, np, r), r.bpc);
+  if (threadIdx.x == 0) {
     Scal& s = scal[r.item];
     if (s.done != kRunning) return;
     s.rr = rr;
@@ -1243,11 +1263,11 @@ static __global__ void k_scal_fixed(Scal* scal, const double* part, int np, int 
 static __global__ void k_reduce_items(const double* part, int np, int ncell, int nv, double* out) {
   const ItemRef r = item_ref(np, ncell, nv);
   if (!r.valid) return;
-  const double x = warp_sum(item_part(part, r.l, np, r), r.bpc);
-  if ((threadIdx.x & 31) == 0) out[r.item] = x;
+  const double x = block_sum(item_part(part, r.l, np, r), r.bpc);
+  if (threadIdx.x == 0) out[r.item] = x;
 }
 
-inline int item_blocks(int items) { return (items * 32 + kRedThreads - 1) / kRedThreads; }
+inline int item_blocks(int items) { return items; }
 
 // ----------------------------------------------------------------------------
 // misc elementwise kernels
