@@ -308,8 +308,9 @@ def run_reference(args):
 # Sources that define the operator and CG kernels and their launch shapes (the
 # host drivers -- C API, batches, network -- do not change what a recorded
 # capture of these kernels measured).
-KERNEL_SOURCES = ("fh_fft.cuh", "fh_kernels.cuh", "fh_tma.cuh", "fh_plan.h", "fh_launch.cuh",
-                  "fh_launch_impl.cuh", "fh_launch_f32_d2.cu", "fh_pipeline.cuh", "fh_pipeline_impl.cuh")
+KERNEL_SOURCES = ("fh_fft.cuh", "fh_dfloat.cuh", "fh_kernels.cuh", "fh_tma.cuh", "fh_plan.h",
+                  "fh_launch.cuh", "fh_launch_impl.cuh", "fh_launch_f32_d2.cu", "fh_pipeline.cuh",
+                  "fh_pipeline_impl.cuh")
 
 
 def csrc_digest() -> str:

@@ -396,7 +396,8 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
           xin[l] = g.x64[l];
           rout[l] = g.r64[l];
         }
-        int rc = g.p64->residual(xin, rout, false, Ev, rr.data(), err);
+        // float64-accuracy residual; its Green pass runs in double-float
+        int rc = g.p64->residual(xin, rout, false, Ev, rr.data(), err, true);
         if (rc) return fail(rc);
         const long long cn = g.pb.nodes / g.pb.ncell;
         eta[gi].assign(st[gi].size(), 1.0);

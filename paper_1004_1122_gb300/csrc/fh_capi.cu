@@ -627,7 +627,8 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
       double rr;
       const double* xin[fh::kMaxLoads] = {c->d_x64};
       double* rout[fh::kMaxLoads] = {c->d_r64};
-      rc = Q->residual(xin, rout, false, Ev, &rr, err);
+      // float64-accuracy residual; its Green pass runs in double-float
+      rc = Q->residual(xin, rout, false, Ev, &rr, err, true);
       if (rc) return from_rc(c, rc, err);
       rel_true = std::sqrt(rr / e2);
       if (!std::isfinite(rel_true)) { status = fh::kBreakdown; break; }

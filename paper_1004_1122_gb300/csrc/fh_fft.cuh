@@ -1,5 +1,5 @@
 // fh_fft.cuh -- device FFT building blocks for odd lengths (radix 3, 5, 7 and
-// their products), float32 and float64.
+// their products), float32, float64 and double-float (fh_dfloat.cuh).
 //
 // The discrete Fourier transform is the one of Eq. (DFT_def): forward
 // X[k] = sum_m x[m] exp(-2 pi i k m / n), inverse with +i and no 1/n (the
@@ -26,6 +26,8 @@
 #include <type_traits>
 #include <utility>
 
+#include "fh_dfloat.cuh"
+
 namespace fh {
 
 // ----------------------------------------------------------------------------
@@ -34,7 +36,19 @@ namespace fh {
 template <typename T> struct cplx_t;
 template <> struct cplx_t<float> { using type = float2; };
 template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<dfl> { using type = dfc; };
 template <typename T> using cplx = typename cplx_t<T>::type;
+
+// Read-only load of one stage twiddle.
+template <typename C>
+__device__ __forceinline__ C ld_tw(const C* p) { return __ldg(p); }
+__device__ __forceinline__ dfc ld_tw(const dfc* p) {
+  const float4 w = __ldg(reinterpret_cast<const float4*>(p));
+  dfc r;
+  r.x = dfl(w.x, w.y);
+  r.y = dfl(w.z, w.w);
+  return r;
+}
 
 template <typename T>
 __device__ __forceinline__ cplx<T> cmk(T x, T y) { cplx<T> r; r.x = x; r.y = y; return r; }
@@ -222,6 +236,7 @@ template <int R, int S, bool INV, typename T> struct RegDFT {
 template <typename T> struct RegBudget;
 template <> struct RegBudget<float> { static constexpr int value = 27; };
 template <> struct RegBudget<double> { static constexpr int value = 9; };
+template <> struct RegBudget<dfl> { static constexpr int value = 9; };
 
 // Sequence element i of the sequence this thread works on lives at
 // sm[i * is].  u in [0, nthr) is the thread's rank within the sequence's
@@ -266,7 +281,7 @@ __device__ __forceinline__ void stockham_stage(cplx<T> (&v)[EM], cplx<T>* sm, in
         int ti = ks;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const C w = __ldg(tw + ti);
+          const C w = ld_tw(tw + ti);
           ti += ks;
           v[b * R + r] = INV ? cmulc(v[b * R + r], w) : cmul(v[b * R + r], w);
         }
@@ -347,7 +362,7 @@ __device__ __forceinline__ void fused_middle(cplx<T> (&v)[EM], cplx<T>* sm, int 
         int ti = j;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          v[b * R + r] = cmul(v[b * R + r], __ldg(tw + ti));
+          v[b * R + r] = cmul(v[b * R + r], ld_tw(tw + ti));
           ti += j;
         }
       }

@@ -652,6 +652,106 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
   }
 }
 
+// Green projection of one value of a 2-D float64 spectrum held in double-float
+// registers (the refinement residual's Green pass, k_col_green_df): the same
+// map as GreenPoint2, y_a = xi_a (xi . v) / (xi . L0 . xi) / |N|, with every
+// product, sum and the quotient in double-float arithmetic.
+struct GreenPointDF {
+  dfl invY0, xi1, L00, L01, L10, L11, inv_nodes;
+  int n, a;
+  bool pad, kl0;
+  __device__ __forceinline__ void init(const Geom& g, const double* L0src, int t, int q, int n_) {
+    const int c = (q / g.M) % g.C;
+    const int kl = t * g.C + c;
+    invY0 = df_from(g.invY[0]);
+    xi1 = df_mul_f(df_from(g.invY[1]), (float)kl);  // |kl| < 2^24: exact in float32
+    L00 = df_from(L0src[0]);
+    L01 = df_from(L0src[1]);
+    L10 = df_from(L0src[3]);
+    L11 = df_from(L0src[4]);
+    inv_nodes = df_from(g.inv_nodes);
+    n = n_;
+    a = q & 1;
+    pad = kl >= g.H;
+    kl0 = kl == 0;
+  }
+  __device__ __forceinline__ dfc operator()(dfc v, int i, bool act) const {
+    dfc o;
+    o.x = df_shfl_xor(v.x, 1);
+    o.y = df_shfl_xor(v.y, 1);
+    const int k0 = i <= (n - 1) / 2 ? i : i - n;
+    const dfl xi0 = df_mul_f(invY0, (float)k0);
+    const dfc v0 = a == 0 ? v : o;
+    const dfc v1 = a == 0 ? o : v;
+    const bool zero = !act || pad || (k0 == 0 && kl0);
+    const dfl den = xi0 * (L00 * xi0 + L01 * xi1) + xi1 * (L10 * xi0 + L11 * xi1);
+    const dfl f = zero ? dfl(0.0f, 0.0f) : df_div(inv_nodes, zero ? dfl(1.0f, 0.0f) : den);
+    const dfl sre = xi0 * v0.x + xi1 * v1.x;
+    const dfl sim = xi0 * v0.y + xi1 * v1.y;
+    const dfl xaf = (a == 0 ? xi0 : xi1) * f;
+    dfc y;
+    y.x = xaf * sre;
+    y.y = xaf * sim;
+    return y;
+  }
+};
+
+// Green pass of a 2-D float64 spectrum in double-float arithmetic: the same
+// forward FFT along axis 0, projection and inverse FFT as k_col<double, 2,
+// kColGreen>, on the same launch shape and shared memory (a complex
+// double-float is 16 bytes, like a double2).  Each value is split into
+// hi + lo float32 parts when the tile is read and recombined when it is
+// written; in between, every operation runs on the float32 pipes.  Used for
+// the float64 residual of the refined solves, where the result must be
+// accurate far below the float32 rounding level but not to the last float64
+// bit (relative error ~1e-14 against ~1e-16).  In 2-D every tile row is Q
+// whole double2 values (16-byte aligned), so the tile moves as 16-byte words.
+template <typename PS = DynPlan>
+__global__ void __launch_bounds__(kColMaxThreads) k_col_green_df(ColArgs<double> a, const dfc* __restrict__ twdf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dfc* sm = reinterpret_cast<dfc*>(smem_raw);
+  const ColArgsBase& b = a.b;
+  const Geom& g = b.g;
+  const int n = b.plan.n, Q = b.Q;
+  const int blk_outer = blockIdx.x / b.nb_inner;
+  const int blk_inner = blockIdx.x - blk_outer * b.nb_inner;
+  const int cell = g.ncell > 1 ? blk_inner : 0;  // 2-D batches: the inner block index is the cell
+  if (all_done(a.scal ? a.scal + cell * g.nloads : nullptr, g.nloads)) return;
+  const long long base = blk_outer * b.base_outer + blk_inner * b.base_inner;
+  const int nq = n * Q;
+  constexpr int kUnroll = 4;
+  for (int w0 = threadIdx.x; w0 < nq; w0 += kUnroll * blockDim.x) {
+    double2 buf[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int w = w0 + u * blockDim.x;
+      if (w < nq) {
+        const int i = w / Q, j = w - i * Q;
+        buf[u] = __ldg(a.S + base + i * b.stride_i + j);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int w = w0 + u * blockDim.x;
+      if (w < nq) sm[w] = dfc_from(buf[u]);
+    }
+  }
+  __syncthreads();
+
+  const int q = threadIdx.x % Q;
+  const int u0 = threadIdx.x / Q;
+  const int u = u0 < b.tpc ? u0 : n;
+  const double* L0src = a.L0cell ? a.L0cell + 9 * cell : g.L0;
+  GreenPointDF gp;
+  gp.init(g, L0src, blk_outer, q, n);
+  fft_fused_plan<dfl, PS>(sm + q, Q, b.plan, u, b.tpc, twdf, gp);
+
+  for (int w = threadIdx.x; w < nq; w += blockDim.x) {
+    const int i = w / Q, j = w - i * Q;
+    a.S[base + i * b.stride_i + j] = dfc_to(sm[w]);
+  }
+}
+
 // Persistent, double-buffered Green pass for 2-D grids.  A work item is the
 // spectrum block of one (tile, cell): n rows of Q = C*M complex values, one
 // contiguous, 16-byte aligned range.  One thread moves each block into shared

@@ -24,6 +24,10 @@ struct LaunchTable {
   cudaError_t (*col_pipe)(const Launch&, const ColArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*set_smem_pipe)(size_t bytes) = nullptr;
   cudaError_t (*occupancy_pipe)(int block, size_t smem, int* per_sm) = nullptr;
+  // 2-D float64 Green pass in double-float arithmetic (the refinement
+  // residual); tw_df is the axis-0 twiddle table as complex double-floats.
+  // nullptr for float and for 3-D.
+  cudaError_t (*col_df)(const Launch&, const ColArgs<T>&, const void* tw_df, cudaStream_t) = nullptr;
   cudaError_t (*cg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*bicg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*current_sum)(const Launch&, const T*, const uint8_t*, const double*, long long nodes,

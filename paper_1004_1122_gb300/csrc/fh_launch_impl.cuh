@@ -41,6 +41,10 @@ template <int D, int NL>
 using CtPlan = typename std::conditional<D == 2, typename std::conditional<NL == 1, Plan2187, Plan729>::type,
                                          Plan243>::type;
 
+// The double-float Green pass exists for the 2-D float64 pipelines.
+template <typename T, int D>
+constexpr bool kHasDf = std::is_same<T, double>::value && D == 2;
+
 template <typename T, int D, int NL>
 struct Launchers {
   static cudaError_t set_smem(size_t rs, size_t c0, size_t c1) {
@@ -71,6 +75,7 @@ struct Launchers {
     FH_SM((k_col<T, D, kColEta>), c0)
     FH_SM((k_col<T, D, kColFwd>), c1)
     FH_SM((k_col<T, D, kColInv>), c1)
+    if constexpr (kHasDf<T, D>) FH_SM((k_col_green_df<>), c0)
 #undef FH_SM
     return cudaSuccess;
   }
@@ -152,6 +157,13 @@ struct Launchers {
     }
     return cudaErrorInvalidValue;
   }
+  static cudaError_t col_df(const Launch& L, const ColArgs<T>& a, const void* tw, cudaStream_t st) {
+    if constexpr (kHasDf<T, D>) {
+      k_col_green_df<><<<L.grid, L.block, L.smem, st>>>(a, static_cast<const dfc*>(tw));
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
   static cudaError_t set_smem_pipe(size_t bytes) {
     if constexpr (kHasCt<T, D, NL> && D == 2 && NL == 1) {
       cudaError_t e = opt_in_smem(k_col_pipe<T, D, Plan2187>, bytes);
@@ -196,6 +208,7 @@ struct Launchers {
       t.set_smem_pipe = &set_smem_pipe;
       t.occupancy_pipe = &occupancy_pipe;
     }
+    if (kHasDf<T, D>) t.col_df = &col_df;
     t.cg_update = &cg_update;
     t.bicg_update = &bicg_update;
     t.current_sum = &current_sum;

@@ -78,6 +78,8 @@ struct Pipeline {
   C* tw_last = nullptr;
   C* tw0 = nullptr;
   C* tw1 = nullptr;
+  dfc* tw0_df = nullptr;     // 2-D float64: axis-0 twiddles as double-floats (lt.col_df)
+  bool df_green = false;     // route the next Green passes through lt.col_df
   C* S = nullptr;
   T* dtab = nullptr;   // dL per phase
   T* qtab = nullptr;   // L0 for every phase: the passes then apply Q = Gamma0 L0
@@ -166,9 +168,11 @@ struct Pipeline {
   // ---- reductions ---------------------------------------------------------
   // out[l] = ||x_l||^2 (sum over the vector), synchronous
   int norm2(T* const* v, double* out, std::string& err);
-  // ||rhs - A x||^2 per load into out (synchronous), residual field into r
+  // ||rhs - A x||^2 per load into out (synchronous), residual field into r.
+  // df: run the Green pass in double-float arithmetic where the pipeline has
+  // that kernel (2-D float64); the other passes stay in T.
   int residual(const T* const* xin, T* const* rout, bool rhs_field, const double (*E)[kMaxD],
-               double* out, std::string& err);
+               double* out, std::string& err, bool df = false);
   // column of <tab e> (tab = L) in float64
   int current_mean(const T* e, double* col, std::string& err);
   int eta_e(const T* e, double* eta, std::string& err);

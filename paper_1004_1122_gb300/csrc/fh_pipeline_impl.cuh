@@ -261,6 +261,18 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   if ((rc = upload_tw(g.nlast, &tw_last))) return rc;
   if ((rc = upload_tw(pb.N[0], &tw0))) return rc;
   if (d == 3 && (rc = upload_tw(pb.N[1], &tw1))) return rc;
+  if (d == 2 && lt.col_df) {
+    // axis-0 twiddles as complex double-floats: hi = fl32(w), lo = fl32(w - hi)
+    std::vector<double> re, im;
+    twiddles(pb.N[0], re, im);
+    std::vector<dfc> h(pb.N[0]);
+    for (int m = 0; m < pb.N[0]; ++m) {
+      h[m].x = dfl(re[m]);
+      h[m].y = dfl(im[m]);
+    }
+    if ((rc = dev_alloc(allocs, &tw0_df, pb.N[0], err))) return rc;
+    FH_CKS(cudaMemcpy(tw0_df, h.data(), pb.N[0] * sizeof(dfc), cudaMemcpyHostToDevice));
+  }
   {
     const int nt = std::max(1, nphase) * d * d * ncell;
     std::vector<T> hd(nt), hl(nt);
@@ -385,6 +397,7 @@ cudaError_t Pipeline<T>::launch_green(int mode, Scal* sc, double* pt) {
   }
   ++launches;
   if (mode == kColEta) return lt.col(kColEta, col0, a, st);
+  if (df_green && g.d == 2) return lt.col_df(col0, a, tw0_df, st);
   if (green_pipe) {
     FH_CK(lt.col_pipe(colp, a, st));
   } else {
@@ -578,7 +591,7 @@ int Pipeline<T>::matnorm2(const T* e, const double* Mx, double* out, std::string
 
 template <typename T>
 int Pipeline<T>::residual(const T* const* xin, T* const* rout, bool rhs_field,
-                          const double (*E)[kMaxD], double* out, std::string& err) {
+                          const double (*E)[kMaxD], double* out, std::string& err, bool df) {
   const int nscal = std::max(items, kMaxLoads);
   for (int it = 0; it < items; ++it) {
     const int l = it % nloads;
@@ -596,7 +609,10 @@ int Pipeline<T>::residual(const T* const* xin, T* const* rout, bool rhs_field,
     a.out[l] = rout[l];
     a.rhs[l] = rhs_field ? rhs[l] : nullptr;
   }
-  FH_CKS(passes(kProApply, kEpiResid, a, a, scal_aux));
+  df_green = df && lt.col_df != nullptr && tw0_df != nullptr;
+  const cudaError_t pe = passes(kProApply, kEpiResid, a, a, scal_aux);
+  df_green = false;
+  FH_CKS(pe);
   ++launches;
   k_reduce_items<<<item_blocks(items), kRedThreads, 0, st>>>(part, row.grid, ncell, nloads, d_red);
   FH_CKS(cudaGetLastError());

@@ -82,6 +82,31 @@ def test_fp32_refined_meets_1e6(method):
     assert np.max(np.abs(col - Lo)) / np.max(np.abs(Lo)) < 1e-6
 
 
+@pytest.mark.parametrize("N,rho", [(81, 1e2), (243, 1e4), (135, 1e3)])
+def test_refined_true_residual_is_float64_accurate(N, rho):
+    """The outer residual of the refined solves (float64 fields, Green pass in
+    double-float arithmetic) equals the oracle's float64 residual of the
+    returned field to 1e-11 |e0|; a float32-accuracy Green pass would miss by
+    ~1e-7.  (The two-load Green pass of fh_solve_all and of the batches is
+    covered by their L_eff parity tests.)"""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase = micro.rsa_disks(N, 0.35, N / 40, N / 20, seed=micro.config_seed(5, N))
+    L = micro.isotropic_table([1.0, rho], 2)
+    L0 = oracle.reference_medium(L)
+    E = [0.6, -0.8]
+    with fh.Solver(phase, L, precision="fp32_refined") as s:
+        x, _, info = s.solve(E, tol=1e-6, method="cg", max_iter=50000)
+    assert info["status"] == "FH_OK", info
+    assert info["outer_iters"] >= 1
+    e0 = oracle.operator.macroscopic_field(E, (N, N))
+    r = e0 - oracle.apply_A(x.cpu().numpy(), phase, L, L0)
+    rel_o = float(np.linalg.norm(r) / np.linalg.norm(e0))
+    assert 0.0 < rel_o <= 1e-6
+    assert abs(info["rel_res_true"] - rel_o) <= 1e-11, (info["rel_res_true"], rel_o)
+
+
 def test_fp32_plain_converges():
     torch = cuda_or_skip()
     from paper_1004_1122_gb300 import fh
