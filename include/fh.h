@@ -67,8 +67,8 @@ typedef enum {
   FH_FP32 = 1,         /* float32 vectors and FFTs, float64 scalars (no refinement) */
   FH_FP32_REFINED = 2  /* float32 inner solves on A d = r, float64 outer residual
                           r = e0 - A x and float64 x += d until the float64 residual
-                          meets the tolerance.  The outer residual's fields and row
-                          passes are float64; in 2-D its Green pass runs in
+                          meets the tolerance.  The outer residual's fields and
+                          pointwise work are float64; in 2-D its FFTs run in
                           double-float arithmetic (two float32 parts, ~48 bits:
                           residual accurate to ~1e-14 |e0| instead of ~1e-16) */
 } fh_precision;

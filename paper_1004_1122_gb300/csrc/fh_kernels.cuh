@@ -139,6 +139,7 @@ template <typename T> struct RowArgs {
   int tpl;        // threads per sequence
   int nseq;       // complex sequences per CTA
   const cplx<T>* tw;
+  const dfc* twdf;          // line twiddles as double-floats: run the line FFT in double-float
   cplx<T>* S;
   const uint8_t* phase;
   const T* tab;   // per-phase d x d table (dL, or L for the equilibrium norm), T
@@ -246,6 +247,25 @@ __device__ __forceinline__ void prefetch_range(const void* p, long long bytes) {
   for (long long i = threadIdx.x; i < nl; i += blockDim.x) prefetch_l2(b + i * 128);
 }
 
+// Line FFTs of float64 sequences in double-float arithmetic: the packed
+// sequences are split in place into hi + lo float32 parts (a complex
+// double-float takes the 16 bytes of a double2), transformed on the float32
+// pipes and recombined in place.  Used by the float64 residual passes, whose
+// pointwise work stays float64.  Every thread of the CTA calls it.
+template <bool INV>
+__device__ __forceinline__ void line_fft_df(double2* sm, int nseq, int n, const FFTPlan& plan, int tpl,
+                                            const dfc* __restrict__ twdf) {
+  dfc* smd = reinterpret_cast<dfc*>(sm);
+  const int tot = nseq * n;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) smd[i] = dfc_from(sm[i]);
+  __syncthreads();
+  const int s = threadIdx.x / tpl;
+  const int u = s < nseq ? threadIdx.x - s * tpl : n;  // idle threads never touch smem
+  fft_plan<INV, dfl, DynPlan>(smd + (size_t)(s < nseq ? s : 0) * n, 1, plan, u, tpl, twdf);
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) sm[i] = dfc_to(smd[i]);
+  __syncthreads();
+}
+
 // ----------------------------------------------------------------------------
 // row forward pass
 // ----------------------------------------------------------------------------
@@ -256,7 +276,8 @@ enum : int {
   kProDirPlain = 3   // p = r + beta p; tau = p
 };
 
-template <typename T, int D, int NL, int PRO, typename PS = DynPlan>
+// DF (float64 only): the line FFT runs in double-float arithmetic (line_fft_df).
+template <typename T, int D, int NL, int PRO, typename PS = DynPlan, bool DF = false>
 __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks) k_row_fwd(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -369,7 +390,10 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
   __syncthreads();
 
   // 2. forward FFT of every sequence
-  {
+  if constexpr (DF) {
+    static_assert(std::is_same<T, double>::value, "double-float line FFTs are for float64 rows");
+    line_fft_df<false>(sm, a.nseq, n, a.plan, a.tpl, a.twdf);
+  } else {
     const int s = threadIdx.x / a.tpl;
     const int u = s < a.nseq ? threadIdx.x - s * a.tpl : n;  // idle threads never touch smem
     fft_plan<false, T, PS>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
@@ -839,7 +863,8 @@ enum : int {
   kEpiResid = 5     // out = rhs - in - y, dot |out|^2     [residual]
 };
 
-template <typename T, int D, int NL, int EPI, typename PS = DynPlan>
+// DF (float64 only): the line FFT runs in double-float arithmetic (line_fft_df).
+template <typename T, int D, int NL, int EPI, typename PS = DynPlan, bool DF = false>
 __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks) k_row_inv(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -905,7 +930,10 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
   __syncthreads();
 
   // 2. inverse FFT
-  {
+  if constexpr (DF) {
+    static_assert(std::is_same<T, double>::value, "double-float line FFTs are for float64 rows");
+    line_fft_df<true>(sm, a.nseq, n, a.plan, a.tpl, a.twdf);
+  } else {
     const int s = threadIdx.x / a.tpl;
     const int u = s < a.nseq ? threadIdx.x - s * a.tpl : n;
     fft_plan<true, T, PS>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);

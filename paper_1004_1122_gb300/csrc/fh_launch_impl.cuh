@@ -41,7 +41,9 @@ template <int D, int NL>
 using CtPlan = typename std::conditional<D == 2, typename std::conditional<NL == 1, Plan2187, Plan729>::type,
                                          Plan243>::type;
 
-// The double-float Green pass exists for the 2-D float64 pipelines.
+// The double-float passes of the float64 residual (Green pass, and the A x and
+// residual row passes with double-float line FFTs) exist for the 2-D float64
+// pipelines.
 template <typename T, int D>
 constexpr bool kHasDf = std::is_same<T, double>::value && D == 2;
 
@@ -75,11 +77,22 @@ struct Launchers {
     FH_SM((k_col<T, D, kColEta>), c0)
     FH_SM((k_col<T, D, kColFwd>), c1)
     FH_SM((k_col<T, D, kColInv>), c1)
-    if constexpr (kHasDf<T, D>) FH_SM((k_col_green_df<>), c0)
+    if constexpr (kHasDf<T, D>) {
+      FH_SM((k_col_green_df<>), c0)
+      FH_SM((k_row_fwd<T, D, NL, kProApply, DynPlan, true>), rs)
+      FH_SM((k_row_inv<T, D, NL, kEpiResid, DynPlan, true>), rs)
+    }
 #undef FH_SM
     return cudaSuccess;
   }
   static cudaError_t row_fwd(int pro, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
+    if constexpr (kHasDf<T, D>) {
+      if (a.twdf != nullptr) {  // float64 residual: double-float line FFTs
+        if (pro != kProApply) return cudaErrorInvalidValue;
+        k_row_fwd<T, D, NL, kProApply, DynPlan, true><<<L.grid, L.block, L.smem, st>>>(a);
+        return cudaGetLastError();
+      }
+    }
     if constexpr (kHasCt<T, D, NL>) {
       using P = CtPlan<D, NL>;
       if (pro == kProDir && L.block <= RowBounds<P>::threads && cplan_is<P>(a.plan)) {
@@ -97,6 +110,13 @@ struct Launchers {
     return cudaGetLastError();
   }
   static cudaError_t row_inv(int epi, const Launch& L, const RowArgs<T>& a, cudaStream_t st) {
+    if constexpr (kHasDf<T, D>) {
+      if (a.twdf != nullptr) {  // float64 residual: double-float line FFTs
+        if (epi != kEpiResid) return cudaErrorInvalidValue;
+        k_row_inv<T, D, NL, kEpiResid, DynPlan, true><<<L.grid, L.block, L.smem, st>>>(a);
+        return cudaGetLastError();
+      }
+    }
     if constexpr (kHasCt<T, D, NL>) {
       using P = CtPlan<D, NL>;
       if (epi == kEpiDir && L.block <= RowBounds<P>::threads && cplan_is<P>(a.plan)) {

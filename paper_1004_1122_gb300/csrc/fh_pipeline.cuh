@@ -79,6 +79,7 @@ struct Pipeline {
   C* tw0 = nullptr;
   C* tw1 = nullptr;
   dfc* tw0_df = nullptr;     // 2-D float64: axis-0 twiddles as double-floats (lt.col_df)
+  dfc* tw_last_df = nullptr; // 2-D float64: line twiddles as double-floats
   bool df_green = false;     // route the next Green passes through lt.col_df
   C* S = nullptr;
   T* dtab = nullptr;   // dL per phase
@@ -169,8 +170,8 @@ struct Pipeline {
   // out[l] = ||x_l||^2 (sum over the vector), synchronous
   int norm2(T* const* v, double* out, std::string& err);
   // ||rhs - A x||^2 per load into out (synchronous), residual field into r.
-  // df: run the Green pass in double-float arithmetic where the pipeline has
-  // that kernel (2-D float64); the other passes stay in T.
+  // df: run the FFTs of the three passes in double-float arithmetic where the
+  // pipeline has those kernels (2-D float64); the pointwise work stays in T.
   int residual(const T* const* xin, T* const* rout, bool rhs_field, const double (*E)[kMaxD],
                double* out, std::string& err, bool df = false);
   // column of <tab e> (tab = L) in float64

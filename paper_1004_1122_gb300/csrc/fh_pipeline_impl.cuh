@@ -262,16 +262,22 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   if ((rc = upload_tw(pb.N[0], &tw0))) return rc;
   if (d == 3 && (rc = upload_tw(pb.N[1], &tw1))) return rc;
   if (d == 2 && lt.col_df) {
-    // axis-0 twiddles as complex double-floats: hi = fl32(w), lo = fl32(w - hi)
-    std::vector<double> re, im;
-    twiddles(pb.N[0], re, im);
-    std::vector<dfc> h(pb.N[0]);
-    for (int m = 0; m < pb.N[0]; ++m) {
-      h[m].x = dfl(re[m]);
-      h[m].y = dfl(im[m]);
-    }
-    if ((rc = dev_alloc(allocs, &tw0_df, pb.N[0], err))) return rc;
-    FH_CKS(cudaMemcpy(tw0_df, h.data(), pb.N[0] * sizeof(dfc), cudaMemcpyHostToDevice));
+    // twiddles as complex double-floats: hi = fl32(w), lo = fl32(w - hi)
+    auto upload_tw_df = [&](int n, dfc** dst) -> int {
+      std::vector<double> re, im;
+      twiddles(n, re, im);
+      std::vector<dfc> h(n);
+      for (int m = 0; m < n; ++m) {
+        h[m].x = dfl(re[m]);
+        h[m].y = dfl(im[m]);
+      }
+      int r2 = dev_alloc(allocs, dst, n, err);
+      if (r2) return r2;
+      FH_CKS(cudaMemcpy(*dst, h.data(), n * sizeof(dfc), cudaMemcpyHostToDevice));
+      return 0;
+    };
+    if ((rc = upload_tw_df(pb.N[0], &tw0_df))) return rc;
+    if ((rc = upload_tw_df(g.nlast, &tw_last_df))) return rc;
   }
   {
     const int nt = std::max(1, nphase) * d * d * ncell;
@@ -609,7 +615,8 @@ int Pipeline<T>::residual(const T* const* xin, T* const* rout, bool rhs_field,
     a.out[l] = rout[l];
     a.rhs[l] = rhs_field ? rhs[l] : nullptr;
   }
-  df_green = df && lt.col_df != nullptr && tw0_df != nullptr;
+  df_green = df && lt.col_df != nullptr && tw0_df != nullptr && tw_last_df != nullptr;
+  if (df_green) a.twdf = tw_last_df;
   const cudaError_t pe = passes(kProApply, kEpiResid, a, a, scal_aux);
   df_green = false;
   FH_CKS(pe);
