@@ -71,6 +71,9 @@ def parse():
                          "(for profiler captures)")
     ap.add_argument("--probe", action="store_true",
                     help="only time each pass kernel a few times (small command for ncu captures)")
+    ap.add_argument("--probe-residual", action="store_true",
+                    help="one refined 729^2 solve, whose two float64 residuals run the double-float "
+                         "passes (small command for ncu captures)")
     return ap.parse_args()
 
 
@@ -855,8 +858,24 @@ def run_probe_nn():
     net.close()
 
 
+def run_probe_residual():
+    from paper_1004_1122_gb300 import fh
+    from paper_1004_1122_gb300 import microstructure as micro
+
+    phase = micro.rsa_disks(729, 0.3, 8, 16, seed=micro.config_seed(2, 729))
+    L = micro.isotropic_table([1.0, 100.0], 2)
+    with fh.Solver(phase, L, precision="fp32_refined") as s:
+        _, _, info = s.solve([1.0, 0.0], tol=1e-6, method="cg", max_iter=20000)
+    print(json.dumps({"probe_residual": {"status": info["status"], "iters": info["iters"],
+                                         "outer_iters": info["outer_iters"],
+                                         "rel_res_true": info["rel_res_true"]}}))
+
+
 def main():
     args = parse()
+    if args.probe_residual:
+        run_probe_residual()
+        return
     if args.probe_nn:
         run_probe_nn()
         return
