@@ -351,6 +351,21 @@ def spectrum_bytes(n0, n1, d, s):
     return 2 * s * d * ((n1 + 1) // 2) * n0  # half spectrum, complex
 
 
+def pass_bytes(n, d, s):
+    """Algorithmic bytes per launch of the four CG-iteration pass kernels on an
+    n x n grid, d components of s bytes: (profile index, bytes).  One CG
+    iteration of the 2-D solver reads and writes exactly these (Section 3's CG
+    with the operator of Eq. mtrx_B split into the row, Green and row passes)."""
+    nodes = n * n
+    spec = spectrum_bytes(n, n, d, s)
+    return {
+        "row_fwd": (0, (3 * d * s + 1) * nodes + spec),          # read r, p, phase; write p, spectrum
+        "col_green": (1, 2 * spec),                              # read + write spectrum
+        "row_inv": (2, spec + 2 * d * s * nodes),                # read spectrum, p; write A p
+        "cg_update": (3, 6 * d * s * nodes),                     # read x, p, r, A p; write x, r
+    }
+
+
 def run_fh(args):
     import numpy as np
     import torch
@@ -444,12 +459,7 @@ def run_fh(args):
     s4, d = 4, 2
     nodes = N * N
     spec = spectrum_bytes(N, N, d, s4)
-    kern = {
-        "row_fwd": (0, (3 * d * s4 + 1) * nodes + spec),          # read r, p, phase; write p, spectrum
-        "col_green": (1, 2 * spec),                              # read + write spectrum
-        "row_inv": (2, spec + 2 * d * s4 * nodes),               # read spectrum, p; write A p
-        "cg_update": (3, 6 * d * s4 * nodes),                    # read x, p, r, A p; write x, r
-    }
+    kern = pass_bytes(N, d, s4)
     times = {k: prof.profile(w, reps=30) for k, (w, _) in kern.items()}
     t_apply = prof.profile(5, reps=30)
     peak, peak_src = load_peaks()
