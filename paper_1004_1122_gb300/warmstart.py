@@ -9,9 +9,10 @@ fields e^(b) - e_b of the d unit loads, and the warm start for a load E is
 
 with Q the compatible projection of Section 2.1 (``fh_nn_warm_start``), so
 that x0 - E is a zero-mean compatible field, the subspace on which the
-Krylov iterates of Section 3 live.  Plain CG from e = E stays the judge: the
-warm start is used only when its true residual is below the cold start's,
-and both run to the same tolerance on the same operator.
+Krylov iterates of Section 3 live.  Plain CG from e = E stays the fallback
+and the yardstick: the warm start is used only when its true residual is
+below the cold start's, and both run to the same tolerance on the same
+operator.
 
 This module sequences the library calls (features, targets, training steps,
 prediction, solves); every arithmetic step runs in the library's kernels.

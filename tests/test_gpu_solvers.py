@@ -1,6 +1,6 @@
 """Parity of fh_solve (CUDA) with the oracle's solvers.
 
-Bars (spec accuracy targets): float64 path <= 1e-10 relative error of the
+Bars (the accuracy targets of the method): float64 path <= 1e-10 relative error of the
 field and of L_eff against the oracle's tight solution; float32 + float64
 refinement <= 1e-6.  Comparisons are made at tolerances where the iteration
 error is below those bars (the field error is at most kappa times the
