@@ -150,7 +150,9 @@ fh_status fh_apply(fh_ctx* ctx, const void* e_in, void* e_out, int transpose, in
  *  Leff_col   host, d float64 for <L e> (column of L_eff for unit E), or NULL.
  *  info       host, or NULL.
  * Returns FH_OK, FH_ERR_NOT_CONVERGED (e_out still holds the last iterate),
- * FH_ERR_BREAKDOWN, FH_ERR_ARG or FH_ERR_CUDA. */
+ * FH_ERR_BREAKDOWN, FH_ERR_ARG, FH_ERR_CUDA, or FH_ERR_TIMEOUT (a bounded
+ * device wait expired, or the iteration guard ran out without a device
+ * status; the context stays usable). */
 fh_status fh_solve(fh_ctx* ctx, const double* E, double tol, int method, int max_iter,
                    const double* e_init, double* e_out, double* Leff_col, fh_info* info);
 
@@ -160,7 +162,8 @@ fh_status fh_solve(fh_ctx* ctx, const double* E, double tol, int method, int max
  * one).  The first call allocates a second set of buffers sized for d loads,
  * kept until fh_destroy.  Leff receives L_eff row-major (column b from load b).
  * infos: host array of d fh_info (iters, outer_iters, status, rel_res_true,
- * launches are filled), or NULL.  Returns the first non-OK status. */
+ * launches are filled), or NULL.  Returns the first non-OK status (the
+ * statuses of fh_solve, FH_ERR_TIMEOUT included). */
 fh_status fh_solve_all(fh_ctx* ctx, double tol, int method, int max_iter,
                        double* Leff, fh_info* infos);
 
@@ -248,7 +251,8 @@ fh_status fh_batch_create(fh_batch** out, int ncells, const int* N, const uint8_
  *  summary  host, or NULL: total iterations, refinement steps, worst true
  *           residual, kernels launched.
  * Returns FH_OK if every (cell, load) converged, else the first failure
- * status.  Synchronises. */
+ * status (FH_ERR_TIMEOUT when a bounded device wait expired or the round
+ * guard ran out).  Synchronises. */
 fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, int max_iter,
                          double* Leff, int* status, int* iters, fh_info* summary);
 
