@@ -347,17 +347,16 @@ fh_status fh_create(fh_ctx** out, int d, const int* N, const double* Y, const ui
     for (int i = 0; i < d * d; ++i) pb.dL[(size_t)p * d * d + i] = pb.L[(size_t)p * d * d + i] - pb.L0[i];
   c->precision = precision;
 
-  cudaError_t e;
   if (stream) {
     c->st = (cudaStream_t)stream;
   } else {
-    if ((e = cudaStreamCreate(&c->st)) != cudaSuccess) {
+    if (cudaStreamCreate(&c->st) != cudaSuccess) {
       fh_destroy(c);
       return FH_ERR_CUDA;
     }
     c->own_stream = true;
   }
-  if ((e = cudaMalloc(&c->d_phase, pb.nodes)) != cudaSuccess) {
+  if (cudaMalloc(&c->d_phase, pb.nodes) != cudaSuccess) {
     fh_destroy(c);
     return FH_ERR_OOM;
   }
@@ -596,7 +595,7 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
     int total = 0, outer = 0, status = fh::kCap, hist_len = 0;
     double prev_rel = INFINITY;
     SolveResult res;
-    double last_alpha = 0.0, last_inner_b = 0.0;
+    double last_alpha = 0.0;
     bool done_first = false;
     if (!e_init) {
       // From e = E the first correction solves A d = -B E, whose complement
@@ -666,14 +665,12 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
       total += res.iters;
       hist_len = res.iters + 1;
       last_alpha = res.alpha;
-      last_inner_b = rr;
       ++c->own_launches;
       k_add_float<<<vec_grid(len), 256, 0, c->st>>>(c->d_x64, P->x[0], len);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "refine add");
       ++outer;
       if (res.status == fh::kBreakdown && res.iters == 0) { status = fh::kBreakdown; break; }
     }
-    (void)last_inner_b;
     if (info) {
       info->iters = total;
       info->outer_iters = outer;
