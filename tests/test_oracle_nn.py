@@ -116,3 +116,45 @@ def test_adam_scalar_recurrence():
         vv = 0.999 * vv + 0.001 * g * g
         q -= 0.01 * (mm / (1 - 0.9 ** t)) / (np.sqrt(vv / (1 - 0.999 ** t)) + 1e-8)
     assert np.isclose(p[0], q)
+
+
+def test_adam_matches_kingma_ba_by_hand():
+    """Adam (Kingma & Ba, Algorithm 1) with lr 0.01, beta1 0.9, beta2 0.999,
+    eps 1e-8, from m = v = 0, values written out by hand.
+
+    Step 1 (g = 0.5): m = 0.05, v = 2.5e-4, m_hat = g, v_hat = g^2, so the
+    update is lr g / (|g| + eps) = 0.01 * 0.5 / 0.50000001 and
+    p = 1 - 0.0099999998 = 0.9900000002.
+    Step 2 (g = -0.2): m = 0.9 * 0.05 - 0.02 = 0.025,
+    v = 0.999 * 2.5e-4 + 0.001 * 0.04 = 2.8975e-4, m_hat = 0.025 / 0.19,
+    v_hat = 2.8975e-4 / 0.001999, p = 0.9900000002 - 0.01 m_hat / (sqrt(v_hat) + eps)
+    = 0.98654394181165106 (evaluated to 30 digits).
+    A wrong bias correction (none, or beta^(t-1)) or a swapped beta moves
+    either step by far more than the tolerance."""
+    p = np.array([1.0, -2.0])
+    m = np.zeros(2)
+    v = np.zeros(2)
+    nn.adam(p, np.array([0.5, -3.0]), m, v, 1, lr=0.01)
+    assert abs(p[0] - 0.9900000002) < 1e-15
+    # the first step is lr * sign(g) up to eps whatever |g|: -2 + 0.01 * 3 / (3 + 1e-8)
+    assert abs(p[1] - (-2.0 + 0.03 / 3.00000001)) < 1e-15
+    assert np.allclose(m, [0.05, -0.3], rtol=0, atol=1e-16)
+    assert np.allclose(v, [2.5e-4, 9e-3], rtol=1e-15, atol=0)
+    nn.adam(p, np.array([-0.2, 0.0]), m, v, 2, lr=0.01)
+    assert abs(m[0] - 0.025) < 1e-16 and abs(v[0] - 2.8975e-4) < 1e-18
+    assert abs(p[0] - 0.98654394181165106) < 1e-14
+
+
+def test_leaky_and_mse_literal_values():
+    """Leaky ReLU with slope 0.1 on the negative side, and the mean squared
+    error over every entry with gradient 2 (y - t) / count, on literal values."""
+    x = np.array([-2.0, -0.5, 0.0, 0.3, 4.0])
+    assert np.array_equal(nn.leaky(x), np.array([-0.2, -0.05, 0.0, 0.3, 4.0]))
+    g = np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+    assert np.allclose(nn.leaky_backward(x, g), [0.1, 0.2, 0.3, 4.0, 5.0], rtol=0, atol=1e-15)
+    y = np.array([[1.0, 2.0], [3.0, 4.0]])
+    t = np.array([[0.0, 0.0], [1.0, 6.0]])
+    loss, gy = nn.mse(y, t)
+    # diff = [[1, 2], [2, -2]]: squares 1 + 4 + 4 + 4 = 13 over 4 entries
+    assert loss == 13.0 / 4.0
+    assert np.array_equal(gy, np.array([[0.5, 1.0], [1.0, -1.0]]))
