@@ -91,10 +91,18 @@ typedef struct {
   int history_len;        /* out: entries written */
   long long launches;     /* out: CUDA kernels this call launched (graph replays included) */
   int flags;              /* in: FH_INFO_ETA_E requests eta_e (one float64 operator pass) */
+  int ct_plans;           /* out: FH_CT_* bits of the compile-time FFT plans whose kernels
+                             ran every pass of the float32 CG iterations of this call
+                             (0: run-time-plan kernels, or no float32 CG iteration) */
 } fh_info;
 
 /* fh_info.flags bits */
 #define FH_INFO_ETA_E 1
+
+/* fh_info.ct_plans bits: compile-time plans of the float32 CG-iteration passes */
+#define FH_CT_2187 1      /* 2-D, one load per launch, 2187 = 27 * 27 * 3 along both axes */
+#define FH_CT_729 2       /* 2-D, two loads per launch, 729 = 27 * 27 along both axes */
+#define FH_CT_243 4       /* 3-D, one or three loads per launch, 243 = 27 * 9 along every axis */
 
 /* fh_create -- build a solver context for one microstructure.
  *
@@ -149,10 +157,10 @@ fh_status fh_apply(fh_ctx* ctx, const void* e_in, void* e_out, int transpose, in
  *  e_out      device float64 [d][N...] for the solution, or NULL.
  *  Leff_col   host, d float64 for <L e> (column of L_eff for unit E), or NULL.
  *  info       host, or NULL.
- * Returns FH_OK, FH_ERR_NOT_CONVERGED (e_out still holds the last iterate),
- * FH_ERR_BREAKDOWN, FH_ERR_ARG, FH_ERR_CUDA, or FH_ERR_TIMEOUT (a bounded
- * device wait expired, or the iteration guard ran out without a device
- * status; the context stays usable). */
+ * Returns FH_OK, FH_ERR_NOT_CONVERGED (the iteration cap, or the host's
+ * iteration guard ran out without a device status; e_out still holds the
+ * last iterate), FH_ERR_BREAKDOWN, FH_ERR_ARG, FH_ERR_CUDA, or FH_ERR_TIMEOUT
+ * (a bounded device wait expired; the context stays usable). */
 fh_status fh_solve(fh_ctx* ctx, const double* E, double tol, int method, int max_iter,
                    const double* e_init, double* e_out, double* Leff_col, fh_info* info);
 
@@ -251,8 +259,8 @@ fh_status fh_batch_create(fh_batch** out, int ncells, const int* N, const uint8_
  *  summary  host, or NULL: total iterations, refinement steps, worst true
  *           residual, kernels launched.
  * Returns FH_OK if every (cell, load) converged, else the first failure
- * status (FH_ERR_TIMEOUT when a bounded device wait expired or the round
- * guard ran out).  Synchronises. */
+ * status (FH_ERR_TIMEOUT when a bounded device wait expired,
+ * FH_ERR_NOT_CONVERGED when the host's round guard ran out).  Synchronises. */
 fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, int max_iter,
                          double* Leff, int* status, int* iters, fh_info* summary);
 
@@ -301,10 +309,12 @@ void fh_batch_destroy(fh_batch* b);
  * host threads) race and give wrong results: order them.  The first call on
  * each device (with that device current) performs a one-time set-up -- it
  * looks up the arrays' device addresses and raises the kernels' shared-memory
- * limit -- and should come before any stream capture on that device.  The
- * call is asynchronous on `stream` apart from small table uploads from host
- * memory.  Errors: FH_ERR_ARG, FH_ERR_EVEN_N, FH_ERR_NOT_SPD,
- * FH_ERR_UNSUPPORTED, FH_ERR_CUDA. */
+ * limit, both kept until the process exits -- and should come before any
+ * stream capture on that device; resetting the device (cudaDeviceReset)
+ * after that first call is not supported.  Every call is asynchronous on
+ * `stream`: its twiddle and dL tables are filled by a kernel on that stream
+ * (nothing is copied from host memory).  Errors: FH_ERR_ARG, FH_ERR_EVEN_N,
+ * FH_ERR_NOT_SPD, FH_ERR_UNSUPPORTED, FH_ERR_CUDA. */
 fh_status fh_apply_noalloc(int d, const int* N, const double* Y, const uint8_t* phase,
                            int nphase, const double* L, const double* L0, const double* e_in,
                            double* e_out, int transpose, void* stream, char* errbuf,

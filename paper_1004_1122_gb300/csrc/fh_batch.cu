@@ -345,7 +345,12 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
         all = all && done[gi];
       }
       if (all) break;
-      if (round > (long long)max_iter + 64) return FH_ERR_TIMEOUT;
+      if (round > (long long)max_iter + 64) {
+        // the host ran out of rounds before every item reported a status: an
+        // iteration overrun, not an expired device wait
+        err = "iteration guard exceeded without a device status";
+        return FH_ERR_NOT_CONVERGED;
+      }
     }
     for (int gi = 0; gi < ng; ++gi) {
       Group& g = *groups[gi];
@@ -467,7 +472,10 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
           all = all && !active[gi];
         }
         if (all) break;
-        if (round > (long long)budget + 64) return FH_ERR_TIMEOUT;
+        if (round > (long long)budget + 64) {
+          err = "iteration guard exceeded without a device status";
+          return FH_ERR_NOT_CONVERGED;
+        }
       }
       for (int gi = 0; gi < ng; ++gi) {
         Group& g = *groups[gi];
@@ -561,6 +569,10 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
     summary->eta_e = NAN;
     summary->history_len = 0;
     summary->launches = launches - launches0;
+    summary->ct_plans = 0;
+    if (method == FH_CG)
+      for (Group& g : b->groups)
+        if (g.p32) summary->ct_plans |= fh::ct_plan_bit(g.p32->ct_plan);
   }
   for (Group& g : b->groups)
     if (cudaStreamSynchronize(g.st) != cudaSuccess) return FH_ERR_CUDA;
@@ -658,6 +670,7 @@ int solve_all_loads(const Problem& pb, int precision, double tol, int method, in
     res.rel[l] = rel[0][l];
   }
   res.launches = own + g->p64->launches + (g->p32 ? g->p32->launches : 0) - l0;
+  res.ct_plans = (method == FH_CG && g->p32) ? ct_plan_bit(g->p32->ct_plan) : 0;
   if (cudaStreamSynchronize(g->st) != cudaSuccess) return FH_ERR_CUDA;
   return 0;
 }

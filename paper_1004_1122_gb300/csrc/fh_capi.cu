@@ -550,6 +550,7 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
     info->iters = info->outer_iters = info->matvecs = 0;
     info->history_len = 0;
     info->launches = 0;
+    info->ct_plans = 0;
     info->rel_res_true = info->rel_res = info->eta_r = info->eta_e = NAN;
   }
   const long long launches0 = c->own_launches + (c->p32 ? c->p32->launches : 0) +
@@ -712,6 +713,7 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
     info->matvecs = info->iters * (method == FH_BICG ? 2 : 1) + 1 + info->outer_iters;
     info->launches = c->own_launches + (c->p32 ? c->p32->launches : 0) +
                      (c->p64 ? c->p64->launches : 0) - launches0;
+    info->ct_plans = (method == FH_CG && c->precision != FH_FP64 && c->p32) ? fh::ct_plan_bit(c->p32->ct_plan) : 0;
   }
   if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(c, e, "fh_solve");
   return st;
@@ -757,6 +759,7 @@ fh_status fh_solve_all(fh_ctx* c, double tol, int method, int max_iter, double* 
       inf.eta_e = NAN;
       inf.history_len = 0;
       inf.launches = r.launches;
+      inf.ct_plans = r.ct_plans;
     }
   }
   return first;

@@ -15,6 +15,7 @@ struct LoadsResult {
   double rel[kMaxLoads];   // float64 true relative residual per load
   int outer = 0;
   long long launches = 0;
+  int ct_plans = 0;        // fh_info.ct_plans bits of the float32 CG iterations
 };
 
 // Solves (I + B) e = e_b for b = 1..d with the loads batched (NL = d).  The

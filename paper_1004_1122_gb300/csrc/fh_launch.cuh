@@ -35,6 +35,12 @@ struct LaunchTable {
                              cudaStream_t) = nullptr;
   cudaError_t (*matnorm2)(const Launch&, const T*, long long nodes, int ncell, long long cell_nodes,
                           const Mat3&, double*, cudaStream_t) = nullptr;
+  // Length of the compile-time FFT plan that every pass kernel of a CG
+  // iteration (direction pass, A p pass, Green pass and, in 3-D, the
+  // middle-axis passes) runs for these plans and launch shapes, or 0 when at
+  // least one of them runs a run-time-plan kernel.
+  int (*ct_plan)(const FFTPlan& prow, const Launch& row, const FFTPlan& pc0, const Launch& col0,
+                 const FFTPlan& pc1, const Launch& col1) = nullptr;
 };
 
 // Supported (D, NL): (2, 1), (2, 2), (3, 1), (3, 3).

@@ -215,6 +215,17 @@ struct Launchers {
     k_matnorm2<T, D><<<L.grid, L.block, 0, st>>>(e, nodes, ncell, cell_nodes, m, part);
     return cudaGetLastError();
   }
+  static int ct_plan(const FFTPlan& prow, const Launch& row, const FFTPlan& pc0, const Launch& col0,
+                     const FFTPlan& pc1, const Launch& col1) {
+    if constexpr (kHasCt<T, D, NL>) {
+      using P = CtPlan<D, NL>;
+      bool ok = row.block <= RowBounds<P>::threads && cplan_is<P>(prow) &&
+                col0.block <= ColBounds<P>::threads && cplan_is<P>(pc0);
+      if (D == 3) ok = ok && col1.block <= ColBounds<P>::threads && cplan_is<P>(pc1);
+      return ok ? P::n : 0;
+    }
+    return 0;
+  }
   static LaunchTable<T> table() {
     LaunchTable<T> t;
     t.D = D;
@@ -233,6 +244,7 @@ struct Launchers {
     t.bicg_update = &bicg_update;
     t.current_sum = &current_sum;
     t.matnorm2 = &matnorm2;
+    t.ct_plan = &ct_plan;
     return t;
   }
 };

@@ -20,8 +20,15 @@
 //
 // Set-up: the first call on each device, with that device current, looks up
 // the device addresses of the arrays (cudaGetSymbolAddress) and raises the
-// pass kernels' shared-memory limit.  That first call should come before any
-// stream capture on the device.
+// pass kernels' shared-memory limit; both are kept for the life of the
+// process.  That first call should come before any stream capture on the
+// device.  A cudaDeviceReset (or any other teardown of the device's primary
+// context) after it is not supported: the kept addresses would be stale.
+//
+// Tables: every call fills the twiddle and dL arrays with a small kernel on
+// the caller's stream (the dL values travel as a by-value kernel argument), so
+// after the set-up every operation of a call is a kernel launch on that stream
+// and nothing is staged from host memory.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -48,6 +55,35 @@ struct DeviceSymbols {
   double2* tw = nullptr;
   double* tab = nullptr;
 };
+
+// The dL table of one call, passed by value (18 KB of kernel parameters).
+struct DLTable {
+  double v[kTabEntries];
+};
+
+// g_tw[off_k + m] = exp(-2 pi i m / n_k) for the (up to) three axis lengths,
+// back to back; g_tab[i] = dL entry i for i < nt and 0 beyond (phase ids that
+// have no tensor act as L = L0).
+__global__ void k_fill_tables(int n0, int n1, int n2, DLTable dl, int nt) {
+  const int total = n0 + n1 + n2;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    int m = i, n = n0;
+    if (m >= n0) {
+      m -= n0;
+      n = n1;
+      if (m >= n1) {
+        m -= n1;
+        n = n2;
+      }
+    }
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)n, &sn, &cs);
+    g_tw[i] = make_double2(cs, -sn);
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kTabEntries; i += stride)
+    g_tab[i] = i < nt ? dl.v[i] : 0.0;
+}
 
 DeviceSymbols g_dev[kMaxDevices];
 std::mutex g_mu;
@@ -85,9 +121,13 @@ fh_status device_setup(DeviceSymbols& s, char* errbuf, size_t errlen) {
   cudaError_t e = cudaGetSymbolAddress((void**)&s.scratch, g_scratch);
   if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.tw, g_tw);
   if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.tab, g_tab);
+  // raise the pass kernels' dynamic shared-memory limit to the device maximum
+  // once (the limit does not depend on the grid)
+  if (e == cudaSuccess) e = fh::launch_table<double>(2, 1).set_smem(0, 0, 0);
+  if (e == cudaSuccess) e = fh::launch_table<double>(3, 1).set_smem(0, 0, 0);
   if (e != cudaSuccess) {
     char msg[256];
-    std::snprintf(msg, sizeof msg, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    std::snprintf(msg, sizeof msg, "device set-up: %s", cudaGetErrorString(e));
     set_err(errbuf, errlen, msg);
     return FH_ERR_CUDA;
   }
@@ -258,40 +298,24 @@ extern "C" fh_status fh_apply_noalloc(int d, const int* N, const double* Y, cons
     col1.smem = (size_t)N[1] * cb1.Q * esz;
   }
   LaunchTable<double> lt = launch_table<double>(d, 1);
-  ce = lt.set_smem(row.smem, col0.smem, d == 3 ? col1.smem : 0);
-  if (ce != cudaSuccess) { set_err(errbuf, errlen, cudaGetErrorString(ce)); return FH_ERR_CUDA; }
-
-  // ---- tables into the static arrays (staged from host stack memory) ----
-  double2 htw[3 * kMaxAxis];
-  const int lens[3] = {g.nlast, N[0], d == 3 ? N[1] : 0};
-  int offs[3] = {0, 0, 0};
-  int total = 0;
-  for (int k = 0; k < 3; ++k) {
-    offs[k] = total;
-    const int n = lens[k];
-    for (int m = 0; m < n; ++m) {
-      long long num = 8LL * m, den = n;
-      double sgn_s = 1.0, sgn_c = 1.0;
-      bool swap = false;
-      if (2 * num >= 8 * den) { num = 8 * den - num; sgn_s = -1.0; }
-      if (2 * num > 4 * den) { num = 4 * den - num; sgn_c = -1.0; }
-      if (num > den) { num = 2 * den - num; swap = true; }
-      const double x = (ct::kPi / 4.0) * (double)num / (double)den;
-      double c = std::cos(x), s = std::sin(x);
-      if (swap) { const double t = c; c = s; s = t; }
-      htw[total + m].x = sgn_c * c;
-      htw[total + m].y = -(sgn_s * s);
-    }
-    total += n;
+  if (col0.smem > (size_t)optin || (d == 3 && col1.smem > (size_t)optin)) {
+    set_err(errbuf, errlen, "column pass does not fit one CTA");
+    return FH_ERR_UNSUPPORTED;
   }
-  double htab[kTabEntries];
-  const int nt = 256 * d * d;  // unused phase ids carry dL = 0
-  for (int i = 0; i < nt; ++i) htab[i] = 0.0;
-  for (int p = 0; p < nphase; ++p)
-    for (int i = 0; i < d * d; ++i) htab[p * d * d + i] = L[(size_t)p * d * d + i] - L0[i];
-  ce = cudaMemcpyAsync(sym.tw, htw, total * sizeof(double2), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(sym.tab, htab, nt * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (ce != cudaSuccess) { set_err(errbuf, errlen, cudaGetErrorString(ce)); return FH_ERR_CUDA; }
+
+  // ---- tables into the static arrays, filled on the device --------------
+  const int lens[3] = {g.nlast, N[0], d == 3 ? N[1] : 0};
+  const int offs[3] = {0, lens[0], lens[0] + lens[1]};
+  {
+    DLTable dl;
+    const int nt = nphase * d * d;
+    for (int p = 0; p < nphase; ++p)
+      for (int i = 0; i < d * d; ++i) dl.v[p * d * d + i] = L[(size_t)p * d * d + i] - L0[i];
+    for (int i = nt; i < kTabEntries; ++i) dl.v[i] = 0.0;
+    k_fill_tables<<<8, 256, 0, st>>>(lens[0], lens[1], lens[2], dl, nt);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) { set_err(errbuf, errlen, cudaGetErrorString(ce)); return FH_ERR_CUDA; }
+  }
 
   // ---- the three (2-D) or five (3-D) passes ------------------------------
   RowArgs<double> a;

@@ -121,6 +121,7 @@ struct Pipeline {
   std::map<int, long long> graph_kernels;    // kernels per captured chunk
 
   Tuning tuning{};   // the shape actually in use
+  int ct_plan = 0;   // compile-time plan length of the CG-iteration passes (0: run-time plans)
   int init(const Problem& pb, int nloads_, bool krylov, cudaStream_t stream, std::string& err,
            const Tuning* want = nullptr);
   // Time the CG-iteration pass kernels for candidate tunings (temporary
@@ -191,6 +192,9 @@ struct Pipeline {
   // 2 row_inv (inverse FFT + A p + dot), 3 CG vector update, 5 operator apply.
   int profile(int what, int reps, double* ms, std::string& err);
 };
+
+// fh_info.ct_plans bit of a compile-time plan length (FH_CT_2187, FH_CT_729, FH_CT_243).
+inline int ct_plan_bit(int n) { return n == 2187 ? 1 : n == 729 ? 2 : n == 243 ? 4 : 0; }
 
 extern template struct Pipeline<float>;
 extern template struct Pipeline<double>;

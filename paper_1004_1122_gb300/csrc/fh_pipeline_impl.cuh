@@ -240,6 +240,8 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     cudaGetLastError();  // clear a refused opt-in
   }
   tuning.pipe = green_pipe ? 1 : 0;
+  ct_plan = lt.ct_plan(prow, row, pcol0, green_pipe ? colp : col0, pcol1, col1);
+  if (green_pipe && nloads != 1) ct_plan = 0;  // the persistent Green pass has no two-load plan
 
   // device buffers
   int rc;
@@ -702,7 +704,7 @@ int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int
     if (solve_done()) break;
     if (++run_guard_ > run_guard_max_) {
       err = "iteration guard exceeded without a device status";
-      return 8;  // FH_ERR_TIMEOUT
+      return 6;  // FH_ERR_NOT_CONVERGED: a host-side overrun, not an expired device wait
     }
   }
   solve_results(res);

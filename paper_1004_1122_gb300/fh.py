@@ -15,10 +15,29 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libfh.so")
-# Launch-shape cache read by fh_create and written by fh_autotune (see fh.h);
-# the package ships the shapes tuned on GB300 for its benchmark grids.
-TUNE_CACHE = os.path.join(_HERE, "tune_cache.txt")
-os.environ.setdefault("FH_TUNE_CACHE", TUNE_CACHE)
+# Launch-shape cache read by fh_create and written by fh_autotune (see fh.h).
+# The package ships the shapes tuned on GB300 for its benchmark grids as a
+# read-only seed; runs read and append to a private copy next to the built
+# library (never to the shipped file), unless FH_TUNE_CACHE names another file.
+TUNE_SEED = os.path.join(_HERE, "tune_cache.txt")
+TUNE_CACHE = os.path.join(_HERE, "lib", "tune_cache.txt")
+
+
+def _default_tune_cache() -> str:
+    if not os.path.exists(TUNE_CACHE):
+        try:
+            os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
+            with open(TUNE_SEED) as src, open(TUNE_CACHE, "x") as dst:
+                dst.write(src.read())
+        except FileExistsError:
+            pass
+        except OSError:  # read-only install: read the seed, tune results are not kept
+            return TUNE_SEED
+    return TUNE_CACHE
+
+
+if "FH_TUNE_CACHE" not in os.environ:
+    os.environ["FH_TUNE_CACHE"] = _default_tune_cache()
 
 FH_OK = 0
 STATUS = {
@@ -59,7 +78,11 @@ class FhInfo(ctypes.Structure):
         ("history_len", ctypes.c_int),
         ("launches", ctypes.c_longlong),
         ("flags", ctypes.c_int),
+        ("ct_plans", ctypes.c_int),
     ]
+
+
+CT_PLANS = {1: 2187, 2: 729, 4: 243}  # fh_info.ct_plans bits (FH_CT_*)
 
 
 class FhError(RuntimeError):
@@ -173,6 +196,7 @@ def _info_dict(info: FhInfo, hist: Optional[np.ndarray]) -> dict:
         "eta_r": info.eta_r,
         "eta_e": info.eta_e,
         "launches": info.launches,
+        "ct_plans": [n for bit, n in CT_PLANS.items() if info.ct_plans & bit],
     }
     if hist is not None:
         out["history"] = hist[: info.history_len].copy()

@@ -4,10 +4,12 @@ Some callers cannot call cudaMalloc (a framework that owns every device
 allocation through its own pool, a latency-critical loop that cannot afford
 cudaMalloc's implicit synchronisation, a fixed device-memory budget).  For
 them the library offers fh_apply_noalloc, whose scratch lives in fixed arrays
-inside the library.  This file checks, through the C ABI, that two calls in a
-row (different grids, so the second call reuses scratch the first one left
-behind) give the same result as fh_apply within the operator tolerance used
-by tests/test_gpu_operator.py, and that oversize grids are refused.
+inside the library.  This file checks, through the C ABI, that calls in a row
+(different grids, so each call reuses scratch the previous one left behind)
+give the oracle's product (I + B) e or (I + B^T) e element by element within
+the operator tolerance of tests/test_gpu_operator.py, for both products on
+both grids, in place (e_in == e_out) as well as out of place, with phase ids
+beyond the table (which act as L = L0), and that oversize grids are refused.
 
 The file name sorts last so that a run stopping at its first failure has
 already run every other test.
@@ -17,6 +19,8 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
+
 from gpu_util import cuda_or_skip, spd
 
 pytestmark = pytest.mark.gpu
@@ -24,47 +28,53 @@ pytestmark = pytest.mark.gpu
 U64 = 2.0 ** -53
 
 
-def _noalloc(lib, phase_t, L, L0, e_t, out_t, transpose, Y, stream):
+def _noalloc(lib, phase_t, nphase, L, L0, e_t, out_t, transpose, Y, stream):
     d = e_t.shape[0]
     N = (ctypes.c_int * d)(*phase_t.shape)
-    Lh = np.ascontiguousarray(L, dtype=np.float64)
+    Lh = np.ascontiguousarray(L[:nphase], dtype=np.float64)
     L0h = np.ascontiguousarray(L0, dtype=np.float64)
     Yh = None if Y is None else np.ascontiguousarray(Y, dtype=np.float64)
     buf = ctypes.create_string_buffer(256)
     pD = ctypes.POINTER(ctypes.c_double)
     rc = lib.fh_apply_noalloc(d, N, None if Yh is None else Yh.ctypes.data_as(pD),
-                              ctypes.c_void_p(phase_t.data_ptr()), Lh.shape[0], Lh.ctypes.data_as(pD),
+                              ctypes.c_void_p(phase_t.data_ptr()), nphase, Lh.ctypes.data_as(pD),
                               L0h.ctypes.data_as(pD), ctypes.c_void_p(e_t.data_ptr()),
                               ctypes.c_void_p(out_t.data_ptr()), int(transpose), ctypes.c_void_p(stream),
                               buf, 256)
     return rc, buf.value.decode()
 
 
-def test_noalloc_matches_fh_apply_on_two_calls_in_a_row():
+def test_noalloc_matches_oracle_on_calls_in_a_row():
     torch = cuda_or_skip()
     from paper_1004_1122_gb300 import fh
 
     lib = fh.load_library()
     stream = torch.cuda.current_stream().cuda_stream
-    cases = [((81, 45), (1.0, 2.0), False, 11), ((15, 21, 9), None, True, 12)]
-    for N, Y, transpose, seed in cases:
+    cases = [((81, 45), (1.0, 2.0), 11), ((15, 21, 9), None, 12)]
+    calls = 0
+    for N, Y, seed in cases:
         rng = np.random.default_rng(seed)
         d = len(N)
-        phase = rng.integers(0, 3, size=N).astype(np.uint8)
-        L = np.stack([spd(rng, d) for _ in range(3)])
+        nphase = 3
+        # ids 3 and 4 have no tensor in the call: they must act as L = L0
+        phase = rng.integers(0, nphase + 2, size=N).astype(np.uint8)
         L0 = spd(rng, d, 1.0, 3.0)
+        L = np.stack([spd(rng, d) for _ in range(nphase)] + [L0, L0])
         e = rng.normal(size=(d,) + N)
-        e_t = torch.from_numpy(e).cuda()
-        with fh.Solver(phase, L, L0=L0, Y=Y, precision="fp64") as s:
-            ref = s.apply(e_t, transpose=transpose).cpu().numpy()
         phase_t = torch.from_numpy(phase).cuda()
-        out_t = torch.empty_like(e_t)
-        rc, msg = _noalloc(lib, phase_t, L, L0, e_t, out_t, transpose, Y, stream)
-        torch.cuda.synchronize()
-        assert rc == 0, msg
-        got = out_t.cpu().numpy()
         tol = 64 * U64 * (1.0 + np.max(np.abs(L - L0[None]))) * np.max(np.abs(e))
-        assert np.max(np.abs(got - ref)) <= tol, (N, np.max(np.abs(got - ref)), tol)
+        for transpose in (False, True):
+            ref = (oracle.apply_AT if transpose else oracle.apply_A)(e, phase, L, L0, Y)
+            for in_place in (False, True):
+                e_t = torch.from_numpy(e).cuda()
+                out_t = e_t if in_place else torch.empty_like(e_t)
+                rc, msg = _noalloc(lib, phase_t, nphase, L, L0, e_t, out_t, transpose, Y, stream)
+                torch.cuda.synchronize()
+                assert rc == 0, msg
+                calls += 1
+                err = np.max(np.abs(out_t.cpu().numpy() - ref))
+                assert err <= tol, (N, transpose, in_place, err, tol)
+    assert calls == 8
 
 
 def test_noalloc_refuses_grids_beyond_its_scratch():
@@ -75,6 +85,6 @@ def test_noalloc_refuses_grids_beyond_its_scratch():
     N = (2187, 729)
     phase_t = torch.zeros(N, dtype=torch.uint8, device="cuda")
     e_t = torch.zeros((2,) + N, dtype=torch.float64, device="cuda")
-    rc, msg = _noalloc(lib, phase_t, np.eye(2)[None], 2.0 * np.eye(2), e_t, e_t, False, None,
+    rc, msg = _noalloc(lib, phase_t, 1, np.eye(2)[None], 2.0 * np.eye(2), e_t, e_t, False, None,
                        torch.cuda.current_stream().cuda_stream)
     assert rc == 9 and "scratch" in msg
