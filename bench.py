@@ -57,7 +57,6 @@ def parse():
     ap.add_argument("--impl", default="fh", choices=["fh", "reference"])
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT float64 CG baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--cpu-iters", type=int, default=6)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--c5-n", type=int, default=135, help="grid of the warm-start workload (a multiple of 27)")
     ap.add_argument("--c5-train", type=int, default=200, help="training cells of the warm-start workload")
@@ -184,99 +183,165 @@ def make_inputs():
 
 
 # --------------------------------------------------------------------------
-# plain float64 CG on cuFFT (torch.fft): the comparison baseline, never the product
+# CG on cuFFT (torch.fft): the comparison baselines, never the product
 # --------------------------------------------------------------------------
-def cufft_fp64_cg(torch, phase_t, L, E, tol, max_iter):
-    """Same operator (e + F^-1 Gamma0 F dL e) and the same CG (Saad Alg. 6.18) from
-    e = E, float64, torch.fft.rfft2 / irfft2.  Stops on the recursive residual,
-    then checks the true one.  Returns (iters, rel_true, L_eff column <L e>)."""
-    dev = phase_t.device
-    lam = [L[p][0, 0] for p in range(L.shape[0])]
-    l0 = 0.5 * (min(lam) + max(lam))
-    dl = torch.tensor([x - l0 for x in lam], dtype=torch.float64, device=dev)[phase_t.long()]
-    n0, n1 = phase_t.shape
-    k0 = torch.fft.fftfreq(n0, d=1.0 / n0, dtype=torch.float64, device=dev)[:, None]
-    k1 = torch.fft.rfftfreq(n1, d=1.0 / n1, dtype=torch.float64, device=dev)[None, :]
-    den = l0 * (k0 * k0 + k1 * k1)
-    den[0, 0] = 1.0
-    g00, g01, g11 = k0 * k0 / den, k0 * k1 / den, k1 * k1 / den
-    g00[0, 0] = g01[0, 0] = g11[0, 0] = 0.0
+class CufftOperator:
+    """The same operator e + F^-1 Gamma0 F (dL e) as the library, on torch.fft
+    (cuFFT) in the given dtype: rfft2 / irfft2 of the isotropic two-phase cell,
+    Gamma0 of Section 2.1 with L0 of Eq. (opt_ref)."""
 
-    def A(e):
-        t0 = torch.fft.rfft2(dl * e[0])
-        t1 = torch.fft.rfft2(dl * e[1])
-        y0 = torch.fft.irfft2(g00 * t0 + g01 * t1, s=(n0, n1))
-        y1 = torch.fft.irfft2(g01 * t0 + g11 * t1, s=(n0, n1))
-        return torch.stack([e[0] + y0, e[1] + y1])
+    def __init__(self, torch, phase_t, L, dtype):
+        dev = phase_t.device
+        self.torch = torch
+        lam = [L[p][0, 0] for p in range(L.shape[0])]
+        l0 = 0.5 * (min(lam) + max(lam))
+        self.dl = torch.tensor([x - l0 for x in lam], dtype=dtype, device=dev)[phase_t.long()]
+        self.lam = torch.tensor(lam, dtype=torch.float64, device=dev)[phase_t.long()]
+        n0, n1 = phase_t.shape
+        self.shape = (n0, n1)
+        k0 = torch.fft.fftfreq(n0, d=1.0 / n0, dtype=torch.float64, device=dev)[:, None]
+        k1 = torch.fft.rfftfreq(n1, d=1.0 / n1, dtype=torch.float64, device=dev)[None, :]
+        den = l0 * (k0 * k0 + k1 * k1)
+        den[0, 0] = 1.0
+        g = [k0 * k0 / den, k0 * k1 / den, k1 * k1 / den]
+        for x in g:
+            x[0, 0] = 0.0
+        self.g00, self.g01, self.g11 = [x.to(dtype) for x in g]
 
-    b = torch.stack([torch.full((n0, n1), E[0], dtype=torch.float64, device=dev),
-                     torch.full((n0, n1), E[1], dtype=torch.float64, device=dev)])
-    x = b.clone()
+    def __call__(self, e):
+        fft = self.torch.fft
+        t0 = fft.rfft2(self.dl * e[0])
+        t1 = fft.rfft2(self.dl * e[1])
+        y0 = fft.irfft2(self.g00 * t0 + self.g01 * t1, s=self.shape)
+        y1 = fft.irfft2(self.g01 * t0 + self.g11 * t1, s=self.shape)
+        return self.torch.stack([e[0] + y0, e[1] + y1])
+
+
+def torch_cg(torch, A, b, x, tol, max_iter, check_every=8):
+    """CG (Saad Alg. 6.18) on A x = b from x, in the dtype of b; the recursive
+    relative residual is read back every `check_every` iterations (the device
+    runs ahead between checks).  Returns (x, iterations)."""
     r = b - A(x)
     p = r.clone()
-    rr = torch.sum(r * r)
-    nb = torch.sqrt(torch.sum(b * b))
+    rr = torch.sum(r * r, dtype=torch.float64)
+    nb = torch.sqrt(torch.sum(b * b, dtype=torch.float64))
     it = 0
     while it < max_iter:
-        if (torch.sqrt(rr) / nb).item() <= tol:
+        if it % check_every == 0 and (torch.sqrt(rr) / nb).item() <= tol:
             break
         Ap = A(p)
-        alpha = rr / torch.sum(p * Ap)
-        x += alpha * p
-        r -= alpha * Ap
-        rr_new = torch.sum(r * r)
-        p = r + (rr_new / rr) * p
+        alpha = rr / torch.sum(p * Ap, dtype=torch.float64)
+        x += alpha.to(x.dtype) * p
+        r -= alpha.to(x.dtype) * Ap
+        rr_new = torch.sum(r * r, dtype=torch.float64)
+        p = r + (rr_new / rr).to(x.dtype) * p
         rr = rr_new
         it += 1
+    return x, it
+
+
+def cufft_fp64_cg(torch, phase_t, L, E, tol, max_iter):
+    """Plain float64 CG on cuFFT from e = E to the recursive residual tol, then
+    the true one.  Returns (iters, rel_true, L_eff column <L e>)."""
+    A = CufftOperator(torch, phase_t, L, torch.float64)
+    n0, n1 = A.shape
+    b = torch.stack([torch.full((n0, n1), E[0], dtype=torch.float64, device=phase_t.device),
+                     torch.full((n0, n1), E[1], dtype=torch.float64, device=phase_t.device)])
+    x, it = torch_cg(torch, A, b, b.clone(), tol, max_iter)
     res = b - A(x)
-    lam_t = torch.tensor(lam, dtype=torch.float64, device=dev)[phase_t.long()]
-    col = [float(torch.mean(lam_t * x[0]).item()), float(torch.mean(lam_t * x[1]).item())]
-    return it, (torch.sqrt(torch.sum(res * res)) / nb).item(), col
+    col = [float(torch.mean(A.lam * x[0]).item()), float(torch.mean(A.lam * x[1]).item())]
+    return it, (torch.sqrt(torch.sum(res * res)) / torch.sqrt(torch.sum(b * b))).item(), col
+
+
+def cufft_fp32_refined_cg(torch, phase_t, L, E, tol, max_iter):
+    """The library's precision scheme on cuFFT: float32 CG iterations with a
+    float64 outer residual r = e0 - A x and x += d (first step from x = E to a
+    relative residual of 1e-3, later inner steps to clamp(0.3 tol / rel, 2e-6,
+    0.1)).  Returns (inner iterations, outer steps, rel_true, L_eff column)."""
+    A64 = CufftOperator(torch, phase_t, L, torch.float64)
+    A32 = CufftOperator(torch, phase_t, L, torch.float32)
+    n0, n1 = A64.shape
+    dev = phase_t.device
+    b = torch.stack([torch.full((n0, n1), E[0], dtype=torch.float64, device=dev),
+                     torch.full((n0, n1), E[1], dtype=torch.float64, device=dev)])
+    nb = torch.sqrt(torch.sum(b * b)).item()
+    b32 = b.float()
+    x32, total = torch_cg(torch, A32, b32, b32.clone(), max(0.3 * tol, 1e-3), max_iter)
+    x = x32.double()
+    outer, prev, rel = 1, float("inf"), float("inf")
+    while True:
+        r = b - A64(x)
+        rel = torch.sqrt(torch.sum(r * r)).item() / nb
+        if rel <= tol or total >= max_iter or not rel < 0.9 * prev:
+            break
+        prev = rel
+        eta = min(0.1, max(2e-6, 0.3 * tol / rel))
+        d, it = torch_cg(torch, A32, r.float(), torch.zeros_like(b32), eta, max_iter - total)
+        total += it
+        x += d.double()
+        outer += 1
+    col = [float(torch.mean(A64.lam * x[0]).item()), float(torch.mean(A64.lam * x[1]).item())]
+    return total, outer, rel, col
+
+
+def cufft_matvec_ms(torch, phase_t, L, dtype, reps=30):
+    """CUDA-event time of one operator application on cuFFT in `dtype`."""
+    A = CufftOperator(torch, phase_t, L, dtype)
+    e = torch.randn((2,) + tuple(phase_t.shape), dtype=dtype, device=phase_t.device)
+    for _ in range(3):
+        A(e)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(reps):
+        A(e)
+    ev[1].record()
+    ev[1].synchronize()
+    return ev[0].elapsed_time(ev[1]) / reps
 
 
 # --------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # --------------------------------------------------------------------------
-def cpu_oracle_sample(phase, tables, iters):
-    """Time `iters` oracle CG iterations at full size (rho = 1e2) on the host."""
-    import numpy as np
-
+def cpu_oracle_solve(phase, tables):
+    """One complete oracle solve of the workload on the host: rho = 1e1,
+    E = (1, 0), CG from e = E to relative residual 1e-6 (the oracle's FFTs on
+    every host core).  Returns (seconds, iterations, fft threads)."""
     import oracle
 
-    L = tables[1]
+    L = tables[0]
     L0 = oracle.reference_medium(L)
     t0 = time.perf_counter()
-    _, info = oracle.cg(phase, L, L0, [1.0, 0.0], tol=1e-30, max_iter=iters)
-    dt = time.perf_counter() - t0
-    # the oracle's cg spends one extra product for the initial and one for the
-    # final true residual: iters + 2 operator applications in total
-    t_iter = dt / (iters + 2)
-    counts = oracle_counts()
-    if counts:
-        total = sum(s["iters"] for s in counts["solves"])
-        src = "oracle CG iteration counts of the 8 solves (tests/golden/c2_cg_iterations.json)"
-    else:
-        total = None
-        src = "no stored oracle iteration counts"
-    del np
-    return t_iter, total, src
+    _, info = oracle.cg(phase, L, L0, [1.0, 0.0], tol=TOL, max_iter=MAX_ITER)
+    return time.perf_counter() - t0, info["iters"], oracle.operator.FFT_WORKERS
 
 
-def cpu_cores_used():
-    return 1  # numpy's pocketfft and the oracle's vector ops run on one thread
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 # --------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # --------------------------------------------------------------------------
 def run_reference(args):
+    """The reference arm of this repository: the CPU oracle on the host cores.
+    Each step times two oracle CG iterations (plus the initial and final
+    operator products) of the workload's rho = 1e1 solve; the value per solve
+    is that time per product times the oracle's mean products per solve over
+    the workload's 8 solves (tests/golden/c2_cg_iterations.json)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     phase, tables = make_inputs()
     import oracle
 
-    L = tables[1]
+    L = tables[0]
     L0 = oracle.reference_medium(L)
     per_step = 2
     times = []
@@ -286,19 +351,20 @@ def run_reference(args):
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt / (per_step + 2))
-    t_iter = statistics.mean(times)
+    t_prod = statistics.mean(times)
     counts = oracle_counts()
-    total = sum(s["iters"] for s in counts["solves"]) if counts else 2000
-    ms_per_solve = t_iter * total / (len(RHOS) * len(LOADS)) * 1e3
-    sample = (f"{per_step} oracle CG iterations per step (+2 operator products) at {N}^2, rho=1e2; "
-              f"scaled by {total} oracle CG iterations over the 8 solves")
+    total = sum(s["iters"] + 2 for s in counts["solves"]) if counts else 2000
+    ms_per_solve = t_prod * total / (len(RHOS) * len(LOADS)) * 1e3
+    workers = oracle.operator.FFT_WORKERS
+    sample = (f"{per_step} oracle CG iterations per step (+2 operator products) at {N}^2, rho=1e1, on "
+              f"{workers} FFT threads; scaled by the {total} operator products of the oracle's 8 solves")
     line = {
         "impl": "reference", "metric": METRIC, "value": ms_per_solve, "unit": "ms/solve",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_iter * per_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "ms_per_step": t_prod * (per_step + 2) * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "working set > L2"},
-        "cpu_baseline": {"value": ms_per_solve, "unit": "ms/solve", "cores": cpu_cores_used(),
+        "cpu_baseline": {"value": ms_per_solve, "unit": "ms/solve", "cores": workers,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": ms_per_solve, "unit": "ms/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -330,10 +396,15 @@ def csrc_digest() -> str:
     return h.hexdigest()[:16]
 
 
+TRAFFIC_SUMMARY = os.path.join("profiles", "traffic_c2_2187_fp32.md")
+
+
 def recorded_traffic(kernel: str):
-    """DRAM bytes per launch (read + write) of `kernel` from the committed ncu
-    summary, or None when the summary was taken on other kernel sources."""
-    path = os.path.join(ROOT, "profiles", "traffic_c2_2187_fp32.md")
+    """DRAM bytes per launch (read + write) of `kernel` as recorded by an ncu
+    capture (a cold-L2 launch of `bench.py --probe`) in the committed summary,
+    or None when the summary was taken on other kernel sources.  This is a
+    recorded figure, not a measurement of this run."""
+    path = os.path.join(ROOT, TRAFFIC_SUMMARY)
     if not os.path.exists(path):
         return None
     digest = csrc_digest()
@@ -469,13 +540,23 @@ def run_fh(args):
     b_apply = (d * s4 + 1) * nodes + spec + 2 * spec + spec + 2 * d * s4 * nodes
     traffic = recorded_traffic(dom)
 
-    # ---- plain float64 CG on cuFFT (baseline, measured once) ---------------
-    base = None
+    # ---- CG on cuFFT (baselines, measured once) ----------------------------
+    base = base32 = None
     if not args.no_baseline and rank == 0:
         ph_t = torch.from_numpy(phase).cuda()
+
+        def leff_diffs(cols):
+            # effective tensors of both solvers (each to true rel.res <= 1e-6), contrast by contrast
+            out = []
+            for i in range(len(tables)):
+                ref = np.array([cols[2 * i + j] for j in range(len(LOADS))]).T
+                out.append(float(np.max(np.abs(leff[i] - ref)) / np.max(np.abs(ref))))
+            return out
+
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # plain float64 CG (the comparison baseline of the metric)
         tb0 = time.perf_counter()
         its, rels, cols = [], [], []
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         b0.record()
         for L in tables:
@@ -487,26 +568,39 @@ def run_fh(args):
         b1.record()
         b1.synchronize()
         base_ms = b0.elapsed_time(b1) / nsolve
-        # effective tensors of both solvers (each to true rel.res <= 1e-6), contrast by contrast
-        diffs = []
-        for i in range(len(tables)):
-            ref = np.array([cols[2 * i + j] for j in range(len(LOADS))]).T
-            diffs.append(float(np.max(np.abs(leff[i] - ref)) / np.max(np.abs(ref))))
         base = {"ms_per_solve": base_ms, "iters": its, "rel_res_true_max": max(rels),
                 "speedup_of_value": base_ms / value, "wall_s": time.perf_counter() - tb0,
-                "Leff_rel_diff_vs_ours": diffs}
+                "matvec_ms": cufft_matvec_ms(torch, ph_t, tables[1], torch.float64),
+                "Leff_rel_diff_vs_ours": leff_diffs(cols)}
+        # the same precision scheme as ours (float32 CG + float64 refinement) on cuFFT
+        its, outs, rels, cols = [], [], [], []
+        torch.cuda.synchronize()
+        b0.record()
+        for L in tables:
+            for E in LOADS:
+                it, o, rel, col = cufft_fp32_refined_cg(torch, ph_t, L, E, TOL, MAX_ITER)
+                its.append(it)
+                outs.append(o)
+                rels.append(rel)
+                cols.append(col)
+        b1.record()
+        b1.synchronize()
+        ms32 = b0.elapsed_time(b1) / nsolve
+        mv32 = cufft_matvec_ms(torch, ph_t, tables[1], torch.float32)
+        base32 = {"ms_per_solve": ms32, "inner_iters": its, "outer_iters": outs, "rel_res_true_max": max(rels),
+                  "speedup_of_value": ms32 / value, "matvec_ms": mv32,
+                  "matvec_speedup_of_ours": mv32 / t_apply,
+                  "Leff_rel_diff_vs_ours": leff_diffs(cols)}
 
-    # ---- CPU oracle baseline ----------------------------------------------
+    # ---- CPU oracle: one complete solve on the host cores -----------------
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        t_iter, total, src = cpu_oracle_sample(phase, tables, args.cpu_iters)
-        if total is None:
-            total = sum(iters)
-            src = "no stored oracle counts; scaled by this run's inner iteration counts"
-        cpu = {"value": t_iter * total / nsolve * 1e3, "unit": "ms/solve", "cores": cpu_cores_used(),
-               "kind": "oracle",
-               "sample": f"{args.cpu_iters} numpy-oracle CG iterations at {N}^2 rho=1e2 "
-                         f"({t_iter:.2f} s/iteration), scaled by {total} iterations: {src}"}
+        t_s, cpu_iters, workers = cpu_oracle_solve(phase, tables)
+        cpu = {"value": t_s * 1e3, "unit": "ms/solve", "cores": workers, "kind": "oracle",
+               "sample": f"one complete oracle solve of the workload (rho=1e1, E=(1,0), CG from e=E to "
+                         f"rel.res {TOL:g}: {cpu_iters} iterations, {cpu_iters + 2} operator products) "
+                         f"at {N}^2; the oracle's FFTs on {workers} host threads, its pointwise numpy "
+                         f"work on one; host {cpu_model()}"}
 
     if rank == 0:
         line = {
@@ -530,6 +624,9 @@ def run_fh(args):
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                         "traffic_source": (f"recorded, not measured by this run: ncu dram__bytes_read.sum + "
+                                            f"dram__bytes_write.sum of a cold-L2 launch ({TRAFFIC_SUMMARY}, "
+                                            f"kernel sources {csrc_digest()})") if traffic else None,
                          "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": kern[dom][1],
                          "ms_per_launch": times[dom]},
@@ -543,6 +640,7 @@ def run_fh(args):
             "solver": {"inner_iters": iters, "outer_iters": outer, "rel_res_true_max": rel_true,
                        "L_eff": [m.tolist() for m in leff], "rhos": RHOS},
             "fp64_cufft_cg": base,
+            "fp32_cufft": base32,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -554,7 +652,10 @@ def run_fh(args):
 
 def run_probe():
     """A few launches of every pass kernel of the float32 CG iteration on the
-    full-size workload (rho = 1e2), for profiler captures."""
+    full-size workload (rho = 1e2), for profiler captures.  Before each kernel's
+    launches a 512 MiB buffer is written, which evicts L2 (126 MB): the first
+    launch of each kernel reads its whole working set from DRAM, as a launch
+    inside a solve does, where the other passes stream ~0.5 GB in between."""
     import torch
 
     import __graft_entry__
@@ -563,9 +664,13 @@ def run_probe():
     from paper_1004_1122_gb300 import fh
 
     phase, tables = make_inputs()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
     with fh.Solver(phase, tables[1], precision="fp32") as s:
-        out = {name: s.profile(w, reps=3) for name, w in
-               (("row_fwd", 0), ("col_green", 1), ("row_inv", 2), ("cg_update", 3), ("apply", 5))}
+        for name, w in (("row_fwd", 0), ("col_green", 1), ("row_inv", 2), ("cg_update", 3), ("apply", 5)):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            out[name] = s.profile(w, reps=3)
     torch.cuda.synchronize()
     print(json.dumps({"probe_ms": out}))
 

@@ -10,7 +10,7 @@ arithmetic.
 Everything here is plain, slow and in float64:
 
 ``operator``   the collocation operator ``A = I + B`` of Eq. (linear_system)
-               and Eq. (mtrx_B), with ``numpy.fft`` as the DFT step.
+               and Eq. (mtrx_B), with a library FFT (scipy.fft) as the DFT step.
 ``dense``      Tier 1, tiny grids only: the DFT matrices of Eq. (DFT_def)
                written out, ``I + B`` assembled densely and solved by LU; and
                an independent potential (equilibrium) formulation of the same

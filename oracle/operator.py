@@ -1,4 +1,4 @@
-"""The collocation operator A = I + B, matrix-free, float64, numpy.fft as DFT.
+"""The collocation operator A = I + B, matrix-free, float64, a library FFT as DFT.
 
 Test infrastructure only (see the package docstring).
 
@@ -8,7 +8,8 @@ Notation (Section 2): a field ``e`` has shape ``(d, N_0, ..., N_{d-1})``
 reference conductivity ``(d, d)``; ``Y`` holds the half side lengths of the
 cell ``Y = prod (-Y_a, Y_a)`` (Section 2.1).
 
-The operator follows Eq. (mtrx_B) factor by factor, right to left:
+The operator follows Eq. (mtrx_B) factor by factor, right to left (the DFT
+step is a library FFT, scipy.fft on every host core):
 
     B e = F^-1 [ Gamma0(k) . F( dL . e ) ]
 
@@ -31,7 +32,25 @@ and the adjoint identity <A u, v> = <u, A^T v>.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
+from scipy import fft as _fft
+
+# The DFT step runs on every host core (scipy.fft's pocketfft with worker
+# threads computes the same unnormalised forward / 1/|N| inverse DFT as
+# numpy.fft); ORACLE_FFT_WORKERS caps the thread count.
+FFT_WORKERS = int(os.environ.get("ORACLE_FFT_WORKERS", str(os.cpu_count() or 1)))
+
+
+def fftn(x, axes):
+    """Forward DFT of Eq. (DFT_def) over ``axes`` (unnormalised)."""
+    return _fft.fftn(x, axes=axes, workers=FFT_WORKERS)
+
+
+def ifftn(x, axes):
+    """Inverse DFT of Eq. (DFT_def) over ``axes`` (with the 1/|N| factor)."""
+    return _fft.ifftn(x, axes=axes, workers=FFT_WORKERS)
 
 
 def signed_frequencies(n: int) -> np.ndarray:
@@ -91,10 +110,10 @@ def _spatial_axes(e: np.ndarray) -> tuple[int, ...]:
 def green_apply(t: np.ndarray, N, Y, L0) -> np.ndarray:
     """F^-1 Gamma0 F t: the three leftmost factors of Eq. (mtrx_B)."""
     axes = _spatial_axes(t)
-    th = np.fft.fftn(t, axes=axes)
+    th = fftn(t, axes=axes)
     G = gamma_hat(N, Y, L0)
     yh = np.einsum("ab...,b...->a...", G, th)
-    return np.real(np.fft.ifftn(yh, axes=axes))
+    return np.real(ifftn(yh, axes=axes))
 
 
 def apply_B(e, phase, L, L0, Y=None) -> np.ndarray:

@@ -36,7 +36,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .operator import apply_A, apply_AT, macroscopic_field, signed_frequencies
+from .operator import apply_A, apply_AT, fftn, macroscopic_field, signed_frequencies
 
 
 def _dot(a: np.ndarray, b: np.ndarray) -> float:
@@ -224,7 +224,7 @@ def eta_e(e, phase, L, Y=None) -> float:
     e = np.asarray(e, dtype=np.float64)
     N = e.shape[1:]
     Y = np.ones(len(N)) if Y is None else np.asarray(Y, dtype=np.float64)
-    jh = np.fft.fftn(current(e, phase, L), axes=tuple(range(1, e.ndim)))
+    jh = fftn(current(e, phase, L), axes=tuple(range(1, e.ndim)))
     ks = np.meshgrid(*[signed_frequencies(n) / Y[a] for a, n in enumerate(N)], indexing="ij")
     div = sum(ks[a] * jh[a] for a in range(len(N)))
     j0 = jh[(slice(None),) + (0,) * len(N)]
