@@ -63,8 +63,10 @@ def parse():
     ap.add_argument("--c5-eval", type=int, default=32, help="held-out cells of the warm-start workload")
     ap.add_argument("--c5-epochs", type=int, default=20, help="training epochs of the warm-start workload")
     ap.add_argument("--c5-lr", type=float, default=1e-3, help="peak Adam learning rate of the warm-start workload")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
-                    help="c2: 2187^2 contrast sweep (default); c3: 243^3 full tensor; c4: 512-cell sweep")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "x1"],
+                    help="c2: 2187^2 contrast sweep (default); c3: 243^3 full tensor; c4: 512-cell sweep; "
+                         "c5: learned warm start; x1: the paper's 255^2 model problem (omega and contrast "
+                         "sweeps of CG, BiCG and FFTH, eta_r / eta_e, cost per iteration)")
     ap.add_argument("--probe-nn", action="store_true",
                     help="a few forward passes and one training step of the warm-start network at 81^3 "
                          "(for profiler captures)")
@@ -822,6 +824,120 @@ def run_c3(args):
     print(json.dumps(line), flush=True)
 
 
+X1_RHOS = [1e1, 1e2, 1e3, 1e4]
+X1_OMEGAS = [0.1, 0.25, 0.5, 0.75, 1.0, 2.0]
+X1_EPS = 1e-4
+
+
+def run_x1(args):
+    """Section 3's model problem: a square array of disks at volume fraction 0.5
+    (one centred disk per 255^2 cell, 255 = 3 * 5 * 17: the radix-17 plans),
+    matrix L = I, particle L = rho I, E = (1, 0), reference medium
+    L0(omega) = (1 - omega + rho omega) I (Eq. ref_media_choice), float64.
+    For every (rho, omega) CG, BiCG and the fixed-point scheme (FFTH) run with
+    their per-iteration norm histories; the iteration count is the first step
+    m with eta_r (Eq. errR_def) <= 1e-4, plus one, and eta_r / eta_e is taken
+    at that iterate (Figs. example1a/b, example2).  FFTH runs where its series
+    converges (l0 > rho / 2) and is capped elsewhere.  Then the cost per
+    iteration of the three methods (Fig. example1c) on 255^2 (float64) and on
+    the 2187^2 benchmark cell (float32, rho = 1e2)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1004_1122_gb300 import fh
+    from paper_1004_1122_gb300 import microstructure as micro
+
+    n = 255
+    phase = micro.centred_disk(n, 0.5)
+    E = [1.0, 0.0]
+    rows = []
+    clocks = Clocks(dist_env()[2])
+    clocks.start()
+    t_all = time.perf_counter()
+    for rho in X1_RHOS:
+        L = micro.isotropic_table([1.0, rho], 2)
+        for om in X1_OMEGAS:
+            l0 = 1.0 - om + rho * om
+            L0 = l0 * np.eye(2)
+            row = {"rho": rho, "omega": om, "l0": l0}
+            with fh.Solver(phase, L, L0=L0, precision="fp64") as s:
+                for method in ("cg", "bicg", "fixed_point"):
+                    ffth_converges = l0 > rho / 2.0
+                    if method == "fixed_point":
+                        tol = X1_EPS / l0  # FFTH: eta_r = l0 * rel.res exactly
+                        # rate 1 - 1/l0 at best: ~l0 ln(l0 / eps) steps from eta_r ~ l0
+                        cap = int(min(4e5, 3.0 * l0 * np.log(max(l0, 2.0) / X1_EPS) + 1000)) \
+                            if ffth_converges else 2000
+                    else:
+                        # eta_r measures the step, which may exceed the residual by the
+                        # condition number (~rho): run the residual well past the target
+                        # and read the count from the history
+                        tol = max(X1_EPS / (l0 * rho * 5.0), 1e-14)
+                        cap = 20000
+                    _, _, info = s.solve(E, tol=tol, method=method, max_iter=cap, history=cap + 2, norms=True)
+                    er, ee = info["eta_r_history"], info["eta_e_history"]
+                    hit = np.nonzero(er <= X1_EPS)[0]
+                    if hit.size and np.all(np.isfinite(er[: hit[0] + 1])):
+                        m = int(hit[0])
+                        row[method] = {"iters": m + 1, "eta_r": float(er[m]), "eta_e": float(ee[m + 1]),
+                                       "eta_r_over_eta_e": float(er[m] / ee[m + 1]) if ee[m + 1] > 0 else None,
+                                       "status": info["status"]}
+                    else:
+                        row[method] = {"iters": None, "status": info["status"], "iters_run": info["iters"],
+                                       "note": "eta_r <= 1e-4 not reached" +
+                                               ("" if ffth_converges or method != "fixed_point"
+                                                else " (the Neumann series diverges for l0 <= rho/2)")}
+            f = row["fixed_point"]["iters"]
+            for m in ("cg", "bicg"):
+                row[m]["rel_to_ffth"] = (row[m]["iters"] / f) if (f and row[m]["iters"]) else None
+            rows.append(row)
+    sweep_s = time.perf_counter() - t_all
+
+    # cost per iteration (no norm histories): 255^2 float64 and 2187^2 float32
+    def per_iter(solver, method, tol, cap):
+        solver.solve(E, tol=tol, method=method, max_iter=cap, want_field=False)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(solver.stream)
+        _, _, info = solver.solve(E, tol=tol, method=method, max_iter=cap, want_field=False)
+        ev[1].record(solver.stream)
+        ev[1].synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        return {"ms": ms, "iters": info["iters"], "ms_per_iter": ms / max(info["iters"], 1)}
+
+    cost = {}
+    L = micro.isotropic_table([1.0, 1e2], 2)
+    with fh.Solver(phase, L, precision="fp64") as s:
+        cost["255_fp64_rho1e2"] = {m: per_iter(s, m, 1e-8, 100000) for m in ("cg", "bicg", "fixed_point")}
+    ph_big, tables = make_inputs()
+    with fh.Solver(ph_big, tables[1], precision="fp32") as s:
+        cost["2187_fp32_rho1e2"] = {m: per_iter(s, m, 1e-4, 100000) for m in ("cg", "bicg", "fixed_point")}
+    for k, c in cost.items():
+        f = c["fixed_point"]["ms_per_iter"]
+        for m in ("cg", "bicg"):
+            c[m]["per_iter_over_ffth"] = c[m]["ms_per_iter"] / f
+    clk = clocks.stop()
+    head = next(r for r in rows if r["rho"] == 1e4 and r["omega"] == 0.5)
+    line = {
+        "metric": "Section 3 model problem: CG iterations relative to FFTH at eta_r <= 1e-4 (rho = 1e4, omega = 0.5)",
+        "value": head["cg"]["rel_to_ffth"], "unit": "fraction", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": 1e3 * sweep_s, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (cost per iteration also f32 at 2187^2)", "data": "synthetic",
+        "config": {"workload": f"2-D N={n}^2 centred disk vf 0.5 (square array), L = 1 / rho, E = (1,0), "
+                               f"L0 = (1 - omega + rho omega) I, rho in {X1_RHOS}, omega in {X1_OMEGAS}, "
+                               f"stop at eta_r <= {X1_EPS:g}"},
+        "clocks": clk,
+        "sweep": rows,
+        "cost_per_iteration": cost,
+        "paper": {"cg_rel_iters": "50 % (mild contrast) to 2 % (rho = 1e4)", "cg_per_iter_over_ffth": 1.1,
+                  "bicg_per_iter_over_ffth": 2.0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def make_c5_cell(n, seed):
     """3-D two-phase cell: overlapping balls (odd seeds) or randomly oriented
     ellipsoids (aspect <= 3, even seeds) of size n/27..n/13 to digital volume
@@ -996,6 +1112,9 @@ def main():
         return
     if args.workload == "c5" and args.impl != "reference":
         run_c5(args)
+        return
+    if args.workload == "x1" and args.impl != "reference":
+        run_x1(args)
         return
     if args.probe:
         run_probe()

@@ -94,6 +94,16 @@ typedef struct {
   int ct_plans;           /* out: FH_CT_* bits of the compile-time FFT plans whose kernels
                              ran every pass of the float32 CG iterations of this call
                              (0: run-time-plan kernels, or no float32 CG iteration) */
+  /* Per-iteration norms of Section 3, FH_FP64 and FH_FP32 contexts (fh_solve
+   * only; ignored for FH_FP32_REFINED, whose inner iterates are corrections):
+   * host buffers of history_cap doubles, or NULL.  eta_e_history[m] is
+   * Eq. (errE_def) of the iterate after m iterations (one more operator-pass
+   * set per iteration); eta_r_history[m] is Eq. (errR_def) as printed,
+   * ||L0 (e_{m+1} - e_m)|| / ||e0||, for an isotropic L0 (NaN otherwise). */
+  double* eta_e_history;
+  double* eta_r_history;
+  int eta_e_len;          /* out: entries of eta_e_history written */
+  int eta_r_len;          /* out: entries of eta_r_history written */
 } fh_info;
 
 /* fh_info.flags bits */
@@ -112,7 +122,9 @@ typedef struct {
  *  out        host; receives the context (NULL on failure).
  *  d          2 or 3.
  *  N          host, d ints, each odd and >= 3; supported lengths are those
- *             that factor into 3, 5 and 7.
+ *             that factor into 3, 5, 7, 11, 13 and 17 (a length with a
+ *             factor 11, 13 or 17, such as the 255 = 3 * 5 * 17 grid of
+ *             Section 3, runs the extended-radix kernels one load per launch).
  *  Y          host, d half side lengths (> 0), or NULL for all ones.
  *  phase      |N| bytes in C order, phase id per node (< nphase); a host
  *             pointer if phase_on_device == 0, else a device pointer.
@@ -168,7 +180,9 @@ fh_status fh_solve(fh_ctx* ctx, const double* E, double tol, int method, int max
  * ... e_d are solved together, each kernel launch carrying all d loads (for
  * FH_FP64 and FH_FP32_REFINED contexts; an FH_FP32 context solves them one by
  * one).  The first call allocates a second set of buffers sized for d loads,
- * kept until fh_destroy.  Leff receives L_eff row-major (column b from load b).
+ * kept until fh_destroy; grids with an axis that has a factor 11, 13 or 17
+ * solve the loads one by one.  Leff receives L_eff row-major (column b from
+ * load b).
  * infos: host array of d fh_info (iters, outer_iters, status, rel_res_true,
  * launches are filled), or NULL.  Returns the first non-OK status (the
  * statuses of fh_solve, FH_ERR_TIMEOUT included). */
@@ -233,7 +247,8 @@ fh_status fh_autotune_loads(fh_ctx* ctx, double* ms_before, double* ms_after);
  * CUDA-graph chunks.
  *  out        host; receives the batch.
  *  ncells     >= 1.
- *  N          host, 2*ncells ints (N_0, N_1 of each cell; odd, >= 3, factors 3/5/7).
+ *  N          host, 2*ncells ints (N_0, N_1 of each cell; odd, >= 3, factors
+ *             3/5/7, or also 11/13/17 when nloads == 1).
  *  phase      host array of ncells host pointers, cell c has N_0*N_1 bytes.
  *  nphase     host, ncells ints in 1..256.
  *  L          host array of ncells host pointers, cell c has nphase[c]*4
@@ -293,7 +308,7 @@ void fh_batch_destroy(fh_batch* b);
  * 16.1 MiB that every GPU loading the library keeps until the process exits.
  *
  *  d, N, Y     as fh_create (d = 2 or 3, odd N, each axis <= 2187 and built
- *              from 3, 5 and 7; Y may be NULL).  Grids whose float64 half
+ *              from 3, 5, 7, 11, 13 and 17; Y may be NULL).  Grids whose float64 half
  *              spectrum exceeds 16 MiB (for example 2-D above ~1000^2, 3-D
  *              above ~85^3) are rejected with FH_ERR_UNSUPPORTED.
  *  phase       device, |N| bytes; ids >= nphase act as L = L0 (dL = 0).

@@ -20,7 +20,7 @@ Readings of points the paper leaves open:
   is the printed Eq. (errR_def) divided by the reference conductivity.
 * ``eta_r`` in the returned info is Eq. (errR_def) as printed:
   ||L0 (e^(m+1) - e^(m))||_2 / ||e^0||_2, where for CG/BiCG the increment
-  e^(m+1) - e^(m) is alpha p.
+  e^(m+1) - e^(m) is alpha p; ``eta_r_history[m]`` holds it for every step m.
 * The initial guess is e = E (x0 = e^0) unless one is passed.
 * BiCG's shadow residual is r0* = r0.
 * Breakdown ((A p, p) <= 0 for CG, a zero denominator for BiCG, or a
@@ -53,13 +53,14 @@ def _setup(phase, L, L0, E, Y):
     return phase, N, L, L0, Y, b
 
 
-def _info(status, iters, hist, res_true, eta_r, matvecs):
+def _info(status, iters, hist, res_true, eta_r, matvecs, eta_hist):
     return {
         "status": status,
         "iters": iters,
         "history": np.asarray(hist),
         "rel_res_true": res_true,
         "eta_r": eta_r,
+        "eta_r_history": np.asarray(eta_hist),
         "matvecs": matvecs,
     }
 
@@ -80,6 +81,7 @@ def cg(phase, L, L0, E, tol=1e-8, max_iter=10000, Y=None, x0=None):
     p = r.copy()
     rr = _dot(r, r)
     hist = [np.sqrt(rr) / nb]
+    eta_hist = []
     status, it, eta_r, mv = "not_converged", 0, np.nan, 1
     if hist[-1] <= tol:
         status = "converged"
@@ -95,6 +97,7 @@ def cg(phase, L, L0, E, tol=1e-8, max_iter=10000, Y=None, x0=None):
             x += alpha * p
             r -= alpha * Ap
             eta_r = np.linalg.norm(np.einsum("ab,b...->a...", L0, alpha * p)) / nb
+            eta_hist.append(eta_r)
             rr_new = _dot(r, r)
             hist.append(np.sqrt(rr_new) / nb)
             if not np.isfinite(rr_new):
@@ -107,7 +110,7 @@ def cg(phase, L, L0, E, tol=1e-8, max_iter=10000, Y=None, x0=None):
             rr = rr_new
             p = r + beta * p
     res = b - apply_A(x, phase, L, L0, Y)
-    return x, _info(status, len(hist) - 1, hist, np.sqrt(_dot(res, res)) / nb, eta_r, mv + 1)
+    return x, _info(status, len(hist) - 1, hist, np.sqrt(_dot(res, res)) / nb, eta_r, mv + 1, eta_hist)
 
 
 def bicg(phase, L, L0, E, tol=1e-8, max_iter=10000, Y=None, x0=None, record=None):
@@ -130,6 +133,7 @@ def bicg(phase, L, L0, E, tol=1e-8, max_iter=10000, Y=None, x0=None, record=None
     hist = [np.sqrt(_dot(r, r)) / nb]
     if record is not None:
         record.append((r.copy(), rs.copy()))
+    eta_hist = []
     status, it, eta_r, mv = "not_converged", 0, np.nan, 1
     if hist[-1] <= tol:
         status = "converged"
@@ -149,6 +153,7 @@ def bicg(phase, L, L0, E, tol=1e-8, max_iter=10000, Y=None, x0=None, record=None
             if record is not None:
                 record.append((r.copy(), rs.copy()))
             eta_r = np.linalg.norm(np.einsum("ab,b...->a...", L0, alpha * p)) / nb
+            eta_hist.append(eta_r)
             hist.append(np.sqrt(_dot(r, r)) / nb)
             if hist[-1] <= tol:
                 status = "converged"
@@ -162,7 +167,7 @@ def bicg(phase, L, L0, E, tol=1e-8, max_iter=10000, Y=None, x0=None, record=None
             p = r + beta * p
             ps = rs + beta * ps
     res = b - apply_A(x, phase, L, L0, Y)
-    return x, _info(status, len(hist) - 1, hist, np.sqrt(_dot(res, res)) / nb, eta_r, mv + 1)
+    return x, _info(status, len(hist) - 1, hist, np.sqrt(_dot(res, res)) / nb, eta_r, mv + 1, eta_hist)
 
 
 def fixed_point(phase, L, L0, E, tol=1e-8, max_iter=100000, Y=None, x0=None):
@@ -176,12 +181,14 @@ def fixed_point(phase, L, L0, E, tol=1e-8, max_iter=100000, Y=None, x0=None):
     e = b.copy() if x0 is None else np.asarray(x0, dtype=np.float64).copy()
     nb = np.sqrt(_dot(b, b))
     hist = []
+    eta_hist = []
     status, it, eta_r = "not_converged", 0, np.nan
     for it in range(0, max_iter + 1):
         r = b - apply_A(e, phase, L, L0, Y)
         rel = np.sqrt(_dot(r, r)) / nb
         hist.append(rel)
         eta_r = np.linalg.norm(np.einsum("ab,b...->a...", L0, r)) / nb
+        eta_hist.append(eta_r)
         if not np.isfinite(rel):
             status = "breakdown"
             break
@@ -190,7 +197,7 @@ def fixed_point(phase, L, L0, E, tol=1e-8, max_iter=100000, Y=None, x0=None):
             status = "converged"
             break
     res = b - apply_A(e, phase, L, L0, Y)
-    return e, _info(status, it, hist, np.sqrt(_dot(res, res)) / nb, eta_r, it + 2)
+    return e, _info(status, it, hist, np.sqrt(_dot(res, res)) / nb, eta_r, it + 2, eta_hist)
 
 
 def solve(phase, L, L0, E, method="cg", tol=1e-8, max_iter=10000, Y=None, x0=None):

@@ -432,33 +432,64 @@ namespace {
 
 template <typename T>
 fh_status finish_info(fh_ctx* c, Pipeline<T>* P, fh_info* info, int hist_len) {
-  if (info && info->history && info->history_cap > 0 && P->hist && hist_len > 0) {
-    const int n = hist_len < info->history_cap ? hist_len : info->history_cap;
-    cudaError_t e = cudaMemcpyAsync(info->history, P->hist, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (!info || info->history_cap <= 0 || hist_len <= 0) return FH_OK;
+  const int n = hist_len < info->history_cap ? hist_len : info->history_cap;
+  auto copy = [&](double* dst, const double* src, int len, int* out_len) -> fh_status {
+    if (!dst || !src || len <= 0) return FH_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, len * sizeof(double), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "history copy");
-    info->history_len = n;
-  }
-  return FH_OK;
+    *out_len = len;
+    return FH_OK;
+  };
+  fh_status s = copy(info->history, P->hist, n, &info->history_len);
+  if (s == FH_OK) s = copy(info->eta_e_history, P->hist_eta_e, n, &info->eta_e_len);
+  if (s == FH_OK) s = copy(info->eta_r_history, P->hist_eta_r, n - 1, &info->eta_r_len);
+  P->hist_eta_e = nullptr;  // the next solve asks again
+  P->hist_eta_r = nullptr;
+  return s;
 }
 
+// Device history buffers of the pipeline sized for info->history_cap: the
+// residual history, and (norms = true) the eta_e / eta_r histories the
+// caller asked for.
 template <typename T>
-int ensure_hist(Pipeline<T>* P, fh_info* info, std::string& err) {
-  if (!info || !info->history || info->history_cap <= 0) {
+int ensure_hist(Pipeline<T>* P, fh_info* info, std::string& err, bool norms = false) {
+  P->hist_eta_e = nullptr;
+  P->hist_eta_r = nullptr;
+  const int cap = info ? info->history_cap : 0;
+  const bool want_h = info && info->history && cap > 0;
+  const bool want_e = norms && info && info->eta_e_history && cap > 0;
+  const bool want_r = norms && info && info->eta_r_history && cap > 0;
+  if (!want_h && !want_e && !want_r) {
     P->hist = nullptr;
     P->hist_cap = 0;
     return 0;
   }
-  if (P->hist_cap < info->history_cap || P->hist == nullptr) {
+  auto get = [&](double** dst) -> int {
     double* h = nullptr;
-    if (cudaMalloc(&h, info->history_cap * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&h, cap * sizeof(double)) != cudaSuccess) {
       err = "history allocation";
       return FH_ERR_OOM;
     }
     P->allocs.push_back(h);
-    P->hist = h;
+    *dst = h;
+    return 0;
+  };
+  if (P->hist_cap < cap || P->hist == nullptr) {
+    if (int rc = get(&P->hist)) return rc;
+    P->hist_cap = cap;
+    P->eta_bufs[0] = P->eta_bufs[1] = nullptr;  // sized for the old capacity
   }
-  P->hist_cap = info->history_cap;
+  P->hist_cap = cap;
+  if (want_e) {
+    if (!P->eta_bufs[0] && get(&P->eta_bufs[0])) return FH_ERR_OOM;
+    P->hist_eta_e = P->eta_bufs[0];
+  }
+  if (want_r) {
+    if (!P->eta_bufs[1] && get(&P->eta_bufs[1])) return FH_ERR_OOM;
+    P->hist_eta_r = P->eta_bufs[1];
+  }
   return 0;
 }
 
@@ -473,7 +504,7 @@ fh_status solve_direct(fh_ctx* c, Pipeline<T>* P, const double* E, double tol, i
   const long long len = (long long)c->pb.d * c->pb.nodes;
   double Ev[fh::kMaxLoads][fh::kMaxD] = {};
   for (int a = 0; a < c->pb.d; ++a) Ev[0][a] = E[a];
-  int rc = ensure_hist(P, info, err);
+  int rc = ensure_hist(P, info, err, true);
   if (rc) return from_rc(c, rc, err);
   int x0 = fh::kX0Const;
   if (e_init) {
@@ -551,6 +582,7 @@ fh_status fh_solve(fh_ctx* c, const double* E, double tol, int method, int max_i
     info->history_len = 0;
     info->launches = 0;
     info->ct_plans = 0;
+    info->eta_e_len = info->eta_r_len = 0;
     info->rel_res_true = info->rel_res = info->eta_r = info->eta_e = NAN;
   }
   const long long launches0 = c->own_launches + (c->p32 ? c->p32->launches : 0) +
@@ -725,8 +757,15 @@ fh_status fh_solve_all(fh_ctx* c, double tol, int method, int max_iter, double* 
   if (!(tol > 0.0) || max_iter < 0) return fail(c, FH_ERR_ARG, "tol must be > 0, max_iter >= 0");
   if (method < FH_CG || method > FH_FIXED_POINT) return fail(c, FH_ERR_ARG, "unknown method");
   const int d = c->pb.d;
-  if (c->precision == FH_FP32) {
-    // no float64 pipeline to check the loads against: solve them one by one
+  bool ext = false;
+  for (int a = 0; a < d; ++a) {
+    bool e;
+    fh::factorable(c->pb.N[a], e);
+    ext = ext || e;
+  }
+  if (c->precision == FH_FP32 || ext) {
+    // no float64 pipeline to check the loads against (FH_FP32), or an axis
+    // whose plan runs one load per launch only: solve the loads one by one
     fh_status first = FH_OK;
     for (int b = 0; b < d; ++b) {
       double E[3] = {0, 0, 0};

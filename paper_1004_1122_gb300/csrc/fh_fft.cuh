@@ -1,5 +1,6 @@
 // fh_fft.cuh -- device FFT building blocks for odd lengths (radix 3, 5, 7 and
-// their products), float32, float64 and double-float (fh_dfloat.cuh).
+// their products; 11, 13 and 17 in the extended set), float32, float64 and
+// double-float (fh_dfloat.cuh).
 //
 // The discrete Fourier transform is the one of Eq. (DFT_def): forward
 // X[k] = sum_m x[m] exp(-2 pi i k m / n), inverse with +i and no 1/n (the
@@ -304,6 +305,16 @@ __device__ __forceinline__ void stockham_stage(cplx<T> (&v)[EM], cplx<T>* sm, in
 
 // Supported stage radices.  The plan stores them as small integers.
 #define FH_FOR_EACH_RADIX(X) X(3) X(5) X(7) X(9) X(15) X(25) X(27)
+// The extended set of the DynPlanX kernels: lengths with a prime factor 11,
+// 13 or 17 (for example the 255 = 3 * 5 * 17 grid of the paper's Section 3).
+#define FH_FOR_EACH_RADIX_X(X) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(25) X(27)
+
+// Largest prime radix of the extended set; every extended plan's register
+// array holds at least one butterfly of it.
+constexpr int kMaxPrimeX = 17;
+template <typename T> struct RegBudgetX {
+  static constexpr int value = RegBudget<T>::value > kMaxPrimeX ? RegBudget<T>::value : kMaxPrimeX;
+};
 
 // Maximum number of stages in a plan.
 constexpr int kMaxStages = 12;
@@ -312,26 +323,35 @@ struct FFTPlan {
   int n;                    // sequence length
   int nstages;
   int radix[kMaxStages];
+  int ext;                  // 1: uses a radix of the extended set (DynPlanX kernels)
 };
 
-// Run all stages of the plan on one sequence layout.
-template <bool INV, typename T>
+// Run all stages of the plan on one sequence layout.  X selects the extended
+// radix set (and its register budget).
+template <bool INV, typename T, bool X = false>
 __device__ __forceinline__ void run_fft(cplx<T>* sm, int is, const FFTPlan& pl, int u, int nthr,
                                         const cplx<T>* __restrict__ tw) {
-  constexpr int EM = RegBudget<T>::value;
+  constexpr int EM = X ? RegBudgetX<T>::value : RegBudget<T>::value;
   cplx<T> v[EM];
   int Ns = 1;
   for (int s = 0; s < pl.nstages; ++s) {
     const int R = pl.radix[s];
-    switch (R) {
 #define FH_STAGE_CASE(RR)                                                      \
   case RR:                                                                     \
     if constexpr (RR <= EM) stockham_stage<RR, INV, T, EM>(v, sm, is, pl.n, Ns, u, nthr, tw); \
     break;
-      FH_FOR_EACH_RADIX(FH_STAGE_CASE)
-#undef FH_STAGE_CASE
-      default: break;
+    if constexpr (X) {
+      switch (R) {
+        FH_FOR_EACH_RADIX_X(FH_STAGE_CASE)
+        default: break;
+      }
+    } else {
+      switch (R) {
+        FH_FOR_EACH_RADIX(FH_STAGE_CASE)
+        default: break;
+      }
     }
+#undef FH_STAGE_CASE
     Ns *= R;
   }
 }
@@ -390,47 +410,51 @@ __device__ __forceinline__ void fused_middle(cplx<T> (&v)[EM], cplx<T>* sm, int 
   __syncthreads();
 }
 
-template <typename T, typename F>
+template <typename T, typename F, bool X = false>
 __device__ __forceinline__ void run_fft_fused(cplx<T>* sm, int is, const FFTPlan& pl, int u, int nthr,
                                               const cplx<T>* __restrict__ tw, F& mid) {
-  constexpr int EM = RegBudget<T>::value;
+  constexpr int EM = X ? RegBudgetX<T>::value : RegBudget<T>::value;
   cplx<T> v[EM];
   const int S = pl.nstages;
   int Ns = 1;
+#define FH_SWITCH(R, CASE)             \
+  if constexpr (X) {                   \
+    switch (R) {                       \
+      FH_FOR_EACH_RADIX_X(CASE)        \
+      default: break;                  \
+    }                                  \
+  } else {                             \
+    switch (R) {                       \
+      FH_FOR_EACH_RADIX(CASE)          \
+      default: break;                  \
+    }                                  \
+  }
   for (int s = 0; s + 1 < S; ++s) {
-    switch (pl.radix[s]) {
 #define FH_STAGE_CASE(RR)                                                                          \
   case RR:                                                                                         \
     if constexpr (RR <= EM) stockham_stage<RR, false, T, EM>(v, sm, is, pl.n, Ns, u, nthr, tw); \
     break;
-      FH_FOR_EACH_RADIX(FH_STAGE_CASE)
+    FH_SWITCH(pl.radix[s], FH_STAGE_CASE)
 #undef FH_STAGE_CASE
-      default: break;
-    }
     Ns *= pl.radix[s];
   }
-  switch (pl.radix[S - 1]) {
 #define FH_MID_CASE(RR)                                                              \
   case RR:                                                                           \
     if constexpr (RR <= EM) fused_middle<RR, T, EM>(v, sm, is, pl.n, u, nthr, tw, mid); \
     break;
-    FH_FOR_EACH_RADIX(FH_MID_CASE)
+  FH_SWITCH(pl.radix[S - 1], FH_MID_CASE)
 #undef FH_MID_CASE
-    default: break;
-  }
   Ns = pl.radix[S - 1];
   for (int s = S - 2; s >= 0; --s) {
-    switch (pl.radix[s]) {
 #define FH_STAGE_CASE(RR)                                                                         \
   case RR:                                                                                        \
     if constexpr (RR <= EM) stockham_stage<RR, true, T, EM>(v, sm, is, pl.n, Ns, u, nthr, tw); \
     break;
-      FH_FOR_EACH_RADIX(FH_STAGE_CASE)
+    FH_SWITCH(pl.radix[s], FH_STAGE_CASE)
 #undef FH_STAGE_CASE
-      default: break;
-    }
     Ns *= pl.radix[s];
   }
+#undef FH_SWITCH
 }
 
 // ----------------------------------------------------------------------------
@@ -441,6 +465,8 @@ __device__ __forceinline__ void run_fft_fused(cplx<T>* sm, int is, const FFTPlan
 // into the kernel (the run-time dispatcher above instantiates every radix for
 // both directions, which overflows the instruction cache of a busy SM).
 struct DynPlan {};
+// Run-time plan over the extended radix set (primes 11, 13, 17 as well).
+struct DynPlanX {};
 
 template <int... Rs> struct CPlan {
   static constexpr int S = sizeof...(Rs);
@@ -500,7 +526,9 @@ template <bool INV, typename T, typename P>
 __device__ __forceinline__ void fft_plan(cplx<T>* sm, int is, const FFTPlan& pl, int u, int nthr,
                                          const cplx<T>* __restrict__ tw) {
   if constexpr (std::is_same<P, DynPlan>::value)
-    run_fft<INV, T>(sm, is, pl, u, nthr, tw);
+    run_fft<INV, T, false>(sm, is, pl, u, nthr, tw);
+  else if constexpr (std::is_same<P, DynPlanX>::value)
+    run_fft<INV, T, true>(sm, is, pl, u, nthr, tw);
   else
     run_fft_ct<INV, T, P>(sm, is, u, nthr, tw);
 }
@@ -509,7 +537,9 @@ template <typename T, typename P, typename F>
 __device__ __forceinline__ void fft_fused_plan(cplx<T>* sm, int is, const FFTPlan& pl, int u, int nthr,
                                                const cplx<T>* __restrict__ tw, F& mid) {
   if constexpr (std::is_same<P, DynPlan>::value)
-    run_fft_fused<T>(sm, is, pl, u, nthr, tw, mid);
+    run_fft_fused<T, F, false>(sm, is, pl, u, nthr, tw, mid);
+  else if constexpr (std::is_same<P, DynPlanX>::value)
+    run_fft_fused<T, F, true>(sm, is, pl, u, nthr, tw, mid);
   else
     run_fft_fused_ct<T, P>(sm, is, u, nthr, tw, mid);
 }

@@ -89,6 +89,13 @@ struct Scal {
   double best_rel; // smallest relative residual so far
   int best_iter;   // iteration at which best_rel last halved
   int stall_window;// > 0: stop as kStalled after this many iterations without halving
+  // Per-iteration norms of Section 3 (device arrays of hist_cap entries, or nullptr):
+  // hist_eta_r[m] = Eq. (errR_def) ||L0 (e_{m+1} - e_m)|| / ||e0|| for an
+  // isotropic L0 = l0iso I (NaN when l0iso == 0); hist_eta_e[m] = Eq. (errE_def)
+  // of the iterate e_m (written by k_eta_record).
+  double* hist_eta_r;
+  double* hist_eta_e;
+  double l0iso;
 };
 
 // kStalled: the recursive residual stopped decreasing (the working precision's
@@ -1057,6 +1064,7 @@ struct VecArgsBase {
 
 template <typename T> struct VecArgs {
   VecArgsBase b;
+  int want_pp;             // CG: also reduce (p, p) (eta_r history)
   T* x[kMaxLoads];
   T* r[kMaxLoads];
   const T* p[kMaxLoads];
@@ -1095,7 +1103,8 @@ __device__ __forceinline__ void for_range(long long b, long long e, long long t,
   for (long long i = hb + nv * W + t; i < e; i += stride) f.scalar(i);
 }
 
-template <typename T>
+// PP: also accumulate (p, p) into *dpp (the eta_r history of Section 3).
+template <typename T, bool PP = false>
 struct CgUpd {
   using V = typename Vec16<T>::type;
   static constexpr int W = Vec16<T>::n;
@@ -1105,11 +1114,14 @@ struct CgUpd {
   const T* __restrict__ ap;
   T al;
   DotAcc<T>* dot;
+  DotAcc<T>* dpp;
   __device__ __forceinline__ void scalar(long long i) {
-    x[i] += al * p[i];
+    const T pi = p[i];
+    x[i] += al * pi;
     const T rn = r[i] - al * ap[i];
     r[i] = rn;
     dot->add(rn * rn);
+    if (PP) dpp->add(pi * pi);
   }
   __device__ __forceinline__ void vec2(long long k0, long long k1) {
     V xv[2], rv[2], pv[2], av[2];
@@ -1131,6 +1143,7 @@ struct CgUpd {
         const T rn = vlane<V, T>(rv[u], w) - al * vlane<V, T>(av[u], w);
         vlane<V, T>(rv[u], w) = rn;
         dot->add(rn * rn);
+        if (PP) dpp->add(vlane<V, T>(pv[u], w) * vlane<V, T>(pv[u], w));
       }
       reinterpret_cast<V*>(x)[kk[u]] = xv[u];
       reinterpret_cast<V*>(r)[kk[u]] = rv[u];
@@ -1149,14 +1162,17 @@ struct BicgUpd {
   T al;
   DotAcc<T>* d1;
   DotAcc<T>* d2;
+  DotAcc<T>* d3;  // (p, p)
   __device__ __forceinline__ void scalar(long long i) {
-    x[i] += al * p[i];
+    const T pi = p[i];
+    x[i] += al * pi;
     const T rn = r[i] - al * ap[i];
     const T sn = rs[i] - al * atps[i];
     r[i] = rn;
     rs[i] = sn;
     d1->add(rn * sn);
     d2->add(rn * rn);
+    d3->add(pi * pi);
   }
   __device__ __forceinline__ void vec2(long long k0, long long k1) {
     constexpr int W = Vec16<T>::n;
@@ -1188,51 +1204,57 @@ __device__ __forceinline__ void cell_ranges(const VecArgs<T>& a, Mk&& mk) {
   }
 }
 
-// CG: x += alpha p; r -= alpha A p; partial (r, r)
-template <typename T, int NL>
+// CG: x += alpha p; r -= alpha A p; partial (r, r) at slot l, and with PP
+// (p, p) at slot kMaxLoads + l (for the eta_r history)
+template <typename T, int NL, bool PP = false>
 __global__ void k_cg_update(VecArgs<T> a) {
   const int bpc = gridDim.x / a.b.ncell;
   const int cell = blockIdx.x / bpc;
   Scal* const sc = a.scal + cell * NL;
   if (all_done(sc, NL)) return;
-  double acc[NL];
+  constexpr int NV = PP ? kMaxLoads + NL : NL;
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
-    acc[l] = 0.0;
     if (sc[l].done != kRunning) continue;
-    DotAcc<T> dot;
-    CgUpd<T> f{a.x[l], a.r[l], a.p[l], a.ap[l], T(sc[l].alpha), &dot};
+    DotAcc<T> dot, dpp;
+    CgUpd<T, PP> f{a.x[l], a.r[l], a.p[l], a.ap[l], T(sc[l].alpha), &dot, &dpp};
     cell_ranges<T, NL>(a, [&](long long b0, long long e0, long long t, long long stride, int) {
       for_range<T>(b0, e0, t, stride, f);
     });
     acc[l] = dot.get();
+    if (PP) acc[PP ? kMaxLoads + l : 0] = dpp.get();
   }
-  block_reduce_store<NL>(acc, NL, a.part, gridDim.x, blockIdx.x);
+  block_reduce_store<NV>(acc, NV, a.part, gridDim.x, blockIdx.x);
 }
 
-// BiCG: x += alpha p; r -= alpha A p; r* -= alpha A^T p*; partials (r, r*), (r, r)
-// partial layout: (r, r*) of load l at slot l, (r, r) at slot kMaxLoads + l.
+// BiCG: x += alpha p; r -= alpha A p; r* -= alpha A^T p*; partials (r, r*), (r, r), (p, p)
+// partial layout: (r, r*) of load l at slot l, (r, r) at slot kMaxLoads + l,
+// (p, p) at slot 2 kMaxLoads + l.
 template <typename T, int NL>
 __global__ void k_bicg_update(VecArgs<T> a) {
   const int bpc = gridDim.x / a.b.ncell;
   const int cell = blockIdx.x / bpc;
   Scal* const sc = a.scal + cell * NL;
   if (all_done(sc, NL)) return;
-  double acc[2 * kMaxLoads];
+  double acc[3 * kMaxLoads];
 #pragma unroll
-  for (int i = 0; i < 2 * kMaxLoads; ++i) acc[i] = 0.0;
+  for (int i = 0; i < 3 * kMaxLoads; ++i) acc[i] = 0.0;
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
     if (sc[l].done != kRunning) continue;
-    DotAcc<T> d1, d2;
-    BicgUpd<T> f{a.x[l], a.r[l], a.rs[l], a.p[l], a.ap[l], a.atps[l], T(sc[l].alpha), &d1, &d2};
+    DotAcc<T> d1, d2, d3;
+    BicgUpd<T> f{a.x[l], a.r[l], a.rs[l], a.p[l], a.ap[l], a.atps[l], T(sc[l].alpha), &d1, &d2, &d3};
     cell_ranges<T, NL>(a, [&](long long b0, long long e0, long long t, long long stride, int) {
       for (long long i = b0 + t; i < e0; i += stride) f.scalar(i);
     });
     acc[l] = d1.get();
     acc[kMaxLoads + l] = d2.get();
+    acc[2 * kMaxLoads + l] = d3.get();
   }
-  block_reduce_store<2 * kMaxLoads>(acc, 2 * kMaxLoads, a.part, gridDim.x, blockIdx.x);
+  block_reduce_store<3 * kMaxLoads>(acc, 3 * kMaxLoads, a.part, gridDim.x, blockIdx.x);
 }
 
 // ----------------------------------------------------------------------------
@@ -1339,16 +1361,22 @@ static __global__ void k_scal_alpha(Scal* scal, const double* part, int np, int 
 static __global__ void k_scal_beta(Scal* scal, const double* part, int np, int ncell, int nl, int bicg) {
   const ItemRef r = item_ref(np, ncell, nl);
   if (!r.valid) return;
-  double rho_new = 0.0, rr_new;
+  double rho_new = 0.0, rr_new, pp = 0.0;
+  const bool want_pp = scal[r.item].hist_eta_r != nullptr;
   if (bicg) {
     rho_new = block_sum(item_part(part, r.l, np, r), r.bpc);
     rr_new = block_sum(item_part(part, kMaxLoads + r.l, np, r), r.bpc);
+    if (want_pp) pp = block_sum(item_part(part, 2 * kMaxLoads + r.l, np, r), r.bpc);
   } else {
     rr_new = block_sum(item_part(part, r.l, np, r), r.bpc);
+    if (want_pp) pp = block_sum(item_part(part, kMaxLoads + r.l, np, r), r.bpc);
   }
   if (threadIdx.x == 0) {
     Scal& s = scal[r.item];
     if (s.done != kRunning) return;
+    // eta_r of this step: ||L0 alpha p|| / ||e0|| (Eq. errR_def), index = step
+    if (s.hist_eta_r != nullptr && s.iter < s.hist_cap)
+      s.hist_eta_r[s.iter] = s.l0iso > 0.0 ? s.l0iso * fabs(s.alpha) * sqrt(pp / s.b2) : NAN;
     s.iter += 1;
     s.rel = sqrt(rr_new / s.b2);
     record_hist(s);
@@ -1379,11 +1407,26 @@ static __global__ void k_scal_fixed(Scal* scal, const double* part, int np, int 
     s.rr = rr;
     s.rel = sqrt(rr / s.b2);
     record_hist(s);
+    // the step e_{m+1} - e_m of the fixed point is the residual of e_m
+    if (s.hist_eta_r != nullptr && s.iter < s.hist_cap)
+      s.hist_eta_r[s.iter] = s.l0iso > 0.0 ? s.l0iso * s.rel : NAN;
     if (!finite_d(rr)) { s.done = kBreakdown; return; }
     s.iter += 1;
     if (rr <= s.tol2 * s.b2) { s.done = kConverged; return; }
     if (s.iter >= s.max_iter) { s.done = kCap; return; }
     if (stalled(s)) { s.done = kStalled; return; }
+  }
+}
+
+// eta_e history (Eq. errE_def): after the equilibrium-norm passes on the
+// current iterate, hist_eta_e[iter] = sqrt(sum_k |xi . j^(k)|^2 / |j^(0)|^2)
+// from the two partial rows of the kColEta pass (single item).
+static __global__ void k_eta_record(const double* part, int np, const Scal* scal) {
+  const double num = block_sum(part, np);
+  const double den = block_sum(part + np, np);
+  if (threadIdx.x == 0) {
+    const Scal& s = scal[0];
+    if (s.hist_eta_e != nullptr && s.iter < s.hist_cap) s.hist_eta_e[s.iter] = den > 0.0 ? sqrt(num / den) : 0.0;
   }
 }
 

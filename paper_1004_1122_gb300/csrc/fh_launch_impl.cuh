@@ -77,6 +77,22 @@ struct Launchers {
     FH_SM((k_col<T, D, kColEta>), c0)
     FH_SM((k_col<T, D, kColFwd>), c1)
     FH_SM((k_col<T, D, kColInv>), c1)
+    if constexpr (NL == 1) {
+      FH_SM((k_row_fwd<T, D, NL, kProApply, DynPlanX>), rs)
+      FH_SM((k_row_fwd<T, D, NL, kProPlain, DynPlanX>), rs)
+      FH_SM((k_row_fwd<T, D, NL, kProDir, DynPlanX>), rs)
+      FH_SM((k_row_fwd<T, D, NL, kProDirPlain, DynPlanX>), rs)
+      FH_SM((k_row_inv<T, D, NL, kEpiApply, DynPlanX>), rs)
+      FH_SM((k_row_inv<T, D, NL, kEpiApplyT, DynPlanX>), rs)
+      FH_SM((k_row_inv<T, D, NL, kEpiDir, DynPlanX>), rs)
+      FH_SM((k_row_inv<T, D, NL, kEpiDirShadow, DynPlanX>), rs)
+      FH_SM((k_row_inv<T, D, NL, kEpiFixed, DynPlanX>), rs)
+      FH_SM((k_row_inv<T, D, NL, kEpiResid, DynPlanX>), rs)
+      FH_SM((k_col<T, D, kColGreen, DynPlanX>), c0)
+      FH_SM((k_col<T, D, kColEta, DynPlanX>), c0)
+      FH_SM((k_col<T, D, kColFwd, DynPlanX>), c1)
+      FH_SM((k_col<T, D, kColInv, DynPlanX>), c1)
+    }
     if constexpr (kHasDf<T, D>) {
       FH_SM((k_col_green_df<>), c0)
       FH_SM((k_row_fwd<T, D, NL, kProApply, DynPlan, true>), rs)
@@ -99,6 +115,19 @@ struct Launchers {
         k_row_fwd<T, D, NL, kProDir, P><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
       }
+    }
+    if (a.plan.ext) {  // a length with a prime factor 11, 13 or 17
+      if constexpr (NL == 1) {
+        switch (pro) {
+          case kProApply: k_row_fwd<T, D, NL, kProApply, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kProPlain: k_row_fwd<T, D, NL, kProPlain, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kProDir: k_row_fwd<T, D, NL, kProDir, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kProDirPlain: k_row_fwd<T, D, NL, kProDirPlain, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+      }
+      return cudaErrorInvalidValue;
     }
     switch (pro) {
       case kProApply: k_row_fwd<T, D, NL, kProApply><<<L.grid, L.block, L.smem, st>>>(a); break;
@@ -123,6 +152,23 @@ struct Launchers {
         k_row_inv<T, D, NL, kEpiDir, P><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
       }
+    }
+    if (a.plan.ext) {  // a length with a prime factor 11, 13 or 17
+      if constexpr (NL == 1) {
+        switch (epi) {
+          case kEpiApply: k_row_inv<T, D, NL, kEpiApply, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kEpiApplyT: k_row_inv<T, D, NL, kEpiApplyT, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kEpiDir: k_row_inv<T, D, NL, kEpiDir, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kEpiDirShadow:
+            k_row_inv<T, D, NL, kEpiDirShadow, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a);
+            break;
+          case kEpiFixed: k_row_inv<T, D, NL, kEpiFixed, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kEpiResid: k_row_inv<T, D, NL, kEpiResid, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+      }
+      return cudaErrorInvalidValue;
     }
     switch (epi) {
       case kEpiApply: k_row_inv<T, D, NL, kEpiApply><<<L.grid, L.block, L.smem, st>>>(a); break;
@@ -154,6 +200,19 @@ struct Launchers {
           }
         }
       }
+    }
+    if (a.b.plan.ext) {  // a length with a prime factor 11, 13 or 17
+      if constexpr (NL == 1) {
+        switch (mode) {
+          case kColFwd: k_col<T, D, kColFwd, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kColInv: k_col<T, D, kColInv, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kColGreen: k_col<T, D, kColGreen, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          case kColEta: k_col<T, D, kColEta, DynPlanX><<<L.grid, L.block, L.smem, st>>>(a); break;
+          default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+      }
+      return cudaErrorInvalidValue;
     }
     switch (mode) {
       case kColFwd: k_col<T, D, kColFwd><<<L.grid, L.block, L.smem, st>>>(a); break;
@@ -197,7 +256,10 @@ struct Launchers {
     return cudaErrorInvalidValue;
   }
   static cudaError_t cg_update(const Launch& L, const VecArgs<T>& v, cudaStream_t st) {
-    k_cg_update<T, NL><<<L.grid, L.block, 0, st>>>(v);
+    if (v.want_pp)
+      k_cg_update<T, NL, true><<<L.grid, L.block, 0, st>>>(v);
+    else
+      k_cg_update<T, NL, false><<<L.grid, L.block, 0, st>>>(v);
     return cudaGetLastError();
   }
   static cudaError_t bicg_update(const Launch& L, const VecArgs<T>& v, cudaStream_t st) {

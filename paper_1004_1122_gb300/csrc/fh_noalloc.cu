@@ -206,7 +206,7 @@ extern "C" fh_status fh_apply_noalloc(int d, const int* N, const double* Y, cons
   if (!make_fft_plan(g.nlast, true, kRowMaxThreads, prow, tpl) ||
       !make_fft_plan(N[0], true, kColMaxThreads, pc0, tpc0) ||
       (d == 3 && !make_fft_plan(N[1], true, kColMaxThreads, pc1, tpc1))) {
-    set_err(errbuf, errlen, "axis lengths must factor into 3, 5 and 7");
+    set_err(errbuf, errlen, "axis lengths must factor into 3, 5, 7, 11, 13 and 17");
     return FH_ERR_UNSUPPORTED;
   }
   const size_t esz = sizeof(double2);

@@ -110,6 +110,12 @@ struct Pipeline {
   T* rhs[kMaxLoads] = {};
   double* hist = nullptr;
   int hist_cap = 0;
+  // per-iteration Section 3 norms (single-load, single-cell solves): device
+  // arrays of hist_cap entries, or nullptr
+  double* hist_eta_r = nullptr;
+  double* hist_eta_e = nullptr;
+  double l0iso = 0.0;          // L0 = l0iso I, or 0 when L0 is not isotropic
+  double* eta_bufs[2] = {};    // allocations behind hist_eta_e / hist_eta_r
   cudaStream_t st = nullptr;
   std::vector<void*> allocs;
   std::map<int, cudaGraphExec_t> graphs;  // key: method * 1024 + chunk
@@ -164,6 +170,8 @@ struct Pipeline {
   int run_method_ = 0, run_K_ = 8;
   long long run_guard_ = 0, run_guard_max_ = 0;
   cudaError_t enqueue_iter(int method);
+  // eta_e (Eq. errE_def) of the current iterate x[0] into hist_eta_e[iter]
+  cudaError_t enqueue_eta_record();
   cudaError_t enqueue_chunk(int method, int K);
   int chunk_size(int method) const;
 

@@ -81,6 +81,10 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) g.L0[i * 3 + j] = pb.L0[i * d + j];
   g.inv_nodes = 1.0 / (double)g.cell_nodes;
+  l0iso = g.L0[0];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (g.L0[i * 3 + j] != (i == j ? g.L0[0] : 0.0)) l0iso = 0.0;
   vlen = (long long)d * pb.nodes;
   phase = pb.d_phase;
   nphase = pb.nphase;
@@ -95,8 +99,13 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   if (!make_fft_plan(g.nlast, f64, kRowMaxThreads, prow, tpl, w.tpl) ||
       !make_fft_plan(pb.N[0], f64, kColMaxThreads, pcol0, tpc0, w.tpc0) ||
       (d == 3 && !make_fft_plan(pb.N[1], f64, kColMaxThreads, pcol1, tpc1, w.tpc1))) {
-    err = "no FFT plan for this grid (axis lengths must factor into 3, 5 and 7)";
+    err = "no FFT plan for this grid (axis lengths must factor into 3, 5, 7, 11, 13 and 17)";
     return 9;  // FH_ERR_UNSUPPORTED
+  }
+  const bool ext = prow.ext || pcol0.ext || (d == 3 && pcol1.ext);
+  if (ext && nloads != 1) {
+    err = "axis lengths with a prime factor 11, 13 or 17 run one load per launch only";
+    return 9;
   }
   const int M = g.M;
   const size_t smem_green = std::min<size_t>(150 * 1024, (size_t)optin - 4096);
@@ -226,7 +235,7 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     const size_t bytes = (size_t)pb.N[0] * cb0.Q * esz;
     const size_t smem = 128 + 2 * bytes;
     const bool aligned = bytes % 16 == 0 && (cb0.base_outer * esz) % 16 == 0 && (cb0.base_inner * esz) % 16 == 0;
-    if (allow && d == 2 && lt.col_pipe && aligned && col0.block <= kColPipeMaxThreads &&
+    if (allow && d == 2 && !pcol0.ext && lt.col_pipe && aligned && col0.block <= kColPipeMaxThreads &&
         smem + 1024 <= (size_t)optin &&
         lt.set_smem_pipe(smem) == cudaSuccess) {
       int per_sm = 0;
@@ -316,7 +325,7 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   const int nred = std::max(std::max(items, ncell * d), 16);
   if ((rc = dev_alloc(allocs, &scal, nscal, err))) return rc;
   if ((rc = dev_alloc(allocs, &scal_aux, nscal, err))) return rc;
-  if ((rc = dev_alloc(allocs, &part, (size_t)2 * kMaxLoads * part_stride, err))) return rc;
+  if ((rc = dev_alloc(allocs, &part, (size_t)3 * kMaxLoads * part_stride, err))) return rc;
   if ((rc = dev_alloc(allocs, &d_red, nred, err))) return rc;
   FH_CKS(cudaMallocHost(&h_scal, 2 * nscal * sizeof(Scal)));
   FH_CKS(cudaMallocHost(&h_red, nred * sizeof(double)));
@@ -478,11 +487,13 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
     }
     v.scal = scal;
     v.part = part;
+    v.want_pp = hist_eta_r != nullptr && items == 1;
     ++launches;
     FH_CK(lt.cg_update(vec, v, st));
     ++launches;
     k_scal_beta<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, vec.grid, ncell, nloads, 0);
-    return cudaGetLastError();
+    FH_CK(cudaGetLastError());
+    return hist_eta_e != nullptr && items == 1 ? enqueue_eta_record() : cudaSuccess;
   }
   if (method == kBiCG) {
     // A^T p* with p* = r* + beta p*
@@ -525,7 +536,8 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
     FH_CK(lt.bicg_update(vec, v, st));
     ++launches;
     k_scal_beta<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, vec.grid, ncell, nloads, 1);
-    return cudaGetLastError();
+    FH_CK(cudaGetLastError());
+    return hist_eta_e != nullptr && items == 1 ? enqueue_eta_record() : cudaSuccess;
   }
   // fixed point: e <- rhs - B e
   RowArgs<T> f = a, i = a;
@@ -538,12 +550,26 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
   FH_CK(passes(kProApply, kEpiFixed, f, i, scal));
   ++launches;
   k_scal_fixed<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, row.grid, ncell, nloads);
+  FH_CK(cudaGetLastError());
+  return hist_eta_e != nullptr && items == 1 ? enqueue_eta_record() : cudaSuccess;
+}
+
+template <typename T>
+cudaError_t Pipeline<T>::enqueue_eta_record() {
+  // j = L x (the passes of eta_e with the L table), then the equilibrium sums
+  RowArgs<T> a = row_args();
+  a.tab = ltab;
+  for (int l = 0; l < kMaxLoads; ++l) a.in[l] = x[0];
+  FH_CK(launch_row_fwd(kProApply, a));
+  FH_CK(launch_green(kColEta, nullptr, part));
+  ++launches;
+  k_eta_record<<<1, kRedThreads, 0, st>>>(part, col0.grid, scal);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Pipeline<T>::enqueue_chunk(int method, int K) {
-  const int key = (method * 2 + (rhs_active_ ? 1 : 0)) * 4096 + K;
+  const int key = ((method * 2 + (rhs_active_ ? 1 : 0)) * 2 + (hist_eta_e || hist_eta_r ? 1 : 0)) * 4096 + K;
   auto it = graphs.find(key);
   if (it == graphs.end()) {
     cudaGraph_t graph;
@@ -617,7 +643,8 @@ int Pipeline<T>::residual(const T* const* xin, T* const* rout, bool rhs_field,
     a.out[l] = rout[l];
     a.rhs[l] = rhs_field ? rhs[l] : nullptr;
   }
-  df_green = df && lt.col_df != nullptr && tw0_df != nullptr && tw_last_df != nullptr;
+  df_green = df && lt.col_df != nullptr && tw0_df != nullptr && tw_last_df != nullptr && !prow.ext &&
+             !pcol0.ext;  // the double-float kernels run the standard radix set only
   if (df_green) a.twdf = tw_last_df;
   const cudaError_t pe = passes(kProApply, kEpiResid, a, a, scal_aux);
   df_green = false;
@@ -772,6 +799,9 @@ int Pipeline<T>::solve_begin(int method, const double (*E)[kMaxD], bool rhs_fiel
     s.stall_window = stall_window;
     s.hist = items == 1 ? hist : nullptr;
     s.hist_cap = items == 1 ? hist_cap : 0;
+    s.hist_eta_r = items == 1 ? hist_eta_r : nullptr;
+    s.hist_eta_e = items == 1 ? hist_eta_e : nullptr;
+    s.l0iso = l0iso;
     for (int c = 0; c < kMaxD; ++c) s.E[c] = (!rhs_field && c < g.d) ? E[l][c] : 0.0;
   }
   FH_CKS(cudaMemcpyAsync(scal, h_scal, items * sizeof(Scal), cudaMemcpyHostToDevice, st));
@@ -828,6 +858,7 @@ int Pipeline<T>::solve_begin(int method, const double (*E)[kMaxD], bool rhs_fiel
       }
     }
   }
+  if (hist_eta_e != nullptr && items == 1) FH_CKS(enqueue_eta_record());  // iterate 0
   run_method_ = method;
   run_K_ = chunk_size(method);
   run_guard_ = 0;
@@ -848,7 +879,9 @@ int Pipeline<T>::autotune(const Problem& pb, int nloads_, cudaStream_t stream, T
     int best_st = 1 << 30;
     std::vector<std::pair<int, int>> all;  // (stages, tpl)
     for (int t = 1; t <= maxthr; ++t) {
-      std::vector<int> r = plan_radices(n, t, reg_budget(f64));
+      bool ext;
+      factorable(n, ext);
+      std::vector<int> r = plan_radices(n, t, ext ? reg_budget_x(f64) : reg_budget(f64));
       if (r.empty()) continue;
       const int st = (int)r.size();
       if (st < best_st) best_st = st;

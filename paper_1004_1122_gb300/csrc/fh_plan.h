@@ -14,21 +14,30 @@
 
 namespace fh {
 
-// Radices compiled into the stage dispatcher (must match FH_FOR_EACH_RADIX).
+// Radices compiled into the stage dispatchers (must match FH_FOR_EACH_RADIX
+// and FH_FOR_EACH_RADIX_X).  The extended primes 11, 13 and 17 are used only
+// by lengths that have one of them as a factor; those plans run the DynPlanX
+// kernels with the register budget RegBudgetX.
 inline const std::vector<int>& compiled_radices() {
-  static const std::vector<int> r = {27, 25, 15, 9, 7, 5, 3};
+  static const std::vector<int> r = {27, 25, 17, 15, 13, 11, 9, 7, 5, 3};
   return r;
 }
+inline bool extended_radix(int r) { return r % 11 == 0 || r % 13 == 0 || r % 17 == 0; }
 
 inline int reg_budget(bool fp64) { return fp64 ? RegBudget<double>::value : RegBudget<float>::value; }
+inline int reg_budget_x(bool fp64) { return fp64 ? RegBudgetX<double>::value : RegBudgetX<float>::value; }
 
-// Factor n = 3^a 5^b 7^c; returns false if another prime divides n.
-inline bool factor357(int n, int& a, int& b, int& c) {
-  a = b = c = 0;
+// Does n factor into the supported primes 3, 5, 7, 11, 13, 17?  ext is set
+// when one of 11, 13, 17 divides n.
+inline bool factorable(int n, bool& ext) {
+  ext = false;
   if (n < 1) return false;
-  while (n % 3 == 0) { n /= 3; ++a; }
-  while (n % 5 == 0) { n /= 5; ++b; }
-  while (n % 7 == 0) { n /= 7; ++c; }
+  for (int p : {3, 5, 7, 11, 13, 17}) {
+    while (n % p == 0) {
+      n /= p;
+      if (p > 7) ext = true;
+    }
+  }
   return n == 1;
 }
 
@@ -36,45 +45,42 @@ inline bool factor357(int n, int& a, int& b, int& c) {
 // by tpl threads: a stage of radix R is allowed iff every thread holds at most
 // floor(budget / R) butterflies, i.e. ceil(n / R / tpl) * R <= budget.
 // Returns the stage list (empty if impossible).  Radices are emitted largest
-// first.
+// first.  Dynamic programme over the divisors m of n: best[m] is a shortest
+// list of allowed radices whose product is m.
 inline std::vector<int> plan_radices(int n, int tpl, int budget) {
-  int a, b, c;
-  if (!factor357(n, a, b, c)) return {};
-  std::vector<std::tuple<int, int, int, int>> allowed;  // (R, i, j, k)
+  bool ext;
+  if (!factorable(n, ext)) return {};
+  std::vector<int> allowed;
   for (int R : compiled_radices()) {
     if (n % R) continue;
     const int bmax = budget / R;
     if (bmax < 1) continue;
     const int need = (n / R + tpl - 1) / tpl;
     if (need > bmax) continue;
-    int i, j, k;
-    factor357(R, i, j, k);
-    allowed.emplace_back(R, i, j, k);
+    allowed.push_back(R);
   }
-  // DP over exponent vectors
-  std::map<std::tuple<int, int, int>, std::vector<int>> best;
-  best[{0, 0, 0}] = {};
-  for (int x = 0; x <= a; ++x)
-    for (int y = 0; y <= b; ++y)
-      for (int z = 0; z <= c; ++z) {
-        if (x == 0 && y == 0 && z == 0) continue;
-        std::vector<int> cand;
-        bool found = false;
-        for (auto& t : allowed) {
-          int R, i, j, k;
-          std::tie(R, i, j, k) = t;
-          if (i > x || j > y || k > z) continue;
-          auto it = best.find({x - i, y - j, z - k});
-          if (it == best.end()) continue;
-          if (!found || it->second.size() + 1 < cand.size()) {
-            cand = it->second;
-            cand.push_back(R);
-            found = true;
-          }
-        }
-        if (found) best[{x, y, z}] = cand;
+  std::vector<int> divs;
+  for (int m = 1; m <= n; ++m)
+    if (n % m == 0) divs.push_back(m);  // ascending
+  std::map<int, std::vector<int>> best;
+  best[1] = {};
+  for (int m : divs) {
+    if (m == 1) continue;
+    bool found = false;
+    std::vector<int> cand;
+    for (int R : allowed) {
+      if (m % R) continue;
+      auto it = best.find(m / R);
+      if (it == best.end()) continue;
+      if (!found || it->second.size() + 1 < cand.size()) {
+        cand = it->second;
+        cand.push_back(R);
+        found = true;
       }
-  auto it = best.find({a, b, c});
+    }
+    if (found) best[m] = cand;
+  }
+  auto it = best.find(n);
   if (it == best.end()) return {};
   std::vector<int> r = it->second;
   std::sort(r.begin(), r.end(), [](int u, int v) { return u > v; });
@@ -83,9 +89,12 @@ inline std::vector<int> plan_radices(int n, int tpl, int budget) {
 
 // Choose (tpl, radices): fewest stages first, then the fewest threads per
 // sequence (more butterflies per thread, more independent work in flight).
+// Lengths with a prime factor 11, 13 or 17 get an extended plan (pl.ext = 1).
 inline bool make_fft_plan(int n, bool fp64, int max_tpl, FFTPlan& pl, int& tpl,
                           int force_tpl = 0) {
-  const int budget = reg_budget(fp64);
+  bool ext;
+  if (!factorable(n, ext)) return false;
+  const int budget = ext ? reg_budget_x(fp64) : reg_budget(fp64);
   int best_stages = 1 << 30, best_tpl = 0;
   std::vector<int> best_r;
   for (int t = 1; t <= max_tpl; ++t) {
@@ -102,6 +111,7 @@ inline bool make_fft_plan(int n, bool fp64, int max_tpl, FFTPlan& pl, int& tpl,
   pl.n = n;
   pl.nstages = (int)best_r.size();
   for (int s = 0; s < kMaxStages; ++s) pl.radix[s] = s < pl.nstages ? best_r[s] : 0;
+  pl.ext = ext ? 1 : 0;
   tpl = best_tpl;
   return true;
 }

@@ -79,6 +79,10 @@ class FhInfo(ctypes.Structure):
         ("launches", ctypes.c_longlong),
         ("flags", ctypes.c_int),
         ("ct_plans", ctypes.c_int),
+        ("eta_e_history", ctypes.POINTER(ctypes.c_double)),
+        ("eta_r_history", ctypes.POINTER(ctypes.c_double)),
+        ("eta_e_len", ctypes.c_int),
+        ("eta_r_len", ctypes.c_int),
     ]
 
 
@@ -185,7 +189,8 @@ def _dptr(a) -> ctypes.c_double:
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def _info_dict(info: FhInfo, hist: Optional[np.ndarray]) -> dict:
+def _info_dict(info: FhInfo, hist: Optional[np.ndarray], eta_e_h: Optional[np.ndarray] = None,
+               eta_r_h: Optional[np.ndarray] = None) -> dict:
     out = {
         "status": STATUS.get(info.status, info.status),
         "iters": info.iters,
@@ -200,6 +205,10 @@ def _info_dict(info: FhInfo, hist: Optional[np.ndarray]) -> dict:
     }
     if hist is not None:
         out["history"] = hist[: info.history_len].copy()
+    if eta_e_h is not None:
+        out["eta_e_history"] = eta_e_h[: info.eta_e_len].copy()
+    if eta_r_h is not None:
+        out["eta_r_history"] = eta_r_h[: info.eta_r_len].copy()
     return out
 
 
@@ -297,9 +306,12 @@ class Solver:
 
     def solve(self, E: Sequence[float], tol: float = 1e-8, method: str = "cg", max_iter: int = 10000,
               e_init=None, out=None, history: int = 0, want_field: bool = True, check: bool = False,
-              eta_e: bool = False):
+              eta_e: bool = False, norms: bool = False):
         """Solve for the load E.  Returns (field or None, L_eff column, info dict);
-        info["eta_e"] is computed (one float64 pass) only when eta_e is true."""
+        info["eta_e"] is computed (one float64 pass) only when eta_e is true.
+        With history > 0 and norms true, info["eta_e_history"] and
+        info["eta_r_history"] hold Eq. (errE_def) of every iterate and
+        Eq. (errR_def) of every step (FH_FP64 and FH_FP32 contexts)."""
         torch = self._torch
         Eh = np.ascontiguousarray(E, dtype=np.float64)
         if want_field and out is None:
@@ -307,11 +319,15 @@ class Solver:
         col = np.zeros(self.d)
         info = FhInfo()
         info.flags = 1 if eta_e else 0
-        hist = None
+        hist = eh = rh = None
         if history > 0:
             hist = np.zeros(history)
             info.history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             info.history_cap = history
+            if norms:
+                eh, rh = np.zeros(history), np.zeros(history)
+                info.eta_e_history = eh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                info.eta_r_history = rh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         rc = self.lib.fh_solve(self.ctx, _dptr(Eh), float(tol), METHODS[method], int(max_iter),
                                None if e_init is None else ctypes.c_void_p(e_init.data_ptr()),
                                None if out is None else ctypes.c_void_p(out.data_ptr()),
@@ -320,7 +336,7 @@ class Solver:
             self._check(rc, "fh_solve")
         elif rc not in (FH_OK, 6, 7):
             self._check(rc, "fh_solve")
-        return out, col, _info_dict(info, hist)
+        return out, col, _info_dict(info, hist, eh, rh)
 
     def solve_all(self, tol: float = 1e-8, method: str = "cg", max_iter: int = 10000):
         Leff = np.zeros((self.d, self.d))

@@ -32,6 +32,11 @@ CASES_2D = [
     ((5, 7), (1.0, 1.0)),
     ((3, 3), (1.0, 1.0)),          # smallest odd grid: one radix-3 stage per axis
     ((3, 2187), (1.0, 1.0)),       # a single row of tiles along axis 0, long lines
+    ((17, 17), (1.0, 1.0)),        # radix-17 stages (extended-radix plans)
+    ((255, 255), (1.0, 1.0)),      # 3 * 5 * 17: the model-problem grid of Section 3
+    ((51, 85), (1.0, 2.0)),        # 3 * 17 x 5 * 17, non-unit cell
+    ((11, 13), (1.0, 1.0)),        # radix 11 and 13
+    ((143, 9), (1.0, 1.0)),        # 11 * 13 along axis 0, a standard row axis
 ]
 CASES_3D = [
     ((9, 15, 27), (1.0, 1.0, 1.0)),
@@ -39,6 +44,8 @@ CASES_3D = [
     ((5, 21, 45), (1.0, 1.0, 1.0)),
     ((3, 5, 7), (1.0, 1.0, 1.0)),  # smallest mixed-radix 3-D grid
     ((243, 3, 9), (1.0, 1.0, 1.0)),
+    ((17, 11, 13), (1.0, 1.0, 1.0)),  # every axis extended
+    ((9, 17, 15), (1.0, 1.0, 1.0)),   # only the middle axis extended
 ]
 
 

@@ -297,3 +297,84 @@ def test_3d_full_tensor_loads_batched(prec, tol, bar, tmp_path, monkeypatch):
     assert np.max(np.abs(Le - Le.T)) < 10 * bar * np.max(np.abs(Lo))
     if tuned is not None:
         assert np.max(np.abs(tuned - Lo)) / np.max(np.abs(Lo)) < bar
+
+
+def _x1(rho, omega):
+    """Section 3's model problem: one centred disk at volume fraction 0.5 on
+    255^2 nodes, matrix L = I, particle L = rho I, reference medium
+    L0(omega) = (1 - omega + rho omega) I (Eq. ref_media_choice)."""
+    phase = micro.centred_disk(255, 0.5)
+    L = micro.isotropic_table([1.0, rho], 2)
+    L0 = (1.0 - omega + rho * omega) * np.eye(2)
+    return phase, L, L0
+
+
+@pytest.mark.parametrize("method", ["cg", "bicg", "fixed_point"])
+def test_model_problem_255_fp64_matches_oracle(method):
+    """Radix-17 plans on the paper's own grid: float64 CG, BiCG and the
+    fixed-point scheme reach the oracle's solution to 1e-10."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    # omega = 0.75: l0 = 7.75 > rho / 2, where the fixed-point series converges
+    phase, L, L0 = _x1(10.0, 0.75)
+    xo, io = oracle.cg(phase, L, L0, [1.0, 0.0], tol=1e-13)
+    with fh.Solver(phase, L, L0=L0, precision="fp64") as s:
+        x, col, info = s.solve([1.0, 0.0], tol=1e-12, method=method, max_iter=20000)
+    assert info["status"] == "FH_OK", info
+    assert _rel_l2(x.cpu().numpy(), xo) < 1e-10
+    if method == "cg":  # same algorithm, same start, same stopping tolerance
+        _, i12 = oracle.cg(phase, L, L0, [1.0, 0.0], tol=1e-12)
+        assert abs(info["iters"] - i12["iters"]) <= 1, (info["iters"], i12["iters"])
+
+
+def test_model_problem_255_refined_and_full_tensor():
+    """Float32 iterations with float64 refinement on 255^2 (the float64
+    residual runs float64 FFTs there), and fh_solve_all, which solves the loads
+    of an extended-radix grid one by one."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase, L, L0 = _x1(100.0, 0.5)
+    xo, _ = oracle.cg(phase, L, L0, [0.0, 1.0], tol=1e-13)
+    with fh.Solver(phase, L, L0=L0, precision="fp32_refined") as s:
+        x, col, info = s.solve([0.0, 1.0], tol=1e-10, method="cg", max_iter=20000)
+        assert info["status"] == "FH_OK", info
+        assert _rel_l2(x.cpu().numpy(), xo) < 1e-6
+        Le, infos = s.solve_all(tol=1e-10, method="cg", max_iter=20000)
+    assert all(i["status"] == "FH_OK" for i in infos)
+    x0, _ = oracle.cg(phase, L, L0, [1.0, 0.0], tol=1e-13)
+    Lo = oracle.effective_tensor([x0, xo], phase, L)
+    assert np.max(np.abs(Le - Lo)) / np.max(np.abs(Lo)) < 1e-6
+
+
+@pytest.mark.parametrize("method", ["cg", "bicg", "fixed_point"])
+def test_eta_histories_match_oracle(method):
+    """Per-iteration norms of Section 3 on the C1 problem (float64): the
+    eta_r history (Eq. errR_def, one entry per step) against the oracle's, and
+    the eta_e history (Eq. errE_def of every iterate, one extra pass set per
+    iteration) against oracle.eta_e of the oracle's iterates."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase, L, L0 = _c1()
+    E = [1.0, 0.0]
+    tol = 1e-6
+    with fh.Solver(phase, L, precision="fp64") as s:
+        _, _, info = s.solve(E, tol=tol, method=method, max_iter=5000, history=4096, norms=True)
+    assert info["status"] == "FH_OK", info
+    n = info["iters"]
+    er, ee = info["eta_r_history"], info["eta_e_history"]
+    assert len(er) == n and len(ee) == n + 1, (len(er), len(ee), n)
+    solver = {"cg": oracle.cg, "bicg": oracle.bicg, "fixed_point": oracle.fixed_point}[method]
+    _, io = solver(phase, L, L0, E, tol=1e-30, max_iter=n)
+    k = min(n, 12)  # round-off grows along the iteration; the leading steps agree tightly
+    assert np.allclose(er[:k], io["eta_r_history"][:k], rtol=1e-8, atol=0), (er[:k], io["eta_r_history"][:k])
+    for m in sorted({0, 1, 2, min(5, n)}):
+        xm, _ = solver(phase, L, L0, E, tol=1e-30, max_iter=m)
+        # the fixed point's iterate after m steps is the oracle's with max_iter = m - 1
+        if method == "fixed_point":
+            xm = oracle.operator.macroscopic_field(E, phase.shape) if m == 0 else \
+                solver(phase, L, L0, E, tol=1e-30, max_iter=m - 1)[0]
+        ref = oracle.eta_e(xm, phase, L)
+        assert abs(ee[m] - ref) <= 1e-9 * max(ref, 1e-300), (m, ee[m], ref)

@@ -259,3 +259,25 @@ def test_bicg_biorthogonality_nonsymmetric():
     off = M - np.diag(np.diag(M))
     assert np.max(np.abs(off)) < 1e-8
     assert np.min(np.abs(np.diag(M))) > 1e-6
+
+
+def test_eta_r_history_is_the_printed_norm_of_every_step():
+    """Eq. (errR_def) per step, checked against brute force: the CG iterate
+    after m steps is the oracle's result with max_iter = m, so
+    ||L0 (e_{m+1} - e_m)|| / ||e0|| comes from two separate solves; for the
+    fixed-point scheme the step is the residual, so eta_r = l0 * rel.res."""
+    rng = np.random.default_rng(41)
+    N = (15, 21)
+    phase = rng.integers(0, 2, size=N).astype(np.uint8)
+    L = micro.isotropic_table([1.0, 7.0], 2)
+    L0 = oracle.reference_medium(L)
+    E = [0.3, 1.0]
+    nb = np.linalg.norm(oracle.operator.macroscopic_field(E, N))
+    xs = [oracle.cg(phase, L, L0, E, tol=1e-30, max_iter=m)[0] for m in range(6)]
+    _, info = oracle.cg(phase, L, L0, E, tol=1e-30, max_iter=5)
+    assert len(info["eta_r_history"]) == 5
+    for m in range(5):
+        ref = np.linalg.norm(np.einsum("ab,b...->a...", L0, xs[m + 1] - xs[m])) / nb
+        assert abs(info["eta_r_history"][m] - ref) <= 1e-12 * ref, (m, info["eta_r_history"][m], ref)
+    _, fi = oracle.fixed_point(phase, L, L0, E, tol=1e-30, max_iter=6)
+    assert np.allclose(fi["eta_r_history"], L0[0, 0] * fi["history"], rtol=1e-13, atol=0)
