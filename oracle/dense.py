@@ -28,9 +28,14 @@ pins the Green operator and the operator assembly against an L0-free
 formulation.
 
 Storage order equals centred order: storage index i holds the node with
-centred index m = i - (N-1)/2 (odd N), and ``centred_indices`` lists m
-ascending, so a flattened storage-order field is already in centred order;
-only the centred m enters the DFT exponent.
+centred index m = i + min Z^N, and ``centred_indices`` lists m ascending, so a
+flattened storage-order field is already in centred order; only the centred m
+enters the DFT exponent (a constant shift of the node indices commutes with
+the operator).
+
+Even axes (the paper's grids are odd): the Green operator and the gradient
+leave out the frequencies with a Nyquist component, the reading under which
+both formulations are real and agree.
 """
 from __future__ import annotations
 
@@ -72,6 +77,16 @@ def _frequency_grid(N, Y):
     return np.stack([k.ravel().astype(np.float64) / Y[a] for a, k in enumerate(ks)])
 
 
+def _nyquist(N):
+    """True for the k in Z^N (C-order) with a component k_a = N_a / 2 on an even axis."""
+    ks = np.meshgrid(*[centred_indices(n) for n in N], indexing="ij")
+    out = np.zeros(int(np.prod(N)), bool)
+    for a, n in enumerate(N):
+        if n % 2 == 0:
+            out |= ks[a].ravel() == n // 2
+    return out
+
+
 def assemble_B(phase, L, L0, Y=None) -> np.ndarray:
     """Dense real matrix B of Eq. (mtrx_B) in centred node order, (d|N|, d|N|).
 
@@ -90,7 +105,7 @@ def assemble_B(phase, L, L0, Y=None) -> np.ndarray:
     xi = _frequency_grid(N, Y)
     q = np.einsum("ak,ab,bk->k", xi, L0, xi)
     G = np.zeros((d * size, d * size), dtype=np.complex128)
-    nz = q != 0.0
+    nz = (q != 0.0) & ~_nyquist(N)  # even axes: no Nyquist modes (see oracle.operator.gamma_hat)
     for a in range(d):
         for b in range(d):
             g = np.zeros(size)
@@ -108,7 +123,7 @@ def assemble_B(phase, L, L0, Y=None) -> np.ndarray:
     Fid = scipy.linalg.block_diag(*([Fi] * d))
     B = Fid @ G @ Fd @ DL
     if np.max(np.abs(B.imag)) > 1e-9 * max(1.0, np.max(np.abs(B.real))):
-        raise ValueError("B is not real: even N or non-symmetric frequency set")
+        raise ValueError("B is not real: non-symmetric frequency set")
     return B.real
 
 
@@ -143,11 +158,13 @@ def solve_potential(phase, L, E, Y=None) -> np.ndarray:
     size = int(np.prod(N))
     F, Fi = dft_matrices(N, Y)
     xi = _frequency_grid(N, Y)
+    nyq = _nyquist(N)
     D = []
     for a in range(d):
-        Da = Fi @ np.diag(1j * xi[a]) @ F
+        # the trigonometric gradient on the modes without a Nyquist component
+        Da = Fi @ np.diag(1j * xi[a] * ~nyq) @ F
         if np.max(np.abs(Da.imag)) > 1e-9 * max(1.0, np.max(np.abs(Da.real))):
-            raise ValueError("gradient is not real: even N")
+            raise ValueError("gradient is not real")
         D.append(Da.real)
     Dst = np.vstack(D)  # (d|N|, |N|)
     ph = phase.ravel()
@@ -157,7 +174,14 @@ def solve_potential(phase, L, E, Y=None) -> np.ndarray:
         for b in range(d):
             Lmat[a * size:(a + 1) * size, b * size:(b + 1) * size] = np.diag(Ln[:, a, b])
     Efield = np.repeat(np.asarray(E, dtype=np.float64), size)
-    K = Dst.T @ Lmat @ Dst + np.ones((size, size)) / size
+    # null space of D: the constant and (even axes) the Nyquist modes; add the
+    # orthogonal projector onto it, built from the inverse-DFT columns
+    null = np.nonzero(nyq | (np.abs(xi).sum(axis=0) == 0.0))[0]
+    P = np.zeros((size, size))
+    for j in null:
+        v = Fi[:, j] / np.linalg.norm(Fi[:, j])
+        P += np.outer(v, v.conj()).real
+    K = Dst.T @ Lmat @ Dst + P
     rhs = -Dst.T @ (Lmat @ Efield)
     phi = scipy.linalg.cho_solve(scipy.linalg.cho_factor(K), rhs)
     e = Efield + Dst @ phi

@@ -54,9 +54,22 @@ def ifftn(x, axes):
 
 
 def signed_frequencies(n: int) -> np.ndarray:
-    """Signed frequency of each FFT bin on an axis of length ``n`` (Z^N, Sec. 2.2)."""
+    """Signed frequency of each FFT bin on an axis of length ``n``: the set
+    Z^N of Section 2.2, -n/2 < k <= n/2 (for even n the Nyquist bin is +n/2)."""
     j = np.arange(n)
-    return np.where(j <= (n - 1) // 2, j, j - n)
+    return np.where(j <= n // 2, j, j - n)
+
+
+def nyquist_mask(N) -> np.ndarray:
+    """True at the frequencies with a Nyquist component (k_a = N_a / 2 on an
+    even axis), on the full FFT grid."""
+    d = len(N)
+    masks = [np.arange(n) == n // 2 if n % 2 == 0 else np.zeros(n, bool) for n in N]
+    grids = np.meshgrid(*masks, indexing="ij") if d > 1 else masks
+    out = np.zeros(tuple(N), bool)
+    for m in grids:
+        out |= m
+    return out
 
 
 def reference_medium(L: np.ndarray) -> np.ndarray:
@@ -82,6 +95,11 @@ def gamma_hat(N, Y, L0) -> np.ndarray:
     """Green operator Gamma0(k) of Section 2.1 on the grid: shape (d, d, *N).
 
     Gamma0(0) = 0 and Gamma0(k) = xi (x) xi / (xi . L0 . xi) otherwise.
+    Reading for an even axis (the paper uses odd grids): Gamma0 is zero at
+    every frequency with a Nyquist component.  The collocation operator is
+    then real, and its solution is the equilibrium solution on the
+    trigonometric polynomials without Nyquist modes (``oracle.dense`` checks
+    both characterisations against each other).
     """
     d = len(N)
     xi = wave_vectors(N, Y)
@@ -90,7 +108,7 @@ def gamma_hat(N, Y, L0) -> np.ndarray:
         for b in range(d):
             denom += xi[a] * L0[a, b] * xi[b]
     G = np.zeros((d, d) + tuple(N))
-    nz = denom != 0.0
+    nz = (denom != 0.0) & ~nyquist_mask(N)
     for a in range(d):
         for b in range(d):
             G[a, b][nz] = xi[a][nz] * xi[b][nz] / denom[nz]

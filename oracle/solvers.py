@@ -36,7 +36,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .operator import apply_A, apply_AT, fftn, macroscopic_field, signed_frequencies
+from .operator import apply_A, apply_AT, fftn, macroscopic_field, nyquist_mask, signed_frequencies
 
 
 def _dot(a: np.ndarray, b: np.ndarray) -> float:
@@ -227,6 +227,9 @@ def eta_e(e, phase, L, Y=None) -> float:
 
     eta_e^2 = sum_k |xi . j^(k)|^2 / |j^(0)|_2^2 with j = L e, xi_a = k_a / Y_a
     over every k in Z^N (k = 0 contributes zero); the DFT normalisation cancels.
+    On an even axis the frequencies with a Nyquist component are left out
+    (the reading of ``oracle.operator.gamma_hat``: equilibrium is not imposed
+    there).
     """
     e = np.asarray(e, dtype=np.float64)
     N = e.shape[1:]
@@ -234,5 +237,6 @@ def eta_e(e, phase, L, Y=None) -> float:
     jh = fftn(current(e, phase, L), axes=tuple(range(1, e.ndim)))
     ks = np.meshgrid(*[signed_frequencies(n) / Y[a] for a, n in enumerate(N)], indexing="ij")
     div = sum(ks[a] * jh[a] for a in range(len(N)))
+    div = np.where(nyquist_mask(N), 0.0, div)
     j0 = jh[(slice(None),) + (0,) * len(N)]
     return float(np.sqrt(np.sum(np.abs(div) ** 2) / np.sum(np.abs(j0) ** 2)))

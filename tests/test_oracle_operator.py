@@ -19,7 +19,9 @@ def _spd(rng, d, lo=0.5, hi=5.0):
 
 
 @pytest.mark.parametrize("N,Y", [((9, 15), (1.0, 2.5)), ((11, 7), (1.0, 1.0)),
-                                 ((5, 7, 3), (1.0, 0.5, 2.0))])
+                                 ((5, 7, 3), (1.0, 0.5, 2.0)),
+                                 ((6, 8), (1.0, 1.5)), ((4, 7), (1.0, 1.0)),   # even axes
+                                 ((4, 5, 6), (1.0, 1.0, 0.5))])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_apply_matches_dense_definition(N, Y, transpose):
     """FFT-based (I+B)e equals the dense product built from Eq. (DFT_def) / (mtrx_B).

@@ -24,7 +24,9 @@ def _spd(rng, d, lo=0.5, hi=5.0):
     return q @ np.diag(rng.uniform(lo, hi, size=d)) @ q.T
 
 
-@pytest.mark.parametrize("N,Y", [((15, 9), (1.0, 1.5)), ((5, 7, 5), (1.0, 1.0, 2.0))])
+@pytest.mark.parametrize("N,Y", [((15, 9), (1.0, 1.5)), ((5, 7, 5), (1.0, 1.0, 2.0)),
+                                 ((8, 6), (1.0, 1.0)), ((6, 9), (1.5, 1.0)),   # even axes
+                                 ((4, 6, 5), (1.0, 1.0, 1.0))])
 def test_lu_equals_potential_formulation(N, Y):
     """Dense LU of Eq. (linear_system) == the L0-free equilibrium form (module doc of
     oracle.dense), anisotropic phases, both loads."""
@@ -281,3 +283,24 @@ def test_eta_r_history_is_the_printed_norm_of_every_step():
         assert abs(info["eta_r_history"][m] - ref) <= 1e-12 * ref, (m, info["eta_r_history"][m], ref)
     _, fi = oracle.fixed_point(phase, L, L0, E, tol=1e-30, max_iter=6)
     assert np.allclose(fi["eta_r_history"], L0[0, 0] * fi["history"], rtol=1e-13, atol=0)
+
+
+def test_even_grid_solvers_reach_the_dense_solution_and_equilibrium():
+    """Even axes (zero Green operator on the Nyquist frequencies): CG and the
+    fixed point reach the dense LU solution, eta_e (without the Nyquist
+    frequencies) vanishes there, and the solution has no Nyquist mode."""
+    rng = np.random.default_rng(43)
+    N = (8, 10)
+    phase = rng.integers(0, 2, size=N).astype(np.uint8)
+    L = micro.isotropic_table([1.0, 6.0], 2)
+    L0 = oracle.reference_medium(L)
+    E = [1.0, -0.5]
+    xd = dense.solve_lu(phase, L, L0, E)
+    for solver in (oracle.cg, oracle.fixed_point):
+        x, info = solver(phase, L, L0, E, tol=1e-13, max_iter=20000)
+        assert info["status"] == "converged"
+        assert np.max(np.abs(x - xd)) < 1e-10
+    assert oracle.eta_e(xd, phase, L) < 1e-12
+    xh = np.fft.fft2(xd - np.asarray(E)[:, None, None])
+    nyq = oracle.operator.nyquist_mask(N)
+    assert np.max(np.abs(xh[:, nyq])) < 1e-10 * np.max(np.abs(xh))
