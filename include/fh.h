@@ -7,10 +7,14 @@
  *
  *     (I + B) e = e0,   B = F^-1 Gamma0 F dL          (Eq. linear_system, Eq. mtrx_B)
  *
- * for the periodic field e on an odd grid N = (N_0, ..., N_{d-1}) under a
+ * for the periodic field e on a grid N = (N_0, ..., N_{d-1}) under a
  * prescribed macroscopic field E (Eq. problem_def_2), with
  *   dL(x)     = L(x) - L0                              (Eq. current_decomp)
  *   Gamma0(k) = xi (x) xi / (xi . L0 . xi), Gamma0(0)=0, xi_a = k_a / Y_a  (Section 2.1)
+ * for k in Z^N (Section 2.2).  The paper's grids are odd; on an even axis the
+ * library takes Gamma0 = 0 at every frequency with a Nyquist component
+ * k_a = N_a / 2 (the solution is then the equilibrium solution among the
+ * trigonometric polynomials without Nyquist modes)
  * and returns the effective tensor L_eff[:, b] = <L e^(b)> (nodal mean).
  *
  * Conventions for every call:
@@ -45,8 +49,8 @@ typedef struct fh_ctx fh_ctx;
 typedef enum {
   FH_OK = 0,
   FH_ERR_ARG = 1,            /* invalid argument (null pointer, bad d/N/tol ...) */
-  FH_ERR_EVEN_N = 2,         /* an axis length is even; only odd N is supported
-                                (Section 3 footnote: odd grids avoid the Nyquist mode) */
+  FH_ERR_EVEN_N = 2,         /* reserved: even axis lengths are accepted (Nyquist
+                                frequencies carry no Green operator, see above) */
   FH_ERR_NOT_SPD = 3,        /* a phase tensor or L0 is not symmetric positive definite */
   FH_ERR_OOM = 4,            /* device allocation failed */
   FH_ERR_CUDA = 5,           /* a CUDA runtime call failed */
@@ -121,9 +125,9 @@ typedef struct {
  *
  *  out        host; receives the context (NULL on failure).
  *  d          2 or 3.
- *  N          host, d ints, each odd and >= 3; supported lengths are those
- *             that factor into 3, 5, 7, 11, 13 and 17 (a length with a
- *             factor 11, 13 or 17, such as the 255 = 3 * 5 * 17 grid of
+ *  N          host, d ints, each >= 3; supported lengths are those that
+ *             factor into 2, 3, 5, 7, 11, 13 and 17 (an even length, or one
+ *             with a factor 11, 13 or 17 such as the 255 = 3 * 5 * 17 grid of
  *             Section 3, runs the extended-radix kernels one load per launch).
  *  Y          host, d half side lengths (> 0), or NULL for all ones.
  *  phase      |N| bytes in C order, phase id per node (< nphase); a host
@@ -137,8 +141,8 @@ typedef struct {
  *             (FH_FP32_REFINED allocates both float32 and float64 paths).
  *  stream     cudaStream_t (as void*), or NULL for the legacy default stream.
  *
- * Errors: FH_ERR_ARG, FH_ERR_EVEN_N, FH_ERR_NOT_SPD, FH_ERR_UNSUPPORTED,
- * FH_ERR_OOM, FH_ERR_CUDA.  On error nothing is leaked. */
+ * Errors: FH_ERR_ARG, FH_ERR_NOT_SPD, FH_ERR_UNSUPPORTED, FH_ERR_OOM,
+ * FH_ERR_CUDA.  On error nothing is leaked. */
 fh_status fh_create(fh_ctx** out, int d, const int* N, const double* Y,
                     const uint8_t* phase, int phase_on_device, int nphase,
                     const double* L, const double* L0, int precision, void* stream);
@@ -247,8 +251,8 @@ fh_status fh_autotune_loads(fh_ctx* ctx, double* ms_before, double* ms_after);
  * CUDA-graph chunks.
  *  out        host; receives the batch.
  *  ncells     >= 1.
- *  N          host, 2*ncells ints (N_0, N_1 of each cell; odd, >= 3, factors
- *             3/5/7, or also 11/13/17 when nloads == 1).
+ *  N          host, 2*ncells ints (N_0, N_1 of each cell; >= 3, factors
+ *             3/5/7, or also 2/11/13/17 when nloads == 1).
  *  phase      host array of ncells host pointers, cell c has N_0*N_1 bytes.
  *  nphase     host, ncells ints in 1..256.
  *  L          host array of ncells host pointers, cell c has nphase[c]*4
@@ -256,8 +260,8 @@ fh_status fh_autotune_loads(fh_ctx* ctx, double* ms_before, double* ms_after);
  *  nloads     1 or 2 loads solved per cell.
  *  precision  FH_FP64 or FH_FP32_REFINED.
  * Everything is copied; the batch owns its device memory (one stream per
- * group).  Errors: FH_ERR_ARG, FH_ERR_EVEN_N, FH_ERR_NOT_SPD, FH_ERR_OOM,
- * FH_ERR_CUDA, FH_ERR_UNSUPPORTED. */
+ * group).  Errors: FH_ERR_ARG, FH_ERR_NOT_SPD, FH_ERR_OOM, FH_ERR_CUDA,
+ * FH_ERR_UNSUPPORTED. */
 typedef struct fh_batch fh_batch;
 fh_status fh_batch_create(fh_batch** out, int ncells, const int* N, const uint8_t* const* phase,
                           const int* nphase, const double* const* L, int nloads, int precision);
@@ -307,8 +311,8 @@ void fh_batch_destroy(fh_batch* b);
  * twiddle and dL tables live in fixed arrays inside the library, about
  * 16.1 MiB that every GPU loading the library keeps until the process exits.
  *
- *  d, N, Y     as fh_create (d = 2 or 3, odd N, each axis <= 2187 and built
- *              from 3, 5, 7, 11, 13 and 17; Y may be NULL).  Grids whose float64 half
+ *  d, N, Y     as fh_create (d = 2 or 3, each axis <= 2187 and built from
+ *              2, 3, 5, 7, 11, 13 and 17; Y may be NULL).  Grids whose float64 half
  *              spectrum exceeds 16 MiB (for example 2-D above ~1000^2, 3-D
  *              above ~85^3) are rejected with FH_ERR_UNSUPPORTED.
  *  phase       device, |N| bytes; ids >= nphase act as L = L0 (dL = 0).
@@ -328,12 +332,30 @@ void fh_batch_destroy(fh_batch* b);
  * stream capture on that device; resetting the device (cudaDeviceReset)
  * after that first call is not supported.  Every call is asynchronous on
  * `stream`: its twiddle and dL tables are filled by a kernel on that stream
- * (nothing is copied from host memory).  Errors: FH_ERR_ARG, FH_ERR_EVEN_N,
+ * (nothing is copied from host memory).  Errors: FH_ERR_ARG,
  * FH_ERR_NOT_SPD, FH_ERR_UNSUPPORTED, FH_ERR_CUDA. */
 fh_status fh_apply_noalloc(int d, const int* N, const double* Y, const uint8_t* phase,
                            int nphase, const double* L, const double* L0, const double* e_in,
                            double* e_out, int transpose, void* stream, char* errbuf,
                            size_t errlen);
+
+/* fh_set_wait_limit -- limit, in seconds, of the library's bounded device
+ * waits (the persistent Green pass's bulk-copy waits, the tensor-core
+ * convolution's commit waits): a wait that runs out ends its kernel with a
+ * device error word, and the call that launched it returns FH_ERR_TIMEOUT
+ * with its context still usable.  0 restores the default (2 s).  Applies to
+ * kernels launched, and CUDA graphs captured, after the call; a context keeps
+ * the graphs it captured earlier.  Process-wide.  (A failure-detection
+ * setting; the paper has no counterpart.)  Errors: FH_ERR_ARG. */
+fh_status fh_set_wait_limit(double seconds);
+
+/* fh_wait_selftest -- runs one bounded wait of `seconds` on an mbarrier that
+ * nothing completes, on `stream` (cudaStream_t as void*, NULL = legacy
+ * default stream), and reports it: FH_ERR_TIMEOUT when the wait gave up as it
+ * must (nothing is in flight, so the device stays usable), FH_OK if it
+ * completed.  Synchronises the stream.  Errors: FH_ERR_ARG (seconds outside
+ * (0, 60]), FH_ERR_CUDA. */
+fh_status fh_wait_selftest(double seconds, void* stream);
 
 /* fh_project_compatible -- out = Q in with Q = F^-1 Gamma0 F L0 (Section 2.1):
  * the projection onto the compatible (curl-free, zero-mean) fields along the

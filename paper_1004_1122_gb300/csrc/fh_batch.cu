@@ -141,10 +141,6 @@ fh_status fh_batch_create(fh_batch** out, int ncells, const int* N, const uint8_
       fh_batch_destroy(b);
       return FH_ERR_ARG;
     }
-    if (n0 % 2 == 0 || n1 % 2 == 0) {
-      fh_batch_destroy(b);
-      return FH_ERR_EVEN_N;
-    }
     for (int p = 0; p < nphase[c]; ++p)
       if (!spd2(L[c] + 4 * p)) {
         fh_batch_destroy(b);

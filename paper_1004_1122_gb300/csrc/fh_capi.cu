@@ -2,6 +2,7 @@
 // the matrix-free product, and the solve drivers (float64, float32, and
 // float32 inner solves with float64 refinement).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -260,7 +261,57 @@ bool l0_isotropic(const Problem& pb, double& l0) {
 
 }  // namespace
 
+// ---- bounded device waits ------------------------------------------------
+namespace {
+std::atomic<unsigned long long> g_wait_limit_ns{0};
+
+// Word written by the wait self-test: 1 when its wait gave up.
+__device__ int g_selftest_word;
+
+// One CTA: an mbarrier that expects one arrival which nothing makes; thread 0
+// waits on it with the given limit, then records whether the wait gave up.
+// Nothing is in flight, so the kernel ends cleanly either way.
+__global__ void k_wait_selftest(unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    fh::tma::mbar_init(&bar, 1);
+    fh::tma::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) g_selftest_word = fh::tma::mbar_wait(&bar, 0, limit_ns) ? 0 : 1;
+}
+}  // namespace
+
+namespace fh {
+namespace tma {
+unsigned long long wait_limit_ns() { return g_wait_limit_ns.load(); }
+}  // namespace tma
+}  // namespace fh
+
 extern "C" {
+
+fh_status fh_set_wait_limit(double seconds) {
+  if (!(seconds >= 0.0) || seconds > 3600.0) return FH_ERR_ARG;
+  g_wait_limit_ns.store((unsigned long long)(seconds * 1e9));
+  return FH_OK;
+}
+
+fh_status fh_wait_selftest(double seconds, void* stream) {
+  if (!(seconds > 0.0) || seconds > 60.0) return FH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int zero = 0;
+  cudaError_t e = cudaMemcpyToSymbolAsync(g_selftest_word, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32, 0, st>>>((unsigned long long)(seconds * 1e9));
+    e = cudaGetLastError();
+  }
+  int word = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyFromSymbolAsync(&word, g_selftest_word, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return FH_ERR_CUDA;
+  return word ? FH_ERR_TIMEOUT : FH_OK;
+}
 
 const char* fh_version(void) { return "fh 0.1.0 (sm_103a)"; }
 
@@ -303,7 +354,6 @@ fh_status fh_create(fh_ctx** out, int d, const int* N, const double* Y, const ui
   if (precision < FH_FP64 || precision > FH_FP32_REFINED) return FH_ERR_ARG;
   for (int a = 0; a < d; ++a) {
     if (N[a] < 3) return FH_ERR_ARG;
-    if (N[a] % 2 == 0) return FH_ERR_EVEN_N;
     if (Y && !(Y[a] > 0.0 && std::isfinite(Y[a]))) return FH_ERR_ARG;
   }
   fh_ctx* c = new (std::nothrow) fh_ctx();

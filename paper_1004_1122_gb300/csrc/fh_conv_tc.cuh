@@ -107,6 +107,7 @@ struct ConvTcArgs {
   const float* b;            // [O], or nullptr for no bias
   int n0, n1, n2;            // grid
   int* err;                  // device error word (bounded waits), or nullptr
+  unsigned long long wait_ns;  // limit of the primary waits (0: tma::kWaitLimitNs)
 };
 
 // Byte offset of element (row, k) of a K-major no-swizzle operand chunk.
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvTcArgs a) {
     unsigned char* Bm = A_lo + kABytes;
     if (ch >= 2) {
       // the MMAs of chunk ch - 2 have finished reading this stage
-      if (!tma::mbar_wait(&bar[st], ((ch - 2) >> 1) & 1)) s_fail = 1;
+      if (!tma::mbar_wait(&bar[st], ((ch - 2) >> 1) & 1, a.wait_ns)) s_fail = 1;
       __syncthreads();
       if (s_fail) break;
     }
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvTcArgs a) {
   // wait for the last chunk's MMAs (a commit covers every earlier MMA)
   if (!s_fail && nch > 0) {
     const int lc = nch - 1;
-    if (!tma::mbar_wait(&bar[lc & 1], (lc >> 1) & 1)) s_fail = 1;
+    if (!tma::mbar_wait(&bar[lc & 1], (lc >> 1) & 1, a.wait_ns)) s_fail = 1;
   }
   __syncthreads();
   fence_after();

@@ -1,6 +1,6 @@
-// fh_fft.cuh -- device FFT building blocks for odd lengths (radix 3, 5, 7 and
-// their products; 11, 13 and 17 in the extended set), float32, float64 and
-// double-float (fh_dfloat.cuh).
+// fh_fft.cuh -- device FFT building blocks (radix 3, 5, 7 and their products;
+// 2, 4, 8, 16, 11, 13 and 17 in the extended set for even lengths and the
+// larger primes), float32, float64 and double-float (fh_dfloat.cuh).
 //
 // The discrete Fourier transform is the one of Eq. (DFT_def): forward
 // X[k] = sum_m x[m] exp(-2 pi i k m / n), inverse with +i and no 1/n (the
@@ -12,7 +12,8 @@
 //    |x| <= pi/4 (our own constexpr routine; no math library involved).
 //  * dft<R>() is an R-point DFT held entirely in registers.  Odd primes use
 //    the symmetric form  X_k = x_0 + sum_j (x_j + x_{R-j}) cos - i (x_j - x_{R-j}) sin;
-//    composite R = P*Q is the textbook Cooley-Tukey split with inner twiddles.
+//    radix 2 the sum and difference; composite R = P*Q is the textbook
+//    Cooley-Tukey split with inner twiddles.
 //  * stage<R>() is one Stockham autosort pass over a sequence held in shared
 //    memory: butterfly j reads x[j + r n/R], applies the twiddles
 //    W_{Ns R}^{r (j mod Ns)}, transforms, and writes x[(j - j mod Ns) R + j mod Ns + r Ns]
@@ -189,6 +190,15 @@ template <int P, int S, bool INV, typename T> struct RegDFTImpl<P, S, INV, T, tr
   }
 };
 
+// radix 2 (even lengths): X_0 = x_0 + x_1, X_1 = x_0 - x_1 in either direction
+template <int S, bool INV, typename T> struct RegDFTImpl<2, S, INV, T, true> {
+  static __device__ __forceinline__ void run(cplx<T>* v) {
+    const cplx<T> a = v[0], b = v[S];
+    v[0] = cadd(a, b);
+    v[S] = csub(a, b);
+  }
+};
+
 // composite R = P * Q, P the smallest prime factor (decimation in time):
 //   n = P n2 + n1, k = k1 + Q k2:
 //   X[k1 + Q k2] = sum_n1 W_P^{n1 k2} W_R^{n1 k1} sum_n2 x[P n2 + n1] W_Q^{n2 k1}
@@ -305,9 +315,11 @@ __device__ __forceinline__ void stockham_stage(cplx<T> (&v)[EM], cplx<T>* sm, in
 
 // Supported stage radices.  The plan stores them as small integers.
 #define FH_FOR_EACH_RADIX(X) X(3) X(5) X(7) X(9) X(15) X(25) X(27)
-// The extended set of the DynPlanX kernels: lengths with a prime factor 11,
-// 13 or 17 (for example the 255 = 3 * 5 * 17 grid of the paper's Section 3).
-#define FH_FOR_EACH_RADIX_X(X) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(25) X(27)
+// The extended set of the DynPlanX kernels: lengths with a factor 2 (even
+// axes) or a prime factor 11, 13 or 17 (for example the 255 = 3 * 5 * 17 grid
+// of the paper's Section 3).
+#define FH_FOR_EACH_RADIX_X(X) \
+  X(2) X(3) X(4) X(5) X(7) X(8) X(9) X(11) X(13) X(15) X(16) X(17) X(25) X(27)
 
 // Largest prime radix of the extended set; every extended plan's register
 // array holds at least one butterfly of it.

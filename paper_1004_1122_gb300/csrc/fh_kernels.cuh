@@ -181,6 +181,7 @@ template <typename T> struct ColArgs {
   double* part;
   const double* L0cell;  // per-cell reference medium [ncell][9], or nullptr for g.L0
   int* err;              // device error word (bounded waits that expired), or nullptr
+  unsigned long long wait_ns;  // limit of the bounded waits (0: tma::kWaitLimitNs)
 };
 
 // ----------------------------------------------------------------------------
@@ -193,7 +194,13 @@ __device__ __forceinline__ bool all_done(const Scal* s, int nloads) {
   return true;
 }
 
-__device__ __forceinline__ int signed_freq(int j, int n) { return j <= (n - 1) / 2 ? j : j - n; }
+// Signed frequency of FFT bin j on an axis of n nodes: the set Z^N of
+// Section 2.2, -n/2 < k <= n/2.
+__device__ __forceinline__ int signed_freq(int j, int n) { return j <= n / 2 ? j : j - n; }
+// Bin j is the Nyquist frequency of an even axis.  The Green operator is zero
+// at every frequency with a Nyquist component (the reading for even grids;
+// the paper's grids are odd), and the equilibrium norm leaves them out.
+__device__ __forceinline__ bool nyquist_bin(int j, int n) { return (n & 1) == 0 && 2 * j == n; }
 
 // Dot-product accumulator.  float64 work accumulates directly; float32 work
 // uses compensated (Kahan) summation in float32, whose error is a few float32
@@ -477,19 +484,19 @@ struct GreenPoint2 {
     xi1 = T(kl) * invY1;
     n = n_;
     a = q & 1;
-    pad = kl >= g.H;
+    pad = kl >= g.H || nyquist_bin(kl, g.nlast);  // padding, or the last axis's Nyquist column
     kl0 = kl == 0;
   }
   __device__ __forceinline__ cplx<T> operator()(cplx<T> v, int i, bool act) const {
     cplx<T> o;
     o.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
     o.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
-    const int k0 = i <= (n - 1) / 2 ? i : i - n;
+    const int k0 = i <= n / 2 ? i : i - n;
     const T xi0 = T(k0) * invY0;
     const cplx<T> v0 = a == 0 ? v : o;
     const cplx<T> v1 = a == 0 ? o : v;
     const T den = xi0 * (L00 * xi0 + L01 * xi1) + xi1 * (L10 * xi0 + L11 * xi1);
-    const bool zero = !act || pad || (k0 == 0 && kl0);
+    const bool zero = !act || pad || (k0 == 0 && kl0) || nyquist_bin(i, n);
     const T f = zero ? T(0) : inv_nodes / den;
     const T sre = xi0 * v0.x + xi1 * v1.x;
     const T sim = xi0 * v0.y + xi1 * v1.y;
@@ -537,6 +544,9 @@ __device__ __forceinline__ void green_tile(const ColArgs<T>& a, cplx<T>* sm, int
     if (D == 3) xi[D - 1] = T(kl) * invY[D - 1];
     C* v = sm + (size_t)i * Q + q0;
     const bool pad = kl >= g.H;
+    // even axes: no Green operator and no equilibrium term at a Nyquist frequency
+    const bool nyq = nyquist_bin(i, n) || nyquist_bin(kl, g.nlast) ||
+                     (D == 3 && nyquist_bin(blk_inner * b.G + gl, g.n[1]));
     if (CM_ == kColGreen) {
       T den = T(0);
 #pragma unroll
@@ -552,7 +562,7 @@ __device__ __forceinline__ void green_tile(const ColArgs<T>& a, cplx<T>* sm, int
         sre += xi[p] * v[p].x;
         sim += xi[p] * v[p].y;
       }
-      const bool zero = pad || (k0 == 0 && k1 == 0 && kl == 0);
+      const bool zero = pad || nyq || (k0 == 0 && k1 == 0 && kl == 0);
       const T f = zero ? T(0) : inv_nodes / den;
 #pragma unroll
       for (int p = 0; p < D; ++p) {
@@ -560,7 +570,7 @@ __device__ __forceinline__ void green_tile(const ColArgs<T>& a, cplx<T>* sm, int
         v[p].y = xi[p] * sim * f;
       }
     } else {
-      if (!pad) {
+      if (!pad && !nyq) {
         double dre = 0.0, dim = 0.0;
 #pragma unroll
         for (int p = 0; p < D; ++p) {
@@ -703,18 +713,18 @@ struct GreenPointDF {
     inv_nodes = df_from(g.inv_nodes);
     n = n_;
     a = q & 1;
-    pad = kl >= g.H;
+    pad = kl >= g.H || nyquist_bin(kl, g.nlast);
     kl0 = kl == 0;
   }
   __device__ __forceinline__ dfc operator()(dfc v, int i, bool act) const {
     dfc o;
     o.x = df_shfl_xor(v.x, 1);
     o.y = df_shfl_xor(v.y, 1);
-    const int k0 = i <= (n - 1) / 2 ? i : i - n;
+    const int k0 = i <= n / 2 ? i : i - n;
     const dfl xi0 = df_mul_f(invY0, (float)k0);
     const dfc v0 = a == 0 ? v : o;
     const dfc v1 = a == 0 ? o : v;
-    const bool zero = !act || pad || (k0 == 0 && kl0);
+    const bool zero = !act || pad || (k0 == 0 && kl0) || nyquist_bin(i, n);
     const dfl den = xi0 * (L00 * xi0 + L01 * xi1) + xi1 * (L10 * xi0 + L11 * xi1);
     const dfl f = zero ? dfl(0.0f, 0.0f) : df_div(inv_nodes, zero ? dfl(1.0f, 0.0f) : den);
     const dfl sre = xi0 * v0.x + xi1 * v1.x;
@@ -831,7 +841,7 @@ __global__ void __launch_bounds__(kColPipeMaxThreads) k_col_pipe(ColArgs<T> a) {
       tma::bulk_wait_read();  // the store of item k-1 has read buffer (k+1)&1
       issue(wn, k + 1);
     }
-    if (!tma::mbar_wait(&bar[k & 1], (k >> 1) & 1)) s_fail = 1;
+    if (!tma::mbar_wait(&bar[k & 1], (k >> 1) & 1, a.wait_ns)) s_fail = 1;
     __syncthreads();
     if (s_fail) break;
     C* sm = buf0 + (k & 1) * bstride;
@@ -850,7 +860,9 @@ __global__ void __launch_bounds__(kColPipeMaxThreads) k_col_pipe(ColArgs<T> a) {
   }
   if (tid == 0) {
     if (s_fail) {
-      // a load is still owed to the other buffer when the next item existed
+      // drain (default limit) the load whose wait gave up, and the load owed
+      // to the other buffer when the next item existed, before leaving
+      tma::mbar_wait(&bar[k & 1], (k >> 1) & 1);
       if (w + gridDim.x < nitems) tma::mbar_wait(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1);
       if (a.err) atomicExch(a.err, 1);
     }
@@ -917,11 +929,11 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
       for (int u = 0; u < kUnroll; ++u) {
         const int kx = kb + u * blockDim.x;
         if (kx >= g.H) continue;
-        if (kx == 0) {
+        if (kx == 0 || 2 * kx == n) {  // bins that are their own Hermitian partner
           C w;
           w.x = y0[u].x;
           w.y = y1[u].x;
-          seq[0] = w;
+          seq[kx] = w;
         } else {
           C w, wm;
           w.x = y0[u].x - y1[u].y;

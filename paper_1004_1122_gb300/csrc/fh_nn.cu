@@ -389,6 +389,7 @@ cudaError_t conv(fh_nn* n, int layer, const float* in, float* out, bool trans) {
     ta.n1 = d.n1;
     ta.n2 = d.n2;
     ta.err = n->dev_err;
+    ta.wait_ns = fh::tma::wait_limit_ns();
     const unsigned g = (unsigned)((d.v() + fh::tc::kM - 1) / fh::tc::kM);
     fh::tc::k_conv_tc<<<g, fh::tc::kThreads, fh::tc::kSmemBytes, n->st>>>(ta);
   }

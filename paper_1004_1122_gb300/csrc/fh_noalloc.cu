@@ -152,7 +152,6 @@ extern "C" fh_status fh_apply_noalloc(int d, const int* N, const double* Y, cons
   long long nodes = 1;
   for (int a = 0; a < d; ++a) {
     if (N[a] < 3) { set_err(errbuf, errlen, "axis length < 3"); return FH_ERR_ARG; }
-    if (N[a] % 2 == 0) { set_err(errbuf, errlen, "even axis length"); return FH_ERR_EVEN_N; }
     if (N[a] > kMaxAxis) { set_err(errbuf, errlen, "axis length > 2187"); return FH_ERR_UNSUPPORTED; }
     if (Y && !(Y[a] > 0.0 && std::isfinite(Y[a]))) { set_err(errbuf, errlen, "bad Y"); return FH_ERR_ARG; }
     nodes *= N[a];
@@ -190,7 +189,7 @@ extern "C" fh_status fh_apply_noalloc(int d, const int* N, const double* Y, cons
   g.d = d;
   for (int a = 0; a < 3; ++a) g.n[a] = a < d ? N[a] : 1;
   g.nlast = N[d - 1];
-  g.H = (g.nlast + 1) / 2;
+  g.H = g.nlast / 2 + 1;  // half spectrum: 0 .. floor(n / 2) (the Nyquist bin of an even axis)
   g.nodes = nodes;
   g.nlines = (int)(nodes / g.nlast);
   g.n1 = d == 3 ? N[1] : 1;
@@ -206,7 +205,7 @@ extern "C" fh_status fh_apply_noalloc(int d, const int* N, const double* Y, cons
   if (!make_fft_plan(g.nlast, true, kRowMaxThreads, prow, tpl) ||
       !make_fft_plan(N[0], true, kColMaxThreads, pc0, tpc0) ||
       (d == 3 && !make_fft_plan(N[1], true, kColMaxThreads, pc1, tpc1))) {
-    set_err(errbuf, errlen, "axis lengths must factor into 3, 5, 7, 11, 13 and 17");
+    set_err(errbuf, errlen, "axis lengths must factor into 2, 3, 5, 7, 11, 13 and 17");
     return FH_ERR_UNSUPPORTED;
   }
   const size_t esz = sizeof(double2);

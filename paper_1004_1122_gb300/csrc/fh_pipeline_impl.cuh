@@ -60,7 +60,7 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   g.d = d;
   for (int a = 0; a < 3; ++a) g.n[a] = a < d ? pb.N[a] : 1;
   g.nlast = pb.N[d - 1];
-  g.H = (g.nlast + 1) / 2;
+  g.H = g.nlast / 2 + 1;  // half spectrum: 0 .. floor(n / 2) (the Nyquist bin of an even axis)
   g.nodes = pb.nodes;
   g.nlines = (int)(pb.nodes / g.nlast);
   g.n1 = d == 3 ? pb.N[1] : 1;
@@ -99,12 +99,12 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
   if (!make_fft_plan(g.nlast, f64, kRowMaxThreads, prow, tpl, w.tpl) ||
       !make_fft_plan(pb.N[0], f64, kColMaxThreads, pcol0, tpc0, w.tpc0) ||
       (d == 3 && !make_fft_plan(pb.N[1], f64, kColMaxThreads, pcol1, tpc1, w.tpc1))) {
-    err = "no FFT plan for this grid (axis lengths must factor into 3, 5, 7, 11, 13 and 17)";
+    err = "no FFT plan for this grid (axis lengths must factor into 2, 3, 5, 7, 11, 13 and 17)";
     return 9;  // FH_ERR_UNSUPPORTED
   }
   const bool ext = prow.ext || pcol0.ext || (d == 3 && pcol1.ext);
   if (ext && nloads != 1) {
-    err = "axis lengths with a prime factor 11, 13 or 17 run one load per launch only";
+    err = "even axis lengths and lengths with a prime factor 11, 13 or 17 run one load per launch only";
     return 9;
   }
   const int M = g.M;
@@ -408,6 +408,7 @@ cudaError_t Pipeline<T>::launch_green(int mode, Scal* sc, double* pt) {
   a.L0cell = L0cell_dev;
   a.err = dev_err;
   m.err = dev_err;
+  a.wait_ns = m.wait_ns = tma::wait_limit_ns();
   if (g.d == 3) {
     ++launches;
     FH_CK(lt.col(kColFwd, col1, m, st));
@@ -776,6 +777,9 @@ int Pipeline<T>::solve_begin(int method, const double (*E)[kMaxD], bool rhs_fiel
     }
   }
   rhs_active_ = rhs_field;
+  // a wait that expired in an earlier solve has been reported; start clean
+  FH_CKS(cudaMemsetAsync(dev_err, 0, sizeof(int), st));
+  *h_err = 0;
   std::vector<double> b2(items);
   if (rhs_field) {
     if ((rc = norm2(rhs, b2.data(), err))) return rc;

@@ -15,27 +15,27 @@
 namespace fh {
 
 // Radices compiled into the stage dispatchers (must match FH_FOR_EACH_RADIX
-// and FH_FOR_EACH_RADIX_X).  The extended primes 11, 13 and 17 are used only
-// by lengths that have one of them as a factor; those plans run the DynPlanX
-// kernels with the register budget RegBudgetX.
+// and FH_FOR_EACH_RADIX_X).  The extended radices (powers of 2 up to 16, and
+// the primes 11, 13 and 17) are used only by lengths that have one of 2, 11,
+// 13, 17 as a factor; those plans run the DynPlanX kernels with the register
+// budget RegBudgetX.
 inline const std::vector<int>& compiled_radices() {
-  static const std::vector<int> r = {27, 25, 17, 15, 13, 11, 9, 7, 5, 3};
+  static const std::vector<int> r = {27, 25, 17, 16, 15, 13, 11, 9, 8, 7, 5, 4, 3, 2};
   return r;
 }
-inline bool extended_radix(int r) { return r % 11 == 0 || r % 13 == 0 || r % 17 == 0; }
 
 inline int reg_budget(bool fp64) { return fp64 ? RegBudget<double>::value : RegBudget<float>::value; }
 inline int reg_budget_x(bool fp64) { return fp64 ? RegBudgetX<double>::value : RegBudgetX<float>::value; }
 
-// Does n factor into the supported primes 3, 5, 7, 11, 13, 17?  ext is set
-// when one of 11, 13, 17 divides n.
+// Does n factor into the supported primes 2, 3, 5, 7, 11, 13, 17?  ext is
+// set when one of 2, 11, 13, 17 divides n (the extended radix set).
 inline bool factorable(int n, bool& ext) {
   ext = false;
   if (n < 1) return false;
-  for (int p : {3, 5, 7, 11, 13, 17}) {
+  for (int p : {2, 3, 5, 7, 11, 13, 17}) {
     while (n % p == 0) {
       n /= p;
-      if (p > 7) ext = true;
+      if (p == 2 || p > 7) ext = true;
     }
   }
   return n == 1;
@@ -89,7 +89,8 @@ inline std::vector<int> plan_radices(int n, int tpl, int budget) {
 
 // Choose (tpl, radices): fewest stages first, then the fewest threads per
 // sequence (more butterflies per thread, more independent work in flight).
-// Lengths with a prime factor 11, 13 or 17 get an extended plan (pl.ext = 1).
+// Even lengths and lengths with a prime factor 11, 13 or 17 get an extended
+// plan (pl.ext = 1).
 inline bool make_fft_plan(int n, bool fp64, int max_tpl, FFTPlan& pl, int& tpl,
                           int force_tpl = 0) {
   bool ext;

@@ -19,7 +19,14 @@
 namespace fh {
 namespace tma {
 
+// Default limit of one wait.  Kernels take their primary waits' limit from
+// their launch arguments (fh_set_wait_limit; 0 there means this default); the
+// waits that drain a kernel's own copies in flight after a failure always use
+// this default, so that no copy can land in shared memory the kernel has left.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+// Process-wide limit set by fh_set_wait_limit (host side; 0 = default).
+unsigned long long wait_limit_ns();
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -79,21 +86,41 @@ __device__ __forceinline__ void bulk_wait_read() {
 // every committed bulk store has completed
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-// Wait until phase `parity` of bar has completed; false after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait until phase `parity` of bar has completed; false after limit_ns
+// nanoseconds (0: kWaitLimitNs).  try_wait may suspend the thread for a
+// hardware-chosen time while the phase is incomplete; with an explicit limit
+// that suspension is capped by the limit itself (the instruction's
+// suspend-time hint), so a short limit runs out even while a copy is still
+// in flight.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = 0) {
   const uint32_t a = saddr(bar);
   const unsigned long long t0 = globaltimer();
+  if (limit_ns == 0) {
+    while (true) {
+      uint32_t ok;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(a), "r"(parity)
+          : "memory");
+      if (ok) return true;
+      if (globaltimer() - t0 > kWaitLimitNs) return false;
+    }
+  }
+  const uint32_t hint = limit_ns < 0x7fffffffull ? (uint32_t)limit_ns : 0x7fffffffu;
   while (true) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(hint)
         : "memory");
     if (ok) return true;
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
 }
 

@@ -55,7 +55,7 @@ EXPORTS = (
     "fh_eta_e", "fh_profile", "fh_autotune", "fh_apply_noalloc", "fh_batch_create", "fh_batch_solve",
     "fh_batch_last_error", "fh_batch_destroy", "fh_project_compatible", "fh_autotune_loads",
     "fh_batch_autotune", "fh_destroy", "fh_status_string", "fh_last_error",
-    "fh_version",
+    "fh_version", "fh_set_wait_limit", "fh_wait_selftest",
     # fh_nn.h
     "fh_nn_create", "fh_nn_param_count", "fh_nn_launches", "fh_nn_set_params", "fh_nn_get_params",
     "fh_nn_forward", "fh_nn_gradients", "fh_nn_train_step", "fh_nn_destroy", "fh_nn_features",
@@ -181,6 +181,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fh_last_error.restype = ctypes.c_char_p
     lib.fh_version.argtypes = []
     lib.fh_version.restype = ctypes.c_char_p
+    lib.fh_set_wait_limit.argtypes = [D]
+    lib.fh_set_wait_limit.restype = I
+    lib.fh_wait_selftest.argtypes = [D, P]
+    lib.fh_wait_selftest.restype = I
     _lib = lib
     return lib
 
@@ -575,6 +579,19 @@ def nn_warm_start(solver: "Solver", pred, E, out, base=None):
     if rc != FH_OK:
         raise FhError(rc, "fh_nn_warm_start")
     return out
+
+
+def set_wait_limit(seconds: float) -> None:
+    """Limit of the bounded device waits (fh_set_wait_limit); 0 = default 2 s."""
+    rc = load_library().fh_set_wait_limit(float(seconds))
+    if rc != FH_OK:
+        raise FhError(rc, "fh_set_wait_limit")
+
+
+def wait_selftest(seconds: float, stream=None) -> int:
+    """fh_wait_selftest: the status of one bounded wait that nothing completes."""
+    st = 0 if stream is None else stream.cuda_stream
+    return int(load_library().fh_wait_selftest(float(seconds), ctypes.c_void_p(st)))
 
 
 def version() -> str:

@@ -51,16 +51,26 @@ def test_status_strings_without_gpu(lib):
 
 
 def test_create_rejects_bad_arguments_before_touching_the_device(lib):
-    """Argument validation happens on the host first: even N, bad d, null pointers."""
+    """Argument validation happens on the host first: short axes, bad d, null pointers."""
     lib.fh_create.restype = ctypes.c_int
     ctx = ctypes.c_void_p()
     N = (ctypes.c_int * 2)(8, 9)
     L = (ctypes.c_double * 4)(1, 0, 0, 1)
     ph = (ctypes.c_uint8 * 72)()
-    rc = lib.fh_create(ctypes.byref(ctx), 2, N, None, ph, 0, 1, L, None, 0, None)
-    assert rc == 2  # FH_ERR_EVEN_N
+    N2 = (ctypes.c_int * 2)(2, 9)
+    rc = lib.fh_create(ctypes.byref(ctx), 2, N2, None, ph, 0, 1, L, None, 0, None)
+    assert rc == 1  # FH_ERR_ARG: an axis below 3 nodes
     rc = lib.fh_create(ctypes.byref(ctx), 4, N, None, ph, 0, 1, L, None, 0, None)
     assert rc == 1  # FH_ERR_ARG
     rc = lib.fh_create(None, 2, N, None, ph, 0, 1, L, None, 0, None)
     assert rc == 1
     assert not ctx.value
+
+
+def test_wait_limit_is_validated_on_the_host(lib):
+    lib.fh_set_wait_limit.restype = ctypes.c_int
+    lib.fh_set_wait_limit.argtypes = [ctypes.c_double]
+    assert lib.fh_set_wait_limit(-1.0) == 1      # FH_ERR_ARG
+    assert lib.fh_set_wait_limit(float("nan")) == 1
+    assert lib.fh_set_wait_limit(0.5) == 0
+    assert lib.fh_set_wait_limit(0.0) == 0        # back to the default

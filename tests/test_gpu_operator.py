@@ -37,6 +37,12 @@ CASES_2D = [
     ((51, 85), (1.0, 2.0)),        # 3 * 17 x 5 * 17, non-unit cell
     ((11, 13), (1.0, 1.0)),        # radix 11 and 13
     ((143, 9), (1.0, 1.0)),        # 11 * 13 along axis 0, a standard row axis
+    ((8, 8), (1.0, 1.0)),          # even axes: radix 2/4/8, Nyquist frequencies
+    ((6, 10), (1.0, 2.0)),
+    ((16, 12), (1.0, 1.0)),
+    ((256, 256), (1.0, 1.0)),      # 2^8: radix-16 stages
+    ((3, 32), (1.0, 1.0)),         # even line, odd column
+    ((30, 3), (1.0, 1.0)),         # even column, odd line
 ]
 CASES_3D = [
     ((9, 15, 27), (1.0, 1.0, 1.0)),
@@ -46,6 +52,8 @@ CASES_3D = [
     ((243, 3, 9), (1.0, 1.0, 1.0)),
     ((17, 11, 13), (1.0, 1.0, 1.0)),  # every axis extended
     ((9, 17, 15), (1.0, 1.0, 1.0)),   # only the middle axis extended
+    ((8, 6, 10), (1.0, 1.0, 1.0)),    # every axis even
+    ((5, 4, 9), (1.0, 1.0, 1.0)),     # only the middle axis even
 ]
 
 

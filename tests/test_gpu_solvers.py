@@ -240,8 +240,9 @@ def test_invalid_inputs_rejected():
     torch = cuda_or_skip()
     from paper_1004_1122_gb300 import fh
 
-    with pytest.raises(fh.FhError):
-        fh.Solver(np.zeros((8, 9), np.uint8), micro.isotropic_table([1.0], 2))
+    with pytest.raises(fh.FhError) as ex:  # 19 has no FFT plan (primes 2 .. 17 only)
+        fh.Solver(np.zeros((19, 9), np.uint8), micro.isotropic_table([1.0], 2))
+    assert ex.value.status == 9  # FH_ERR_UNSUPPORTED
     with pytest.raises(fh.FhError):
         fh.Solver(np.zeros((9, 9), np.uint8), np.array([[[1.0, 2.0], [2.0, 1.0]]]))
     with pytest.raises(fh.FhError):
@@ -378,3 +379,30 @@ def test_eta_histories_match_oracle(method):
                 solver(phase, L, L0, E, tol=1e-30, max_iter=m - 1)[0]
         ref = oracle.eta_e(xm, phase, L)
         assert abs(ee[m] - ref) <= 1e-9 * max(ref, 1e-300), (m, ee[m], ref)
+
+
+@pytest.mark.parametrize("N", [(64, 48), (16, 12, 20)])
+def test_even_grids_match_oracle(N):
+    """Even axes (Green operator zero on the Nyquist frequencies, the reading
+    the oracle's dense and equilibrium forms agree on): float64 CG and float32
+    CG with float64 refinement reach the oracle's solution."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    rng = np.random.default_rng(sum(N))
+    d = len(N)
+    phase = (rng.random(N) < 0.35).astype(np.uint8)
+    L = micro.isotropic_table([1.0, 30.0], d)
+    L0 = oracle.reference_medium(L)
+    E = np.eye(d)[0]
+    xo, _ = oracle.cg(phase, L, L0, E, tol=1e-13)
+    with fh.Solver(phase, L, precision="fp64") as s:
+        x, col, info = s.solve(E, tol=1e-12, method="cg", max_iter=20000)
+    assert info["status"] == "FH_OK", info
+    assert _rel_l2(x.cpu().numpy(), xo) < 1e-10
+    with fh.Solver(phase, L, precision="fp32_refined") as s:
+        x, col, info = s.solve(E, tol=1e-10, method="cg", max_iter=20000)
+    assert info["status"] == "FH_OK", info
+    assert _rel_l2(x.cpu().numpy(), xo) < 1e-6
+    eta = oracle.eta_e(xo, phase, L)
+    assert eta < 1e-9
