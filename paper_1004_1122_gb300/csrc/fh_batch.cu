@@ -72,6 +72,7 @@ struct Group {
   double* x64[fh::kMaxLoads] = {};  // refinement iterate per load
   double* r64[fh::kMaxLoads] = {};
   long long launches0 = 0;
+  fh::LoopCache loops32, loops64;  // device-side iteration loops of this group alone
 };
 
 bool spd2(const double* A) {
@@ -97,14 +98,20 @@ struct fh_batch {
   std::vector<Group> groups;
   std::string err;
   long long own_launches = 0;
+  fh::LoopCache loops32, loops64;  // device-side iteration loops over all groups
 };
 
 extern "C" {
 
 void fh_batch_destroy(fh_batch* b) {
   if (!b) return;
-  for (Group& g : b->groups) {
+  for (Group& g : b->groups)
     if (g.st) cudaStreamSynchronize(g.st);
+  b->loops32.clear();
+  b->loops64.clear();
+  for (Group& g : b->groups) {
+    g.loops32.clear();
+    g.loops64.clear();
     if (g.p32) {
       g.p32->release();
       delete g.p32;
@@ -301,7 +308,7 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
                        double tol, int method, int max_iter, int precision,
                        std::vector<std::vector<int>>& st, std::vector<std::vector<int>>& its,
                        std::vector<std::vector<double>>& rel, int& outer, long long& own_launches,
-                       std::string& err) {
+                       fh::LoopCache& loops32, fh::LoopCache& loops64, std::string& err) {
   double e2[fh::kMaxLoads] = {};
   for (int l = 0; l < nl; ++l)
     for (int a = 0; a < d; ++a) e2[l] += Ev[l][a] * Ev[l][a];
@@ -324,30 +331,11 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
       int rc = g.p64->solve_begin(method, Ev, false, fh::kX0Const, nullptr, tol, max_iter, err);
       if (rc) return fail(rc);
     }
-    std::vector<bool> done(ng, false);
-    for (long long round = 0;; ++round) {
-      bool all = true;
-      for (int gi = 0; gi < ng; ++gi) {
-        if (done[gi]) continue;
-        int rc = (*groups[gi]).p64->solve_step(err);
-        if (rc) return fail(rc);
-      }
-      for (int gi = 0; gi < ng; ++gi) {
-        if (done[gi]) continue;
-        cudaError_t e = cudaStreamSynchronize((*groups[gi]).st);
-        if (e != cudaSuccess) return FH_ERR_CUDA;
-        if ((*groups[gi]).p64->device_error()) return FH_ERR_TIMEOUT;
-        done[gi] = (*groups[gi]).p64->solve_done();
-        all = all && done[gi];
-      }
-      if (all) break;
-      if (round > (long long)max_iter + 64) {
-        // the host ran out of rounds before every item reported a status: an
-        // iteration overrun, not an expired device wait
-        err = "iteration guard exceeded without a device status";
-        return FH_ERR_NOT_CONVERGED;
-      }
-    }
+    // every group's iterations in one graph launch (a while node per group)
+    std::vector<Pipeline<double>*> ps;
+    for (Group* gp : groups) ps.push_back(gp->p64);
+    int rc = fh::run_loops<double>(ps.data(), ng, groups[0]->st, loops64, err);
+    if (rc) return fail(rc);
     for (int gi = 0; gi < ng; ++gi) {
       Group& g = *groups[gi];
       std::vector<SolveResult> res(g.cells.size() * nl);
@@ -430,7 +418,7 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
       for (int gi = 0; gi < ng; ++gi)
         for (size_t it = 0; it < its[gi].size(); ++it)
           if (st[gi][it] == fh::kRunning) budget = std::max(budget, max_iter - its[gi][it]);
-      // inner solves of every group, concurrently
+      // inner solves of every group, all iterations in one graph launch
       std::vector<bool> active(ng, false);
       for (int gi = 0; gi < ng; ++gi) {
         Group& g = *groups[gi];
@@ -453,24 +441,13 @@ fh_status solve_groups(std::vector<Group*>& groups, int d, int nl, const double 
                                     kInnerStallWindow);
         if (rc) return fail(rc);
       }
-      for (long long round = 0;; ++round) {
-        bool all = true;
-        for (int gi = 0; gi < ng; ++gi) {
-          if (!active[gi]) continue;
-          int rc = (*groups[gi]).p32->solve_step(err);
+      {
+        std::vector<Pipeline<float>*> ps;
+        for (int gi = 0; gi < ng; ++gi)
+          if (active[gi]) ps.push_back(groups[gi]->p32);
+        if (!ps.empty()) {
+          int rc = fh::run_loops<float>(ps.data(), (int)ps.size(), ps[0]->st, loops32, err);
           if (rc) return fail(rc);
-        }
-        for (int gi = 0; gi < ng; ++gi) {
-          if (!active[gi]) continue;
-          if (cudaStreamSynchronize((*groups[gi]).st) != cudaSuccess) return FH_ERR_CUDA;
-          if ((*groups[gi]).p32->device_error()) return FH_ERR_TIMEOUT;
-          if ((*groups[gi]).p32->solve_done()) active[gi] = false;
-          all = all && !active[gi];
-        }
-        if (all) break;
-        if (round > (long long)budget + 64) {
-          err = "iteration guard exceeded without a device status";
-          return FH_ERR_NOT_CONVERGED;
         }
       }
       for (int gi = 0; gi < ng; ++gi) {
@@ -515,7 +492,7 @@ fh_status fh_batch_solve(fh_batch* b, const double* E, double tol, int method, i
   int outer = 0;
   std::string err;
   fh_status rs = solve_groups(groups, 2, nl, Ev, tol, method, max_iter, b->precision, st, its, rel, outer,
-                              b->own_launches, err);
+                              b->own_launches, b->loops32, b->loops64, err);
   if (rs != FH_OK) {
     b->err = err;
     return rs;
@@ -583,6 +560,8 @@ void release_loads_group(void* cache) {
   Group* g = static_cast<Group*>(cache);
   if (!g) return;
   if (g->st) cudaStreamSynchronize(g->st);
+  g->loops32.clear();
+  g->loops64.clear();
   if (g->p32) {
     g->p32->release();
     delete g->p32;
@@ -653,7 +632,7 @@ int solve_all_loads(const Problem& pb, int precision, double tol, int method, in
   const long long l0 = g->p64->launches + (g->p32 ? g->p32->launches : 0);
   fh_status rs = solve_groups(groups, d, d, Ev, tol, method, max_iter,
                               precision == FH_FP64 ? FH_FP64 : FH_FP32_REFINED, st, its, rel, res.outer,
-                              own, err);
+                              own, g->loops32, g->loops64, err);
   if (rs != FH_OK) return rs;
   std::vector<double> col(d);
   for (int l = 0; l < d; ++l) {

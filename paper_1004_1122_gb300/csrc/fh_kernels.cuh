@@ -1452,6 +1452,19 @@ static __global__ void k_reduce_items(const double* part, int np, int ncell, int
 
 inline int item_blocks(int items) { return items; }
 
+// Condition of a device-side iteration loop (a while node of a CUDA graph):
+// one more body of iterations while an item is running and fewer than
+// loop[1] bodies have run (loop[0] counts them).  One CTA; every loop ends.
+static __global__ void k_loop_cond(cudaGraphConditionalHandle h, const Scal* scal, int items, int* loop) {
+  int run = 0;
+  for (int i = threadIdx.x; i < items; i += blockDim.x) run |= scal[i].done == kRunning;
+  run = __syncthreads_or(run);
+  if (threadIdx.x == 0) {
+    const int rounds = ++loop[0];
+    cudaGraphSetConditional(h, (run && rounds < loop[1]) ? 1u : 0u);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // misc elementwise kernels
 // ----------------------------------------------------------------------------

@@ -1,11 +1,12 @@
 // fh_pipeline.cuh -- per-precision pass pipeline: plans, tilings, device
-// buffers, kernel launches, and the Krylov solvers driven from the host in
-// graph-captured chunks of iterations.
+// buffers, kernel launches, and the Krylov solvers, whose iterations run on
+// the device in one graph launch (a while node over chunks of iterations).
 //
 // Pipeline<T> is explicitly instantiated for float and double in
 // fh_pipeline_f32.cu / fh_pipeline_f64.cu.
 #pragma once
 
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <string>
@@ -63,6 +64,25 @@ struct SolveResult {
   double alpha = 0.0;
 };
 
+// A number unique to each initialised pipeline in the process (graph caches
+// key on it: a pipeline rebuilt in place gets a new one).
+inline unsigned long long next_pipeline_uid() {
+  static std::atomic<unsigned long long> n{0};
+  return ++n;
+}
+
+// Instantiated graphs of device-side iteration loops (run_loops), keyed by
+// the pipelines, method and chunk they were captured for.
+struct LoopCache {
+  std::map<std::string, cudaGraphExec_t> exec;
+  std::map<std::string, std::vector<long long>> kernels;  // kernels per loop body, per pipeline
+  void clear() {
+    for (auto& kv : exec) cudaGraphExecDestroy(kv.second);
+    exec.clear();
+    kernels.clear();
+  }
+};
+
 template <typename T>
 struct Pipeline {
   using C = cplx<T>;
@@ -118,16 +138,15 @@ struct Pipeline {
   double* eta_bufs[2] = {};    // allocations behind hist_eta_e / hist_eta_r
   cudaStream_t st = nullptr;
   std::vector<void*> allocs;
-  std::map<int, cudaGraphExec_t> graphs;  // key: method * 1024 + chunk
   Launch vec{};
   LaunchTable<T> lt{};
   int sms = 0;
   bool rhs_active_ = false;
   long long launches = 0;                    // kernels enqueued (graph replays included)
-  std::map<int, long long> graph_kernels;    // kernels per captured chunk
 
   Tuning tuning{};   // the shape actually in use
   int ct_plan = 0;   // compile-time plan length of the CG-iteration passes (0: run-time plans)
+  unsigned long long uid = 0;  // next_pipeline_uid() of the last init
   int init(const Problem& pb, int nloads_, bool krylov, cudaStream_t stream, std::string& err,
            const Tuning* want = nullptr);
   // Time the CG-iteration pass kernels for candidate tunings (temporary
@@ -158,21 +177,27 @@ struct Pipeline {
             double tol, int max_iter, SolveResult* res, std::string& err,
             const double* tol_item = nullptr, int stall_window = 0);
   // The same solve in pieces, for drivers that run several pipelines at once:
-  // solve_begin (asynchronous set-up), then repeatedly solve_step (one graph
-  // chunk + async copy of the scalars), a stream synchronisation and
-  // solve_done; finally solve_results.
+  // solve_begin (asynchronous set-up), then run_loops over the pipelines (all
+  // iterations on the device, one graph launch), solve_done and
+  // solve_results.
   int solve_begin(int method, const double (*E)[kMaxD], bool rhs_field, int x0,
                   const T* const* x_init, double tol, int max_iter, std::string& err,
                   const double* tol_item = nullptr, int stall_window = 0);
-  int solve_step(std::string& err);
   bool solve_done() const;
   void solve_results(SolveResult* res) const;
   int run_method_ = 0, run_K_ = 8;
-  long long run_guard_ = 0, run_guard_max_ = 0;
+  long long run_guard_max_ = 0;
+  int* d_loop = nullptr;     // device [2]: rounds run by the device-side loop, round limit
+  int* h_loop = nullptr;     // pinned host mirror
+  LoopCache loops;           // this pipeline's own device-side loop graphs (solve)
+  // Capture `K` iterations of `method` followed by the loop condition into
+  // `body`, the body graph of a while node with handle h (on this pipeline's
+  // stream).  *kernels receives the kernels one body launches.
+  cudaError_t capture_loop_body(cudaGraph_t body, cudaGraphConditionalHandle h, int method, int K,
+                                long long* kernels);
   cudaError_t enqueue_iter(int method);
   // eta_e (Eq. errE_def) of the current iterate x[0] into hist_eta_e[iter]
   cudaError_t enqueue_eta_record();
-  cudaError_t enqueue_chunk(int method, int K);
   int chunk_size(int method) const;
 
   // ---- reductions ---------------------------------------------------------
@@ -204,7 +229,21 @@ struct Pipeline {
 // fh_info.ct_plans bit of a compile-time plan length (FH_CT_2187, FH_CT_729, FH_CT_243).
 inline int ct_plan_bit(int n) { return n == 2187 ? 1 : n == 729 ? 2 : n == 243 ? 4 : 0; }
 
+// Runs the iteration loops of np pipelines, each prepared by solve_begin, in
+// ONE graph launch on `launch`: a CUDA graph with one while node per
+// pipeline, whose body is K iterations and a condition kernel; a body runs
+// again while an item of its pipeline is running and its round guard
+// (max_iter / K + 4 rounds) has not run out, so every loop ends.  Waits for
+// the pipelines' streams before the launch and makes them wait for it after;
+// synchronises `launch` and refreshes each pipeline's host scalars and error
+// word.  Returns 0, 5 (FH_ERR_CUDA) or 8 (FH_ERR_TIMEOUT: a bounded device
+// wait expired).
+template <typename T>
+int run_loops(Pipeline<T>* const* ps, int np, cudaStream_t launch, LoopCache& cache, std::string& err);
+
 extern template struct Pipeline<float>;
 extern template struct Pipeline<double>;
+extern template int run_loops<float>(Pipeline<float>* const*, int, cudaStream_t, LoopCache&, std::string&);
+extern template int run_loops<double>(Pipeline<double>* const*, int, cudaStream_t, LoopCache&, std::string&);
 
 }  // namespace fh

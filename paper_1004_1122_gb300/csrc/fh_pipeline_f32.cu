@@ -3,4 +3,5 @@
 
 namespace fh {
 template struct Pipeline<float>;
+template int run_loops<float>(Pipeline<float>* const*, int, cudaStream_t, LoopCache&, std::string&);
 }  // namespace fh

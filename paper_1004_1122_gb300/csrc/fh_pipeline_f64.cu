@@ -3,4 +3,5 @@
 
 namespace fh {
 template struct Pipeline<double>;
+template int run_loops<double>(Pipeline<double>* const*, int, cudaStream_t, LoopCache&, std::string&);
 }  // namespace fh

@@ -46,6 +46,7 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
                       std::string& err, const Tuning* want) {
   Tuning w;
   if (want) w = *want;
+  uid = next_pipeline_uid();
   st = stream;
   nloads = nloads_;
   const bool f64 = sizeof(T) == 8;
@@ -317,6 +318,8 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
     FH_CKS(cudaMemcpy(ltab64, pb.L.data(), (size_t)nphase * d * d * ncell * sizeof(double),
                       cudaMemcpyHostToDevice));
   }
+  if ((rc = dev_alloc(allocs, &d_loop, 2, err))) return rc;
+  FH_CKS(cudaMallocHost(&h_loop, 2 * sizeof(int)));
   if ((rc = dev_alloc(allocs, &dev_err, 1, err))) return rc;
   FH_CKS(cudaMemset(dev_err, 0, sizeof(int)));
   FH_CKS(cudaMallocHost(&h_err, sizeof(int)));
@@ -348,16 +351,17 @@ int Pipeline<T>::init(const Problem& pb, int nloads_, bool krylov, cudaStream_t 
 
 template <typename T>
 void Pipeline<T>::release() {
-  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
-  graphs.clear();
   for (void* q : allocs) cudaFree(q);
   allocs.clear();
   if (h_scal) cudaFreeHost(h_scal);
   if (h_red) cudaFreeHost(h_red);
   if (h_err) cudaFreeHost(h_err);
+  if (h_loop) cudaFreeHost(h_loop);
+  loops.clear();
   h_scal = nullptr;
   h_red = nullptr;
   h_err = nullptr;
+  h_loop = nullptr;
 }
 
 template <typename T>
@@ -569,31 +573,6 @@ cudaError_t Pipeline<T>::enqueue_eta_record() {
 }
 
 template <typename T>
-cudaError_t Pipeline<T>::enqueue_chunk(int method, int K) {
-  const int key = ((method * 2 + (rhs_active_ ? 1 : 0)) * 2 + (hist_eta_e || hist_eta_r ? 1 : 0)) * 4096 + K;
-  auto it = graphs.find(key);
-  if (it == graphs.end()) {
-    cudaGraph_t graph;
-    const long long before = launches;
-    FH_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < K && e == cudaSuccess; ++k) e = enqueue_iter(method);
-    cudaError_t e2 = cudaStreamEndCapture(st, &graph);
-    graph_kernels[key] = launches - before;
-    launches = before;
-    if (e != cudaSuccess) return e;
-    if (e2 != cudaSuccess) return e2;
-    cudaGraphExec_t exec;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    FH_CK(e);
-    it = graphs.emplace(key, exec).first;
-  }
-  launches += graph_kernels[key];
-  return cudaGraphLaunch(it->second, st);
-}
-
-template <typename T>
 int Pipeline<T>::norm2(T* const* v, double* out, std::string& err) {
   const Mat3 I = {{1, 0, 0, 0, 1, 0, 0, 0, 1}};
   for (int l = 0; l < nloads; ++l) {
@@ -721,29 +700,115 @@ int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int
                        std::string& err, const double* tol_item, int stall_window) {
   int rc = solve_begin(method, E, rhs_field, x0, x_init, tol, max_iter, err, tol_item, stall_window);
   if (rc) return rc;
-  while (true) {
-    rc = solve_step(err);
-    if (rc) return rc;
-    FH_CKS(cudaStreamSynchronize(st));
-    if (device_error()) {
-      err = "a bounded device wait expired";
-      return 8;  // FH_ERR_TIMEOUT
-    }
-    if (solve_done()) break;
-    if (++run_guard_ > run_guard_max_) {
-      err = "iteration guard exceeded without a device status";
-      return 6;  // FH_ERR_NOT_CONVERGED: a host-side overrun, not an expired device wait
-    }
+  // every iteration runs on the device: one graph launch whose while node
+  // repeats chunks of iterations until the items stop or the guard runs out
+  Pipeline<T>* self = this;
+  rc = run_loops<T>(&self, 1, st, loops, err);
+  if (rc) return rc;
+  if (!solve_done()) {
+    err = "iteration guard exceeded without a device status";
+    return 6;  // FH_ERR_NOT_CONVERGED: the round guard, not an expired device wait
   }
   solve_results(res);
   return 0;
 }
 
 template <typename T>
-int Pipeline<T>::solve_step(std::string& err) {
-  FH_CKS(enqueue_chunk(run_method_, run_K_));
-  FH_CKS(cudaMemcpyAsync(h_scal, scal, items * sizeof(Scal), cudaMemcpyDeviceToHost, st));
-  FH_CKS(cudaMemcpyAsync(h_err, dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+cudaError_t Pipeline<T>::capture_loop_body(cudaGraph_t body, cudaGraphConditionalHandle h, int method, int K,
+                                           long long* kernels) {
+  const long long before = launches;
+  FH_CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < K && e == cudaSuccess; ++k) e = enqueue_iter(method);
+  if (e == cudaSuccess) {
+    ++launches;
+    k_loop_cond<<<1, 128, 0, st>>>(h, scal, items, d_loop);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &out);
+  *kernels = launches - before;
+  launches = before;
+  return e != cudaSuccess ? e : e2;
+}
+
+template <typename T>
+int run_loops(Pipeline<T>* const* ps, int np, cudaStream_t launch, LoopCache& cache, std::string& err) {
+  std::string key;
+  for (int i = 0; i < np; ++i) {
+    const Pipeline<T>& P = *ps[i];
+    key += std::to_string(P.uid) + ":" + std::to_string(P.run_method_) + ":" +
+           std::to_string(P.run_K_) + ":" + (P.rhs_active_ ? "r" : "c") +
+           (P.hist_eta_e || P.hist_eta_r ? "h" : "-") + ";";
+  }
+  auto it = cache.exec.find(key);
+  if (it == cache.exec.end()) {
+    cudaGraph_t g = nullptr;
+    FH_CKS(cudaGraphCreate(&g, 0));
+    std::vector<long long> kern(np, 0);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+      cudaGraphConditionalHandle h;
+      e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+      if (e != cudaSuccess) break;
+      cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+      if (e != cudaSuccess) break;
+      e = ps[i]->capture_loop_body(cp.conditional.phGraph_out[0], h, ps[i]->run_method_, ps[i]->run_K_, &kern[i]);
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      err = std::string("device-side iteration loop: ") + cudaGetErrorString(e);
+      return 5;
+    }
+    it = cache.exec.emplace(key, exec).first;
+    cache.kernels[key] = kern;
+  }
+  // round guard per pipeline, then start after every pipeline's preparation
+  std::vector<cudaEvent_t> evs;
+  auto cleanup = [&]() {
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+  };
+  for (int i = 0; i < np; ++i) {
+    Pipeline<T>& P = *ps[i];
+    P.h_loop[0] = 0;
+    P.h_loop[1] = (int)std::min<long long>(P.run_guard_max_, 1 << 30);
+    FH_CKS(cudaMemcpyAsync(P.d_loop, P.h_loop, 2 * sizeof(int), cudaMemcpyHostToDevice, P.st));
+    if (P.st != launch) {
+      cudaEvent_t ev;
+      FH_CKS(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      evs.push_back(ev);
+      FH_CKS(cudaEventRecord(ev, P.st));
+      FH_CKS(cudaStreamWaitEvent(launch, ev, 0));
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(it->second, launch);
+  for (int i = 0; i < np && e == cudaSuccess; ++i) {
+    Pipeline<T>& P = *ps[i];
+    e = cudaMemcpyAsync(P.h_scal, P.scal, P.items * sizeof(Scal), cudaMemcpyDeviceToHost, launch);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.h_err, P.dev_err, sizeof(int), cudaMemcpyDeviceToHost, launch);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.h_loop, P.d_loop, 2 * sizeof(int), cudaMemcpyDeviceToHost, launch);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(launch);
+  cleanup();
+  if (e != cudaSuccess) {
+    err = std::string("device-side iteration loop: ") + cudaGetErrorString(e);
+    return 5;
+  }
+  const std::vector<long long>& kern = cache.kernels[key];
+  for (int i = 0; i < np; ++i) {
+    ps[i]->launches += (long long)ps[i]->h_loop[0] * kern[i];
+    if (ps[i]->device_error()) {
+      err = "a bounded device wait expired";
+      return 8;
+    }
+  }
   return 0;
 }
 
@@ -865,7 +930,6 @@ int Pipeline<T>::solve_begin(int method, const double (*E)[kMaxD], bool rhs_fiel
   if (hist_eta_e != nullptr && items == 1) FH_CKS(enqueue_eta_record());  // iterate 0
   run_method_ = method;
   run_K_ = chunk_size(method);
-  run_guard_ = 0;
   run_guard_max_ = (long long)max_iter / run_K_ + 4;
   return 0;
 }
