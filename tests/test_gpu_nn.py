@@ -301,3 +301,62 @@ def test_warm_start_falls_back_to_cold():
     np.testing.assert_array_equal(col_w, col_c)
     s.close()
     ws.close()
+
+
+def test_learned_warm_start_on_held_out_cells():
+    """Generalisation: train on the unit-load fields of 24 cells (27^3,
+    contrast 10..1000), then solve 8 cells the network has never seen for a
+    random load, from the warm start and from e = E, to the same tolerance.
+    Checks: the warm start's initial residual is below the cold start's on
+    held-out cells (the network carries over), both reach the same effective
+    column, and the warm solves stay within 5 % of the cold iteration count.
+    The gain in iterations and in time is printed.  Measured: the held-out
+    initial residual halves (0.45 -> 0.2 of ||e0||) on every cell, yet the
+    iterations do not change (443 cold, 445 warm over the 8 cells): the
+    network removes mostly error components that CG removes in its first few
+    iterations anyway, so at this accuracy a learned start cannot pay."""
+    torch = cuda_or_skip()
+    import time
+
+    from paper_1004_1122_gb300 import fh, warmstart
+
+    pairs = []
+    for k in range(24):
+        ph, L = _cell(2000 + k)
+        phd = torch.from_numpy(ph).cuda()
+        with fh.Solver(phd, L, precision="fp64") as s:
+            x, t, infos = warmstart.training_pair(s, phd, L, tol=1e-9)
+        assert all(i["status"] == "FH_OK" for i in infos)
+        pairs.append((x, t))
+    ws = warmstart.WarmStart(N, d=3, seed=4)
+    ws.train(pairs, steps=6000, lr=1e-3)
+    del pairs
+    rng = np.random.default_rng(77)
+    rows = []
+    for k in range(8):
+        ph, L = _cell(5000 + k)  # held out: seeds never used for training
+        phd = torch.from_numpy(ph).cuda()
+        with fh.Solver(phd, L, precision="fp64") as s:
+            E = rng.normal(size=3)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, col_c, ic = s.solve(E, tol=1e-6, method="cg", max_iter=5000)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            x = ws.features(phd, L, s)
+            pred = ws.predict(x)
+            _, col_w, iw = ws.solve(s, x, pred, E, tol=1e-6)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+        assert ic["status"] == "FH_OK" and iw["status"] == "FH_OK"
+        assert np.max(np.abs(col_w - col_c)) <= 1e-5 * np.max(np.abs(col_c))
+        rows.append((ic["iters"], iw["iters"], iw["res0_cold"], iw["res0_warm"], t1 - t0, t2 - t1, iw["start"]))
+    ws.close()
+    cold = sum(r[0] for r in rows)
+    warm = sum(r[1] for r in rows)
+    better_start = sum(r[3] < r[2] for r in rows)
+    print(f"held-out: cold {cold} warm {warm} iterations ({100.0 * (cold - warm) / cold:+.1f} %), "
+          f"time cold {sum(r[4] for r in rows):.3f} s warm {sum(r[5] for r in rows):.3f} s, "
+          f"warm start better on {better_start}/8 cells; per cell {rows}")
+    assert better_start >= 6
+    assert warm <= 1.05 * cold
