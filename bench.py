@@ -9,12 +9,16 @@ Workload (2-D scalar conductivity, the paper's method at scale):
 
 One step = the 8 solves (4 contrasts x 2 loads) with CG, float32 inner
 iterations and float64 refinement, each to a float64 TRUE relative residual
-<= 1e-6, returning the 2 x 2 effective tensor per contrast.  Inputs (phase
-image, tables) are resident in HBM before timing; the working set (4 contexts,
-~1.4 GB) is far larger than L2, so no explicit flush is needed.
+<= 1e-6, returning the 2 x 2 effective tensor per contrast.  The 8 solves are
+independent: each has its own context and CUDA stream and is driven by its own
+host thread, so they run concurrently on the GPU.  Inputs (phase image,
+tables) are resident in HBM before timing; the working set (8 contexts, ~3 GB)
+is far larger than L2, so no explicit flush is needed.
 
-value  = device time per solve (ms, CUDA events on the solver stream, max over
-         ranks, divided by every solve of every rank).
+value  = device time per solve: the step's time (CUDA events on a master
+         stream that every context stream waits for, max over ranks) divided
+         by every solve of every rank.  latency_sequential repeats the step
+         with the solves one after another.
 e2e    = the same through the public API with host buffers: every step copies
          the phase image from pinned host memory and reads every solved field
          (float64) back into pinned host memory.
@@ -33,6 +37,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -455,29 +460,70 @@ def run_fh(args):
     from paper_1004_1122_gb300 import fh
 
     phase, tables = make_inputs()
-    stream = torch.cuda.Stream()
-    first = fh.Solver(phase, tables[0], precision="fp32_refined", stream=stream)
+    # One context per (contrast, load) on its own stream: the 8 independent
+    # solves of a step run concurrently, one host thread each (a context is
+    # used by one thread at a time), as a serving loop would run them.
+    first = fh.Solver(phase, tables[0], precision="fp32_refined", stream=torch.cuda.Stream())
     tune = None
     if not args.no_tune:
         before, after = first.autotune("fp32")
         tune = {"ms_per_iter_before": before, "ms_per_iter_after": after,
                 "cache": os.environ.get("FH_TUNE_CACHE")}
-    solvers = [first] + [fh.Solver(phase, L, precision="fp32_refined", stream=stream) for L in tables[1:]]
-    nsolve = len(solvers) * len(LOADS)
+    units = [(first, 0, LOADS[0])]
+    for i, L in enumerate(tables):
+        for j, E in enumerate(LOADS):
+            if (i, j) != (0, 0):
+                units.append((fh.Solver(phase, L, precision="fp32_refined", stream=torch.cuda.Stream()), i, E))
+    nsolve = len(units)
+    master = torch.cuda.Stream()
 
-    def step(collect=None):
-        leff = []
-        for s in solvers:
-            cols = []
-            for E in LOADS:
-                _, col, info = s.solve(E, tol=TOL, method="cg", max_iter=MAX_ITER, want_field=False)
-                if info["status"] != "FH_OK":
-                    raise RuntimeError(f"solve failed: {info}")
-                cols.append(col)
-                if collect is not None:
-                    collect.append(info)
-            leff.append(np.stack(cols, axis=1))
-        return leff
+    def run_units(work, concurrent):
+        """Run work(unit) for every unit, on concurrent host threads or one by
+        one; returns the device time (ms, CUDA events on the master stream,
+        which waits for every unit's stream) and the results in unit order."""
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(master)
+        for u in units:
+            u[0].stream.wait_event(ev0)
+        res = [None] * nsolve
+        errs = []
+
+        def one(k):
+            try:
+                res[k] = work(units[k])
+            except Exception as exc:  # reported after the join
+                errs.append(exc)
+
+        if concurrent:
+            ths = [threading.Thread(target=one, args=(k,)) for k in range(nsolve)]
+            for t in ths:
+                t.start()
+            for t in ths:
+                t.join()
+        else:
+            for k in range(nsolve):
+                one(k)
+        if errs:
+            raise errs[0]
+        for u in units:
+            e = torch.cuda.Event()
+            e.record(u[0].stream)
+            master.wait_event(e)
+        ev1.record(master)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1), res
+
+    def solve_unit(u):
+        s, _, E = u
+        _, col, info = s.solve(E, tol=TOL, method="cg", max_iter=MAX_ITER, want_field=False)
+        if info["status"] != "FH_OK":
+            raise RuntimeError(f"solve failed: {info}")
+        return col, info
+
+    def step(concurrent=True):
+        t, res = run_units(solve_unit, concurrent)
+        leff = [np.stack([res[2 * i + j][0] for j in range(len(LOADS))], axis=1) for i in range(len(tables))]
+        return t, leff, [r[1] for r in res]
 
     for _ in range(args.warmup):
         step()
@@ -487,15 +533,14 @@ def run_fh(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    t_ms = 0.0
     for _ in range(args.steps):
-        leff = step(infos)
-    ev1.record(stream)
-    ev1.synchronize()
+        t, leff, inf = step()
+        t_ms += t
+        infos += inf
     torch.cuda.synchronize()
     clk = clocks.stop()
-    t_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    t_ms = max_over_ranks(t_ms, world)
     if world > 1:
         dist.barrier()
     ms_per_step = t_ms / args.steps
@@ -504,31 +549,41 @@ def run_fh(args):
     iters = [i["iters"] for i in infos[:nsolve]]
     outer = [i["outer_iters"] for i in infos[:nsolve]]
     rel_true = max(i["rel_res_true"] for i in infos)
+    # the same step with the 8 solves one after another: the latency of one solve
+    t_seq = sum(step(concurrent=False)[0] for _ in range(2)) / 2
+    latency = {"ms_per_solve": t_seq / nsolve, "ms_per_step": t_seq,
+               "what": "the 8 solves of a step one after another (same contexts)"}
 
     # ---- e2e through the public API with host buffers ----------------------
     ph_pin = torch.from_numpy(phase).pin_memory()
-    out_dev = torch.empty((2, N, N), dtype=torch.float64, device="cuda")
-    out_host = torch.empty((2, N, N), dtype=torch.float64).pin_memory()
-    h2d = d2h = 0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
+    outs = [(torch.empty((2, N, N), dtype=torch.float64, device="cuda"),
+             torch.empty((2, N, N), dtype=torch.float64).pin_memory()) for _ in units]
+    bytes_moved = {"h2d": 0, "d2h": 0}
+    lock = threading.Lock()
+
+    def e2e_unit(u):
+        s, _, E = u
+        k = next(i for i, v in enumerate(units) if v[0] is s)
+        out_dev, out_host = outs[k]
+        s.set_phase(ph_pin.numpy())
+        s.solve(E, tol=TOL, method="cg", max_iter=MAX_ITER, out=out_dev)
+        with torch.cuda.stream(s.stream):
+            out_host.copy_(out_dev, non_blocking=True)
+        with lock:
+            bytes_moved["h2d"] += ph_pin.numel()
+            bytes_moved["d2h"] += out_host.numel() * 8 + 16
+        return None
+
+    e2e_ms = 0.0
     for _ in range(args.steps):
-        for s in solvers:
-            s.set_phase(ph_pin.numpy())
-            h2d += ph_pin.numel()
-            for E in LOADS:
-                s.solve(E, tol=TOL, method="cg", max_iter=MAX_ITER, out=out_dev)
-                with torch.cuda.stream(stream):
-                    out_host.copy_(out_dev, non_blocking=True)
-                d2h += out_host.numel() * 8 + 16
-    e1.record(stream)
-    e1.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        e2e_ms += run_units(e2e_unit, True)[0]
+    e2e_ms = max_over_ranks(e2e_ms, world)
     e2e_value = replica_value(e2e_ms, args.steps, nsolve, world)
+    h2d, d2h = bytes_moved["h2d"], bytes_moved["d2h"]
+    solvers = [u[0] for u in units]
 
     # ---- matvec and per-kernel roofline (float32 pipeline, rho = 1e2 context)
-    prof = solvers[1]
+    prof = solvers[2]  # rho = 1e2, E = (1, 0)
     s4, d = 4, 2
     nodes = N * N
     spec = spectrum_bytes(N, N, d, s4)
@@ -619,7 +674,11 @@ def run_fh(args):
             "dtype": "f32 (f64 refinement)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "solves_per_step": nsolve,
-                       "l2": "no flush: working set (4 contexts, ~1.4 GB) > L2"},
+                       "schedule": "the 8 independent solves of a step on 8 contexts and streams, one host "
+                                   "thread each (value = step time / 8: throughput); latency_sequential "
+                                   "holds the same step run one solve after another",
+                       "l2": "no flush: working set (8 contexts, ~3 GB) > L2"},
+            "latency_sequential": latency,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "ms/solve", "h2d_bytes_per_step": h2d // args.steps,
                     "d2h_bytes_per_step": d2h // args.steps},
