@@ -77,6 +77,8 @@ def parse():
                          "(for profiler captures)")
     ap.add_argument("--probe", action="store_true",
                     help="only time each pass kernel a few times (small command for ncu captures)")
+    ap.add_argument("--probe-3d", action="store_true",
+                    help="only time each 3-D pass kernel a few times at 243^3 (small command for ncu captures)")
     ap.add_argument("--probe-residual", action="store_true",
                     help="one refined 729^2 solve, whose two float64 residuals run the double-float "
                          "passes (small command for ncu captures)")
@@ -865,6 +867,19 @@ def run_c3(args):
     ev1.synchronize()
     clk = clocks.stop()
     t_ms = ev0.elapsed_time(ev1)
+    # roofline of the 3-D float32 CG-iteration passes (the context's one-load
+    # pipeline, the 243-point compile-time plan): algorithmic bytes per launch
+    n3 = 243 ** 3
+    d3, s4 = 3, 4
+    spec3 = 2 * s4 * d3 * ((243 + 1) // 2) * 243 * 243
+    kern3 = {"row_fwd": (0, (3 * d3 * s4 + 1) * n3 + spec3),
+             "col_mid_green_mid": (1, 6 * spec3),  # middle-axis forward, Green pass, middle-axis inverse
+             "row_inv": (2, spec3 + 2 * d3 * s4 * n3),
+             "cg_update": (3, 6 * d3 * s4 * n3)}
+    times3 = {k: s.profile(w, reps=20) for k, (w, _) in kern3.items()}
+    peak, peak_src = load_peaks()
+    dom3 = max(times3, key=lambda k: times3[k])
+    ach3 = kern3[dom3][1] / (times3[dom3] * 1e-3) / 1e9
     s.close()
     line = {
         "metric": "3-D full effective tensor: time per load solve to true rel.res 1e-6 (3 loads per launch)",
@@ -878,7 +893,12 @@ def run_c3(args):
         "gpu_launches": sum(i["launches"] for i in infos[:1]) * args.steps,
         "solver": {"iters": [i["iters"] for i in infos], "outer_iters": infos[0]["outer_iters"],
                    "rel_res_true": [i["rel_res_true"] for i in infos], "status": [i["status"] for i in infos],
-                   "L_eff": Le.tolist()},
+                   "L_eff": Le.tolist(), "ct_plans": infos[0]["ct_plans"]},
+        "roofline": {"bound": "hbm", "achieved": ach3, "peak": peak, "unit": "GB/s", "frac": ach3 / peak,
+                     "traffic": None, "kernel": dom3, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": kern3[dom3][1], "ms_per_launch": times3[dom3],
+                     "note": "one-load float32 pipeline of the same context (fh_profile)"},
+        "kernels_ms": times3,
     }
     print(json.dumps(line), flush=True)
 
@@ -955,6 +975,34 @@ def run_x1(args):
             rows.append(row)
     sweep_s = time.perf_counter() - t_all
 
+    # convergence progress (Fig. example3): eta_r and eta_e of every iterate
+    # of CG and FFTH at omega = 0.5 for rho = 1e1 and 1e3, with the rate
+    # bounds of Eq. conv_rate (FFTH (rho-1)/(rho+1), CG (sqrt(rho)-1)/(sqrt(rho)+1))
+    progress = {}
+    for rho in (1e1, 1e3):
+        L = micro.isotropic_table([1.0, rho], 2)
+        l0 = 0.5 * (1.0 + rho)
+        with fh.Solver(phase, L, L0=l0 * np.eye(2), precision="fp64") as s:
+            entry = {}
+            for method, tol in (("cg", 1e-10 / l0), ("fixed_point", X1_EPS / l0)):
+                cap = 200000
+                _, _, info = s.solve(E, tol=tol, method=method, max_iter=cap, history=cap + 2, norms=True)
+                er, ee = info["eta_r_history"], info["eta_e_history"]
+                idx = np.unique(np.round(np.geomspace(1, max(len(er), 1), 120)).astype(int) - 1)
+                entry[method] = {"m": idx.tolist(), "eta_r": er[idx].tolist(),
+                                 "eta_e": ee[np.minimum(idx + 1, len(ee) - 1)].tolist(), "iters": info["iters"]}
+            g_f = (rho - 1.0) / (rho + 1.0)
+            g_c = (np.sqrt(rho) - 1.0) / (np.sqrt(rho) + 1.0)
+            entry["rate_bounds"] = {"ffth": g_f, "cg": g_c}
+            # measured mean rate of eta_r over the steps, against the bound
+            for method, g in (("cg", g_c), ("fixed_point", g_f)):
+                er = entry[method]["eta_r"]
+                m = entry[method]["m"]
+                if len(er) > 1 and er[0] > 0 and er[-1] > 0 and m[-1] > m[0]:
+                    entry[method]["mean_rate"] = float((er[-1] / er[0]) ** (1.0 / (m[-1] - m[0])))
+                entry[method]["bound"] = g
+            progress[f"rho_{rho:g}"] = entry
+
     # cost per iteration (no norm histories): 255^2 float64 and 2187^2 float32
     def per_iter(solver, method, tol, cap):
         solver.solve(E, tol=tol, method=method, max_iter=cap, want_field=False)  # warm-up (graph capture)
@@ -990,6 +1038,7 @@ def run_x1(args):
                                f"stop at eta_r <= {X1_EPS:g}"},
         "clocks": clk,
         "sweep": rows,
+        "convergence_progress": progress,
         "cost_per_iteration": cost,
         "paper": {"cg_rel_iters": "50 % (mild contrast) to 2 % (rho = 1e4)", "cg_per_iter_over_ffth": 1.1,
                   "bicg_per_iter_over_ffth": 2.0},
@@ -1148,6 +1197,31 @@ def run_probe_nn():
     net.close()
 
 
+def run_probe_3d():
+    """A few launches of every 3-D pass kernel of the float32 CG iteration at
+    243^3 (the C3 spheres, rho = 1e3), with a 512 MiB buffer written before each
+    kernel's launches (cold L2), for profiler captures."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1004_1122_gb300 import fh
+    from paper_1004_1122_gb300 import microstructure as micro
+
+    phase = micro.boolean_spheres(243, 12.0, 0.25, seed=micro.config_seed(3))
+    L = micro.isotropic_table([1.0, 1e3], 3)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    with fh.Solver(phase, L, precision="fp32") as s:
+        for name, w in (("row_fwd", 0), ("cols", 1), ("row_inv", 2), ("cg_update", 3)):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            out[name] = s.profile(w, reps=3)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe_3d_ms": out}))
+
+
 def run_probe_residual():
     from paper_1004_1122_gb300 import fh
     from paper_1004_1122_gb300 import microstructure as micro
@@ -1168,6 +1242,9 @@ def main():
         return
     if args.probe_nn:
         run_probe_nn()
+        return
+    if args.probe_3d:
+        run_probe_3d()
         return
     if args.workload == "c5" and args.impl != "reference":
         run_c5(args)
