@@ -589,7 +589,11 @@ __device__ __forceinline__ void green_tile(const ColArgs<T>& a, cplx<T>* sm, int
   }
 }
 
-template <typename T, int D, int CM_, typename PS = DynPlan>
+// QC, TC > 0: the tile's column count Q and the threads per column FFT are
+// compile-time constants (they must equal a.b.Q and a.b.tpc); the column
+// stride and the thread-to-butterfly mapping then fold into immediate
+// offsets instead of run-time index arithmetic.
+template <typename T, int D, int CM_, typename PS = DynPlan, int QC = 0, int TC = 0>
 __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks) k_col(ColArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -597,7 +601,8 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
   const ColArgsBase& b = a.b;
   const Geom& g = b.g;
   constexpr int d = D;
-  const int n = b.plan.n, Q = b.Q;
+  const int n = b.plan.n, Q = QC ? QC : b.Q;
+  const int tpc = TC ? TC : b.tpc;
   const int blk_outer = blockIdx.x / b.nb_inner;
   const int blk_inner = blockIdx.x - blk_outer * b.nb_inner;
   // 2-D batches: the inner block index is the cell
@@ -651,7 +656,7 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
 
   const int q = threadIdx.x % Q;
   const int u0 = threadIdx.x / Q;
-  const int u = u0 < b.tpc ? u0 : n;
+  const int u = u0 < tpc ? u0 : n;
   if constexpr (CM_ == kColGreen && D == 2) {
     // 2-D: the Green projection runs in registers between the forward and
     // inverse FFTs.  Q = C * M is even and the two components of a frequency
@@ -660,12 +665,12 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
     const double* L0src = a.L0cell ? a.L0cell + 9 * cell : g.L0;
     GreenPoint2<T> gp;
     gp.init(g, L0src, t, q, n);
-    fft_fused_plan<T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw, gp);
+    fft_fused_plan<T, PS>(sm + q, Q, b.plan, u, tpc, a.tw, gp);
   } else {
   if (CM_ == kColFwd || CM_ == kColGreen || CM_ == kColEta)
-    fft_plan<false, T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+    fft_plan<false, T, PS>(sm + q, Q, b.plan, u, tpc, a.tw);
   else
-    fft_plan<true, T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+    fft_plan<true, T, PS>(sm + q, Q, b.plan, u, tpc, a.tw);
 
   if (CM_ == kColGreen || CM_ == kColEta) {
     double acc[2] = {0.0, 0.0};

@@ -47,6 +47,12 @@ using CtPlan = typename std::conditional<D == 2, typename std::conditional<NL ==
 template <typename T, int D>
 constexpr bool kHasDf = std::is_same<T, double>::value && D == 2;
 
+// The 2187^2 Green pass also exists with its tuned tile shape compiled in:
+// tiles of 2 frequencies x 2 components (Q = 4 columns), 81 threads per
+// 2187-point column FFT.
+constexpr int kGreenQ = 4;
+constexpr int kGreenT = 81;
+
 template <typename T, int D, int NL>
 struct Launchers {
   static cudaError_t set_smem(size_t rs, size_t c0, size_t c1) {
@@ -56,6 +62,8 @@ struct Launchers {
       if ((e = opt_in_smem(k_row_fwd<T, D, NL, kProDir, P>, rs)) != cudaSuccess) return e;
       if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, P>, rs)) != cudaSuccess) return e;
       if ((e = opt_in_smem(k_col<T, D, kColGreen, P>, c0)) != cudaSuccess) return e;
+      if constexpr (D == 2 && NL == 1)
+        if ((e = opt_in_smem(k_col<T, D, kColGreen, P, kGreenQ, kGreenT>, c0)) != cudaSuccess) return e;
       if constexpr (D == 3) {
         if ((e = opt_in_smem(k_col<T, D, kColFwd, P>, c1)) != cudaSuccess) return e;
         if ((e = opt_in_smem(k_col<T, D, kColInv, P>, c1)) != cudaSuccess) return e;
@@ -186,6 +194,12 @@ struct Launchers {
       using P = CtPlan<D, NL>;
       if (L.block <= ColBounds<P>::threads && cplan_is<P>(a.b.plan)) {
         if (mode == kColGreen) {
+          if constexpr (D == 2 && NL == 1) {
+            if (a.b.Q == kGreenQ && a.b.tpc == kGreenT) {  // the tuned 2187^2 tile shape
+              k_col<T, D, kColGreen, P, kGreenQ, kGreenT><<<L.grid, L.block, L.smem, st>>>(a);
+              return cudaGetLastError();
+            }
+          }
           k_col<T, D, kColGreen, P><<<L.grid, L.block, L.smem, st>>>(a);
           return cudaGetLastError();
         }
