@@ -54,6 +54,34 @@ template <typename PS> struct RowBounds {
 template <> struct RowBounds<Plan2187> {
   static constexpr int threads = kRowCtThreads, blocks = kRowCtBlocks;
 };
+// Row-pass launch shape fixed at compile time: one line per CTA of NT
+// threads, TPL threads per line FFT (0: from the launch arguments), spectrum
+// tiles of CC frequencies.  The loop bounds, the thread-to-butterfly mapping
+// and the tiled-spectrum index then fold into constants.  RowShape<0, 0, 0>
+// takes all of it from the launch arguments.
+template <int NT, int TPL, int CC> struct RowShape {
+  static constexpr int nt = NT, tpl = TPL, cc = CC;
+  static constexpr int csh = CC <= 1 ? 0 : CC <= 2 ? 1 : CC <= 4 ? 2 : CC <= 8 ? 3 : 4;
+  static_assert(CC == 0 || (1 << csh) == CC, "tile width must be a power of two");
+};
+using RowDyn = RowShape<0, 0, 0>;
+// Axis length of a compile-time plan (0 for run-time plans).
+template <typename PS> struct PlanLen {
+  static constexpr int value = PS::n;
+};
+template <> struct PlanLen<DynPlan> {
+  static constexpr int value = 0;
+};
+template <> struct PlanLen<DynPlanX> {
+  static constexpr int value = 0;
+};
+// Axis length of a plan: a constant for compile-time plans.
+template <typename PS> __device__ __forceinline__ int plan_len(const FFTPlan& pl) {
+  if constexpr (std::is_same<PS, DynPlan>::value || std::is_same<PS, DynPlanX>::value)
+    return pl.n;
+  else
+    return PS::n;
+}
 // Green-pass kernels with a compile-time plan: kColCtBlocks resident CTAs of
 // at most kColCtThreads threads (measured on 2187^2: a cap for 2 x 352 threads
 // or 3 x 352 threads is slower than the 80-register cap of 768 threads).
@@ -96,6 +124,11 @@ struct Scal {
   double* hist_eta_r;
   double* hist_eta_e;
   double l0iso;
+  // CG with the x step deferred to every second iteration: alpha_x is the
+  // step length whose update of x is still owed (direction in the first p
+  // buffer) while xpend is 1.
+  double alpha_x;
+  int xpend;
 };
 
 // kStalled: the recursive residual stopped decreasing (the working precision's
@@ -291,16 +324,24 @@ enum : int {
 };
 
 // DF (float64 only): the line FFT runs in double-float arithmetic (line_fft_df).
-template <typename T, int D, int NL, int PRO, typename PS = DynPlan, bool DF = false>
+// RS: compile-time launch shape (RowShape) or RowDyn.
+template <typename T, int D, int NL, int PRO, typename PS = DynPlan, bool DF = false, typename RS = RowDyn>
 __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks) k_row_fwd(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  T* stab = reinterpret_cast<T*>(sm + (size_t)a.nseq * a.plan.n);
   const Geom& g = a.g;
-  const int n = a.plan.n;
   constexpr int d = D, M = D * NL;
-  const int line0 = blockIdx.x * a.lpc;
+  constexpr bool kFix = RS::nt > 0;
+  const int n = plan_len<PS>(a.plan);
+  const int nthr = kFix ? RS::nt : (int)blockDim.x;
+  const int tpl = (kFix && RS::tpl > 0) ? RS::tpl : a.tpl;
+  const int lpc = kFix ? 1 : a.lpc;
+  const int nseq = kFix ? (M + 1) / 2 : a.nseq;
+  const int Cc = kFix ? RS::cc : g.C, csh = kFix ? RS::csh : g.cshift;
+  const int H = kFix ? n / 2 + 1 : g.H;
+  T* stab = reinterpret_cast<T*>(sm + (size_t)nseq * n);
+  const int line0 = blockIdx.x * lpc;
   const int cell = g.ncell > 1 ? line0 / g.lines_cell : 0;
   Scal* const sc = a.scal ? a.scal + cell * NL : nullptr;
   const T* const tabc = a.tab + (size_t)cell * g.tab_stride;
@@ -312,17 +353,19 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
   T lbeta[NL];
   const T* pin[NL];
   T* pout[NL];
+  const T* pold[NL];  // direction modes: the previous p (a.aux when it is kept apart, else read in place)
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
     lact[l] = !kDir || sc[l].done == kRunning;
     lbeta[l] = kDir ? T(sc[l].beta) : T(0);
     pin[l] = a.in[l];
     pout[l] = a.out[l];
+    pold[l] = a.aux[l] ? a.aux[l] : a.out[l];
   }
   // ask L2 for the CTA's input lines before the table load and the barrier:
   // the gather below then waits on L2 rather than on HBM (direction pass on
   // 2187^2: 50.0 -> 47.2 us; the same hint in the A p pass measured slower)
-  for (int ll = 0; ll < a.lpc; ++ll) {
+  for (int ll = 0; ll < lpc; ++ll) {
     const int line = line0 + ll;
     if (line >= g.nlines) break;
     const long long lo = (long long)line * n;
@@ -331,12 +374,12 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         prefetch_range(pin[l] + c * g.nodes + lo, (long long)n * sizeof(T));
-        if (kDir) prefetch_range(pout[l] + c * g.nodes + lo, (long long)n * sizeof(T));
+        if (kDir) prefetch_range(pold[l] + c * g.nodes + lo, (long long)n * sizeof(T));
       }
     if (kUseTab) prefetch_range(a.phase + lo, n);
   }
   if (kUseTab) {
-    for (int i = threadIdx.x; i < a.nphase * d * d; i += blockDim.x) stab[i] = tabc[i];
+    for (int i = threadIdx.x; i < a.nphase * d * d; i += nthr) stab[i] = tabc[i];
   }
   __syncthreads();
 
@@ -345,17 +388,17 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
   // keeps several global loads in flight (the row pass is latency-bound
   // otherwise).
   constexpr int kUnroll = 4;
-  for (int ll = 0; ll < a.lpc; ++ll) {
+  for (int ll = 0; ll < lpc; ++ll) {
     const int line = line0 + ll;
     const bool valid = line < g.nlines;
     const long long lo = (long long)line * n;
-    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * blockDim.x) {
+    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * nthr) {
       T v[kUnroll][NL][D];
       T pv[kUnroll][NL][D];
       int ph[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * blockDim.x;
+        const int i = i0 + u * nthr;
         const bool ok = valid && i < n;
         ph[u] = (kUseTab && ok) ? a.phase[lo + i] : 0;
 #pragma unroll
@@ -363,12 +406,12 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
 #pragma unroll
           for (int c = 0; c < D; ++c) {
             v[u][l][c] = ok ? __ldg(pin[l] + c * g.nodes + lo + i) : T(0);
-            if (kDir) pv[u][l][c] = ok ? pout[l][c * g.nodes + lo + i] : T(0);
+            if (kDir) pv[u][l][c] = ok ? pold[l][c * g.nodes + lo + i] : T(0);
           }
       }
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * blockDim.x;
+        const int i = i0 + u * nthr;
         if (i >= n) continue;
         const bool ok = valid;
 #pragma unroll
@@ -397,38 +440,38 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
     }
   }
   // zero the imaginary half of a trailing unpaired channel
-  if ((a.lpc * M) & 1) {
-    const int s = a.nseq - 1;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sm[(size_t)s * n + i].y = T(0);
+  if ((lpc * M) & 1) {
+    const int s = nseq - 1;
+    for (int i = threadIdx.x; i < n; i += nthr) sm[(size_t)s * n + i].y = T(0);
   }
   __syncthreads();
 
   // 2. forward FFT of every sequence
   if constexpr (DF) {
     static_assert(std::is_same<T, double>::value, "double-float line FFTs are for float64 rows");
-    line_fft_df<false>(sm, a.nseq, n, a.plan, a.tpl, a.twdf);
+    line_fft_df<false>(sm, nseq, n, a.plan, tpl, a.twdf);
   } else {
-    const int s = threadIdx.x / a.tpl;
-    const int u = s < a.nseq ? threadIdx.x - s * a.tpl : n;  // idle threads never touch smem
-    fft_plan<false, T, PS>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
+    const int s = threadIdx.x / tpl;
+    const int u = s < nseq ? threadIdx.x - s * tpl : n;  // idle threads never touch smem
+    fft_plan<false, T, PS>(sm + (size_t)(s < nseq ? s : 0) * n, 1, a.plan, u, tpl, a.tw);
   }
 
   // 3. unpack two real spectra per sequence and store the half spectrum:
   // one thread per (line, frequency kx), all M channels of that frequency
   // (contiguous in the tiled layout) written together.
-  const int TC = g.Tt * g.C;
-  for (int ll = 0; ll < a.lpc; ++ll) {
+  const int TC = kFix ? (H + Cc - 1) / Cc * Cc : g.Tt * g.C;
+  for (int ll = 0; ll < lpc; ++ll) {
     const int line = line0 + ll;
     if (line >= g.nlines) break;
-    for (int kx = threadIdx.x; kx < TC; kx += blockDim.x) {
-      const int t = kx >> g.cshift, c = kx & (g.C - 1);
+    for (int kx = threadIdx.x; kx < TC; kx += nthr) {
+      const int t = kx >> csh, c = kx & (Cc - 1);
       const int kneg = kx == 0 ? 0 : n - kx;
       C val[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) {
         val[m].x = T(0);
         val[m].y = T(0);
-        if (kx < g.H) {
+        if (kx < H) {
           const int gch = ll * M + m;
           const C* seq = sm + (size_t)(gch >> 1) * n;
           const C z1 = seq[kx];
@@ -442,7 +485,7 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
           }
         }
       }
-      C* dst = a.S + (((long long)t * g.nlines + line) * g.C + c) * M;
+      C* dst = a.S + (((long long)t * g.nlines + line) * Cc + c) * M;
       if constexpr (sizeof(C) == 8 && M % 2 == 0) {
         // float32: two complex values per 16-byte store
 #pragma unroll
@@ -466,10 +509,11 @@ enum : int { kColFwd = 0, kColInv = 1, kColGreen = 2, kColEta = 3 };
 // y_a = xi_a (xi . v) / (xi . L0 . xi) / |N| at (k0, k_last), zero at k = 0 and
 // on padded frequencies.  The caller holds component a = q % 2 of the value;
 // the other component comes from the neighbouring lane (q ^ 1).
-template <typename T>
+// NC > 0: the column length n is the compile-time constant NC.
+template <typename T, int NC = 0>
 struct GreenPoint2 {
   T invY0, invY1, L00, L01, L10, L11, inv_nodes, xi1;
-  int n, a;
+  int n_rt, a;
   bool pad, kl0;
   __device__ __forceinline__ void init(const Geom& g, const double* L0src, int t, int q, int n_) {
     const int c = (q / g.M) % g.C;
@@ -482,12 +526,13 @@ struct GreenPoint2 {
     L11 = T(L0src[4]);
     inv_nodes = T(g.inv_nodes);
     xi1 = T(kl) * invY1;
-    n = n_;
+    n_rt = n_;
     a = q & 1;
     pad = kl >= g.H || nyquist_bin(kl, g.nlast);  // padding, or the last axis's Nyquist column
     kl0 = kl == 0;
   }
   __device__ __forceinline__ cplx<T> operator()(cplx<T> v, int i, bool act) const {
+    const int n = NC > 0 ? NC : n_rt;
     cplx<T> o;
     o.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
     o.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
@@ -601,8 +646,10 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
   const ColArgsBase& b = a.b;
   const Geom& g = b.g;
   constexpr int d = D;
-  const int n = b.plan.n, Q = QC ? QC : b.Q;
+  const int n = plan_len<PS>(b.plan), Q = QC ? QC : b.Q;
   const int tpc = TC ? TC : b.tpc;
+  // 2-D tiles are contiguous: row i of the tile starts Q values after row i - 1
+  const long long stride_i = (QC && D == 2) ? (long long)QC : b.stride_i;
   const int blk_outer = blockIdx.x / b.nb_inner;
   const int blk_inner = blockIdx.x - blk_outer * b.nb_inner;
   // 2-D batches: the inner block index is the cell
@@ -623,7 +670,7 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
   constexpr int kUnroll = 4;
   const int wpr = (int)(Q * sizeof(C) / 16);  // 16-byte words per row
   const bool vec = qvalid == Q && (Q * sizeof(C)) % 16 == 0 && (base * sizeof(C)) % 16 == 0 &&
-                   (b.stride_i * sizeof(C)) % 16 == 0;
+                   (stride_i * sizeof(C)) % 16 == 0;
   if (vec) {
     const int nw = n * wpr;
     for (int w0 = threadIdx.x; w0 < nw; w0 += kUnroll * blockDim.x) {
@@ -633,7 +680,7 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
         const int w = w0 + u * blockDim.x;
         if (w < nw) {
           const int i = w / wpr, j = w - i * wpr;
-          buf[u] = __ldg(reinterpret_cast<const float4*>(a.S + base + i * b.stride_i) + j);
+          buf[u] = __ldg(reinterpret_cast<const float4*>(a.S + base + i * stride_i) + j);
         }
       }
 #pragma unroll
@@ -648,7 +695,7 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
       C v;
       v.x = T(0);
       v.y = T(0);
-      if (q < qvalid) v = a.S[base + i * b.stride_i + q];
+      if (q < qvalid) v = a.S[base + i * stride_i + q];
       sm[idx] = v;
     }
   }
@@ -663,7 +710,7 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
     // sit in columns q and q ^ 1, i.e. adjacent lanes of one warp.
     const int t = blk_outer;
     const double* L0src = a.L0cell ? a.L0cell + 9 * cell : g.L0;
-    GreenPoint2<T> gp;
+    GreenPoint2<T, QC ? PlanLen<PS>::value : 0> gp;
     gp.init(g, L0src, t, q, n);
     fft_fused_plan<T, PS>(sm + q, Q, b.plan, u, tpc, a.tw, gp);
   } else {
@@ -688,12 +735,12 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
     const int nw = n * wpr;
     for (int w = threadIdx.x; w < nw; w += blockDim.x) {
       const int i = w / wpr, j = w - i * wpr;
-      reinterpret_cast<float4*>(a.S + base + i * b.stride_i)[j] = reinterpret_cast<const float4*>(sm)[w];
+      reinterpret_cast<float4*>(a.S + base + i * stride_i)[j] = reinterpret_cast<const float4*>(sm)[w];
     }
   } else {
     for (int idx = threadIdx.x; idx < n * Q; idx += blockDim.x) {
       const int i = idx / Q, qq = idx - i * Q;
-      if (qq < qvalid) a.S[base + i * b.stride_i + qq] = sm[idx];
+      if (qq < qvalid) a.S[base + i * stride_i + qq] = sm[idx];
     }
   }
 }
@@ -888,52 +935,60 @@ enum : int {
 };
 
 // DF (float64 only): the line FFT runs in double-float arithmetic (line_fft_df).
-template <typename T, int D, int NL, int EPI, typename PS = DynPlan, bool DF = false>
+// RS: compile-time launch shape (RowShape) or RowDyn.
+template <typename T, int D, int NL, int EPI, typename PS = DynPlan, bool DF = false, typename RS = RowDyn>
 __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks) k_row_inv(RowArgs<T> a) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  T* stab = reinterpret_cast<T*>(sm + (size_t)a.nseq * a.plan.n);
   const Geom& g = a.g;
-  const int n = a.plan.n;
   constexpr int d = D, M = D * NL;
-  const int line0 = blockIdx.x * a.lpc;
-  const int nch = a.lpc * M;
+  constexpr bool kFix = RS::nt > 0;
+  const int n = plan_len<PS>(a.plan);
+  const int nthr = kFix ? RS::nt : (int)blockDim.x;
+  const int tpl = (kFix && RS::tpl > 0) ? RS::tpl : a.tpl;
+  const int lpc = kFix ? 1 : a.lpc;
+  const int nseq = kFix ? (M + 1) / 2 : a.nseq;
+  const int Cc = kFix ? RS::cc : g.C, csh = kFix ? RS::csh : g.cshift;
+  const int H = kFix ? n / 2 + 1 : g.H;
+  T* stab = reinterpret_cast<T*>(sm + (size_t)nseq * n);
+  const int line0 = blockIdx.x * lpc;
+  const int nch = lpc * M;
   const int cell = g.ncell > 1 ? line0 / g.lines_cell : 0;
   Scal* const sc = a.scal ? a.scal + cell * NL : nullptr;
   const T* const tabc = a.tab + (size_t)cell * g.tab_stride;
   if (all_done(sc, NL)) return;
 
   if (EPI == kEpiApplyT) {
-    for (int i = threadIdx.x; i < a.nphase * D * D; i += blockDim.x) stab[i] = tabc[i];
+    for (int i = threadIdx.x; i < a.nphase * D * D; i += nthr) stab[i] = tabc[i];
   }
 
   // 1. rebuild the full spectrum of each packed sequence from the half spectra
   // (one thread per (sequence, kx); kUnroll frequencies' loads in flight)
   constexpr int kUnroll = 8;
-  for (int s = 0; s < a.nseq; ++s) {
+  for (int s = 0; s < nseq; ++s) {
     const int g0 = 2 * s, g1 = 2 * s + 1;
     const int ll0 = g0 / M, m0 = g0 - ll0 * M;
     const int ll1 = g1 / M, m1 = g1 - ll1 * M;
     const bool has0 = line0 + ll0 < g.nlines;
     const bool has1 = g1 < nch && line0 + ll1 < g.nlines;
     C* seq = sm + (size_t)s * n;
-    for (int kb = threadIdx.x; kb < g.H; kb += kUnroll * blockDim.x) {
+    for (int kb = threadIdx.x; kb < H; kb += kUnroll * nthr) {
       C y0[kUnroll], y1[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        const int kx = kb + u * blockDim.x;
+        const int kx = kb + u * nthr;
         y0[u].x = y0[u].y = y1[u].x = y1[u].y = T(0);
-        if (kx >= g.H) continue;
-        const int t = kx >> g.cshift, c = kx & (g.C - 1);
-        const long long tb = ((long long)t * g.nlines + line0) * g.C + c;
-        if (has0) y0[u] = a.S[(tb + (long long)ll0 * g.C) * M + m0];
-        if (has1) y1[u] = a.S[(tb + (long long)ll1 * g.C) * M + m1];
+        if (kx >= H) continue;
+        const int t = kx >> csh, c = kx & (Cc - 1);
+        const long long tb = ((long long)t * g.nlines + line0) * Cc + c;
+        if (has0) y0[u] = a.S[(tb + (long long)ll0 * Cc) * M + m0];
+        if (has1) y1[u] = a.S[(tb + (long long)ll1 * Cc) * M + m1];
       }
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        const int kx = kb + u * blockDim.x;
-        if (kx >= g.H) continue;
+        const int kx = kb + u * nthr;
+        if (kx >= H) continue;
         if (kx == 0 || 2 * kx == n) {  // bins that are their own Hermitian partner
           C w;
           w.x = y0[u].x;
@@ -956,11 +1011,11 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
   // 2. inverse FFT
   if constexpr (DF) {
     static_assert(std::is_same<T, double>::value, "double-float line FFTs are for float64 rows");
-    line_fft_df<true>(sm, a.nseq, n, a.plan, a.tpl, a.twdf);
+    line_fft_df<true>(sm, nseq, n, a.plan, tpl, a.twdf);
   } else {
-    const int s = threadIdx.x / a.tpl;
-    const int u = s < a.nseq ? threadIdx.x - s * a.tpl : n;
-    fft_plan<true, T, PS>(sm + (size_t)(s < a.nseq ? s : 0) * n, 1, a.plan, u, a.tpl, a.tw);
+    const int s = threadIdx.x / tpl;
+    const int u = s < nseq ? threadIdx.x - s * tpl : n;
+    fft_plan<true, T, PS>(sm + (size_t)(s < nseq ? s : 0) * n, 1, a.plan, u, tpl, a.tw);
   }
 
   // 3. epilogue
@@ -985,18 +1040,18 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
   }
   constexpr bool kReadIn = true;
   constexpr bool kReadAux = (EPI == kEpiDirShadow);
-  for (int ll = 0; ll < a.lpc; ++ll) {
+  for (int ll = 0; ll < lpc; ++ll) {
     const int line = line0 + ll;
     if (line >= g.nlines) break;
     const long long lo = (long long)line * n;
-    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * blockDim.x) {
+    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * nthr) {
       T vin[kUnroll][NL][D];
       T vaux[kUnroll][NL][D];
       T vrhs[kUnroll][NL][D];
       int ph[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * blockDim.x;
+        const int i = i0 + u * nthr;
         const bool ok = i < n;
         ph[u] = (EPI == kEpiApplyT && ok) ? a.phase[lo + i] : 0;
 #pragma unroll
@@ -1012,7 +1067,7 @@ __global__ void __launch_bounds__(RowBounds<PS>::threads, RowBounds<PS>::blocks)
       }
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * blockDim.x;
+        const int i = i0 + u * nthr;
         if (i >= n) continue;
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
@@ -1082,9 +1137,11 @@ struct VecArgsBase {
 template <typename T> struct VecArgs {
   VecArgsBase b;
   int want_pp;             // CG: also reduce (p, p) (eta_r history)
+  int xmode;               // CG: 1 x += alpha p; 0 x untouched (step deferred); 2 x += alpha_x p2 + alpha p
   T* x[kMaxLoads];
   T* r[kMaxLoads];
   const T* p[kMaxLoads];
+  const T* p2[kMaxLoads];  // CG, xmode 2: the previous iteration's direction
   const T* ap[kMaxLoads];
   T* rs[kMaxLoads];        // BiCG shadow residual
   const T* atps[kMaxLoads];// BiCG A^T p*
@@ -1121,7 +1178,11 @@ __device__ __forceinline__ void for_range(long long b, long long e, long long t,
 }
 
 // PP: also accumulate (p, p) into *dpp (the eta_r history of Section 3).
-template <typename T, bool PP = false>
+// XM: the x step.  1: x += al p.  0: x is not touched (its step is owed).
+// 2: x += ax p2, then x += al p -- the owed step of the previous iteration
+// and this one's, in that order, so x receives exactly the float32 sums of two
+// single updates while it is read and written once instead of twice.
+template <typename T, bool PP = false, int XM = 1>
 struct CgUpd {
   using V = typename Vec16<T>::type;
   static constexpr int W = Vec16<T>::n;
@@ -1129,26 +1190,38 @@ struct CgUpd {
   T* __restrict__ r;
   const T* __restrict__ p;
   const T* __restrict__ ap;
-  T al;
+  const T* __restrict__ p2;
+  T al, ax;
   DotAcc<T>* dot;
   DotAcc<T>* dpp;
   __device__ __forceinline__ void scalar(long long i) {
-    const T pi = p[i];
-    x[i] += al * pi;
+    if (XM != 0 || PP) {
+      const T pi = p[i];
+      if (XM == 1) {
+        x[i] += al * pi;
+      } else if (XM == 2) {
+        T xv = x[i];
+        xv += ax * p2[i];
+        xv += al * pi;
+        x[i] = xv;
+      }
+      if (PP) dpp->add(pi * pi);
+    }
     const T rn = r[i] - al * ap[i];
     r[i] = rn;
     dot->add(rn * rn);
-    if (PP) dpp->add(pi * pi);
   }
   __device__ __forceinline__ void vec2(long long k0, long long k1) {
-    V xv[2], rv[2], pv[2], av[2];
+    constexpr bool kP = XM != 0 || PP;
+    V xv[2], rv[2], pv[2], qv[2], av[2];
     const long long kk[2] = {k0, k1};
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (kk[u] < 0) continue;
-      xv[u] = reinterpret_cast<const V*>(x)[kk[u]];
+      if (XM != 0) xv[u] = reinterpret_cast<const V*>(x)[kk[u]];
       rv[u] = reinterpret_cast<const V*>(r)[kk[u]];
-      pv[u] = __ldg(reinterpret_cast<const V*>(p) + kk[u]);
+      if (kP) pv[u] = __ldg(reinterpret_cast<const V*>(p) + kk[u]);
+      if (XM == 2) qv[u] = __ldg(reinterpret_cast<const V*>(p2) + kk[u]);
       av[u] = __ldg(reinterpret_cast<const V*>(ap) + kk[u]);
     }
 #pragma unroll
@@ -1156,14 +1229,39 @@ struct CgUpd {
       if (kk[u] < 0) continue;
 #pragma unroll
       for (int w = 0; w < W; ++w) {
-        vlane<V, T>(xv[u], w) += al * vlane<V, T>(pv[u], w);
+        if (XM == 2) vlane<V, T>(xv[u], w) += ax * vlane<V, T>(qv[u], w);
+        if (XM != 0) vlane<V, T>(xv[u], w) += al * vlane<V, T>(pv[u], w);
         const T rn = vlane<V, T>(rv[u], w) - al * vlane<V, T>(av[u], w);
         vlane<V, T>(rv[u], w) = rn;
         dot->add(rn * rn);
         if (PP) dpp->add(vlane<V, T>(pv[u], w) * vlane<V, T>(pv[u], w));
       }
-      reinterpret_cast<V*>(x)[kk[u]] = xv[u];
+      if (XM != 0) reinterpret_cast<V*>(x)[kk[u]] = xv[u];
       reinterpret_cast<V*>(r)[kk[u]] = rv[u];
+    }
+  }
+};
+
+// The owed x step of CG items that stopped after an iteration whose x update
+// was deferred: x += alpha_x p (p = the first direction buffer).
+template <typename T>
+struct XFlush {
+  using V = typename Vec16<T>::type;
+  static constexpr int W = Vec16<T>::n;
+  T* __restrict__ x;
+  const T* __restrict__ p;
+  T ax;
+  __device__ __forceinline__ void scalar(long long i) { x[i] += ax * p[i]; }
+  __device__ __forceinline__ void vec2(long long k0, long long k1) {
+    const long long kk[2] = {k0, k1};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (kk[u] < 0) continue;
+      V xv = reinterpret_cast<const V*>(x)[kk[u]];
+      V pv = __ldg(reinterpret_cast<const V*>(p) + kk[u]);
+#pragma unroll
+      for (int w = 0; w < W; ++w) vlane<V, T>(xv, w) += ax * vlane<V, T>(pv, w);
+      reinterpret_cast<V*>(x)[kk[u]] = xv;
     }
   }
 };
@@ -1221,9 +1319,10 @@ __device__ __forceinline__ void cell_ranges(const VecArgs<T>& a, Mk&& mk) {
   }
 }
 
-// CG: x += alpha p; r -= alpha A p; partial (r, r) at slot l, and with PP
-// (p, p) at slot kMaxLoads + l (for the eta_r history)
-template <typename T, int NL, bool PP = false>
+// CG: x += alpha p (as selected by XM, see CgUpd); r -= alpha A p; partial
+// (r, r) at slot l, and with PP (p, p) at slot kMaxLoads + l (for the eta_r
+// history)
+template <typename T, int NL, bool PP = false, int XM = 1>
 __global__ void k_cg_update(VecArgs<T> a) {
   const int bpc = gridDim.x / a.b.ncell;
   const int cell = blockIdx.x / bpc;
@@ -1237,7 +1336,7 @@ __global__ void k_cg_update(VecArgs<T> a) {
   for (int l = 0; l < NL; ++l) {
     if (sc[l].done != kRunning) continue;
     DotAcc<T> dot, dpp;
-    CgUpd<T, PP> f{a.x[l], a.r[l], a.p[l], a.ap[l], T(sc[l].alpha), &dot, &dpp};
+    CgUpd<T, PP, XM> f{a.x[l], a.r[l], a.p[l], a.ap[l], a.p2[l], T(sc[l].alpha), T(sc[l].alpha_x), &dot, &dpp};
     cell_ranges<T, NL>(a, [&](long long b0, long long e0, long long t, long long stride, int) {
       for_range<T>(b0, e0, t, stride, f);
     });
@@ -1245,6 +1344,23 @@ __global__ void k_cg_update(VecArgs<T> a) {
     if (PP) acc[PP ? kMaxLoads + l : 0] = dpp.get();
   }
   block_reduce_store<NV>(acc, NV, a.part, gridDim.x, blockIdx.x);
+}
+
+// After the iteration loop: items whose last x step is still owed (xpend)
+// receive it, x += alpha_x p.
+template <typename T, int NL>
+__global__ void k_cg_flush(VecArgs<T> a) {
+  const int bpc = gridDim.x / a.b.ncell;
+  const int cell = blockIdx.x / bpc;
+  const Scal* const sc = a.scal + cell * NL;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    if (!sc[l].xpend) continue;
+    XFlush<T> f{a.x[l], a.p[l], T(sc[l].alpha_x)};
+    cell_ranges<T, NL>(a, [&](long long b0, long long e0, long long t, long long stride, int) {
+      for_range<T>(b0, e0, t, stride, f);
+    });
+  }
 }
 
 // BiCG: x += alpha p; r -= alpha A p; r* -= alpha A^T p*; partials (r, r*), (r, r), (p, p)
@@ -1375,7 +1491,10 @@ static __global__ void k_scal_alpha(Scal* scal, const double* part, int np, int 
 
 // CG: beta = (r+, r+) / (r, r); convergence on the recursive residual.
 // BiCG: beta = (r+, r*+) / (r, r*); convergence on (r+, r+).
-static __global__ void k_scal_beta(Scal* scal, const double* part, int np, int ncell, int nl, int bicg) {
+// xpar (CG with the x step deferred): 0 after an iteration that left its x
+// step owed, 1 after one that settled it, -1 when x moves every iteration.
+static __global__ void k_scal_beta(Scal* scal, const double* part, int np, int ncell, int nl, int bicg,
+                                   int xpar) {
   const ItemRef r = item_ref(np, ncell, nl);
   if (!r.valid) return;
   double rho_new = 0.0, rr_new, pp = 0.0;
@@ -1391,6 +1510,12 @@ static __global__ void k_scal_beta(Scal* scal, const double* part, int np, int n
   if (threadIdx.x == 0) {
     Scal& s = scal[r.item];
     if (s.done != kRunning) return;
+    if (xpar == 0) {
+      s.alpha_x = s.alpha;
+      s.xpend = 1;
+    } else if (xpar == 1) {
+      s.xpend = 0;
+    }
     // eta_r of this step: ||L0 alpha p|| / ||e0|| (Eq. errR_def), index = step
     if (s.hist_eta_r != nullptr && s.iter < s.hist_cap)
       s.hist_eta_r[s.iter] = s.l0iso > 0.0 ? s.l0iso * fabs(s.alpha) * sqrt(pp / s.b2) : NAN;

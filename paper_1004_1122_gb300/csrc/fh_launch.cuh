@@ -29,6 +29,7 @@ struct LaunchTable {
   // nullptr for float and for 3-D.
   cudaError_t (*col_df)(const Launch&, const ColArgs<T>&, const void* tw_df, cudaStream_t) = nullptr;
   cudaError_t (*cg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
+  cudaError_t (*cg_flush)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*bicg_update)(const Launch&, const VecArgs<T>&, cudaStream_t) = nullptr;
   cudaError_t (*current_sum)(const Launch&, const T*, const uint8_t*, const double*, long long nodes,
                              int ncell, long long cell_nodes, int tab_stride, double*,

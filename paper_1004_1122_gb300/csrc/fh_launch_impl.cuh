@@ -52,6 +52,16 @@ constexpr bool kHasDf = std::is_same<T, double>::value && D == 2;
 // 2187-point column FFT.
 constexpr int kGreenQ = 4;
 constexpr int kGreenT = 81;
+// Likewise the 2187^2 A p pass: one line per 96-thread CTA, spectrum tiles of
+// 2 frequencies; the threads per line FFT stay a launch argument (compiled in,
+// they cost registers and the pass spilled: 44.0 against 41.7 us; the
+// direction pass measured no gain from either form: 47.3 / 48.8 against 47.1).
+using RowShape2187 = RowShape<96, 0, 2>;
+template <typename T>
+inline bool row_shape_is_2187(const Launch& L, const RowArgs<T>& a) {
+  return L.block == RowShape2187::nt && a.lpc == 1 && (RowShape2187::tpl == 0 || a.tpl == RowShape2187::tpl) &&
+         a.g.C == RowShape2187::cc && a.nseq == 1;
+}
 
 template <typename T, int D, int NL>
 struct Launchers {
@@ -61,6 +71,8 @@ struct Launchers {
       using P = CtPlan<D, NL>;
       if ((e = opt_in_smem(k_row_fwd<T, D, NL, kProDir, P>, rs)) != cudaSuccess) return e;
       if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, P>, rs)) != cudaSuccess) return e;
+      if constexpr (D == 2 && NL == 1)
+        if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, P, false, RowShape2187>, rs)) != cudaSuccess) return e;
       if ((e = opt_in_smem(k_col<T, D, kColGreen, P>, c0)) != cudaSuccess) return e;
       if constexpr (D == 2 && NL == 1)
         if ((e = opt_in_smem(k_col<T, D, kColGreen, P, kGreenQ, kGreenT>, c0)) != cudaSuccess) return e;
@@ -157,6 +169,12 @@ struct Launchers {
     if constexpr (kHasCt<T, D, NL>) {
       using P = CtPlan<D, NL>;
       if (epi == kEpiDir && L.block <= RowBounds<P>::threads && cplan_is<P>(a.plan)) {
+        if constexpr (D == 2 && NL == 1) {
+          if (row_shape_is_2187(L, a)) {
+            k_row_inv<T, D, NL, kEpiDir, P, false, RowShape2187><<<L.grid, L.block, L.smem, st>>>(a);
+            return cudaGetLastError();
+          }
+        }
         k_row_inv<T, D, NL, kEpiDir, P><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
       }
@@ -195,7 +213,7 @@ struct Launchers {
       if (L.block <= ColBounds<P>::threads && cplan_is<P>(a.b.plan)) {
         if (mode == kColGreen) {
           if constexpr (D == 2 && NL == 1) {
-            if (a.b.Q == kGreenQ && a.b.tpc == kGreenT) {  // the tuned 2187^2 tile shape
+            if (a.b.Q == kGreenQ && a.b.tpc == kGreenT && a.b.stride_i == kGreenQ) {  // the tuned 2187^2 tile shape
               k_col<T, D, kColGreen, P, kGreenQ, kGreenT><<<L.grid, L.block, L.smem, st>>>(a);
               return cudaGetLastError();
             }
@@ -270,10 +288,21 @@ struct Launchers {
     return cudaErrorInvalidValue;
   }
   static cudaError_t cg_update(const Launch& L, const VecArgs<T>& v, cudaStream_t st) {
-    if (v.want_pp)
-      k_cg_update<T, NL, true><<<L.grid, L.block, 0, st>>>(v);
-    else
-      k_cg_update<T, NL, false><<<L.grid, L.block, 0, st>>>(v);
+#define FH_CGU(PP, XM) k_cg_update<T, NL, PP, XM><<<L.grid, L.block, 0, st>>>(v)
+    switch (v.xmode * 2 + (v.want_pp ? 1 : 0)) {
+      case 0: FH_CGU(false, 0); break;
+      case 1: FH_CGU(true, 0); break;
+      case 2: FH_CGU(false, 1); break;
+      case 3: FH_CGU(true, 1); break;
+      case 4: FH_CGU(false, 2); break;
+      case 5: FH_CGU(true, 2); break;
+      default: return cudaErrorInvalidValue;
+    }
+#undef FH_CGU
+    return cudaGetLastError();
+  }
+  static cudaError_t cg_flush(const Launch& L, const VecArgs<T>& v, cudaStream_t st) {
+    k_cg_flush<T, NL><<<L.grid, L.block, 0, st>>>(v);
     return cudaGetLastError();
   }
   static cudaError_t bicg_update(const Launch& L, const VecArgs<T>& v, cudaStream_t st) {
@@ -317,6 +346,7 @@ struct Launchers {
     }
     if (kHasDf<T, D>) t.col_df = &col_df;
     t.cg_update = &cg_update;
+    t.cg_flush = &cg_flush;
     t.bicg_update = &bicg_update;
     t.current_sum = &current_sum;
     t.matnorm2 = &matnorm2;

@@ -123,6 +123,7 @@ struct Pipeline {
   T* x[kMaxLoads] = {};
   T* r[kMaxLoads] = {};
   T* p[kMaxLoads] = {};
+  T* p2[kMaxLoads] = {};     // CG with deferred x steps: the second direction buffer
   T* ap[kMaxLoads] = {};
   T* rs[kMaxLoads] = {};
   T* ps[kMaxLoads] = {};
@@ -186,6 +187,9 @@ struct Pipeline {
   bool solve_done() const;
   void solve_results(SolveResult* res) const;
   int run_method_ = 0, run_K_ = 8;
+  // CG defers every other x step (x is read and written once per two
+  // iterations); off while the eta_e history needs the iterate every iteration
+  bool defer_x_ = false;
   long long run_guard_max_ = 0;
   int* d_loop = nullptr;     // device [2]: rounds run by the device-side loop, round limit
   int* h_loop = nullptr;     // pinned host mirror
@@ -195,7 +199,12 @@ struct Pipeline {
   // stream).  *kernels receives the kernels one body launches.
   cudaError_t capture_loop_body(cudaGraph_t body, cudaGraphConditionalHandle h, int method, int K,
                                 long long* kernels);
-  cudaError_t enqueue_iter(int method);
+  // j: parity of the iteration within the captured body (CG with deferred x
+  // steps alternates the two direction buffers and settles x every second
+  // iteration)
+  cudaError_t enqueue_iter(int method, int j = 0);
+  // CG items that stopped with an x step owed receive it (after the loop)
+  cudaError_t enqueue_x_flush();
   // eta_e (Eq. errE_def) of the current iterate x[0] into hist_eta_e[iter]
   cudaError_t enqueue_eta_record();
   int chunk_size(int method) const;

@@ -461,15 +461,22 @@ int Pipeline<T>::chunk_size(int method) const {
 }
 
 template <typename T>
-cudaError_t Pipeline<T>::enqueue_iter(int method) {
+cudaError_t Pipeline<T>::enqueue_iter(int method, int j) {
   RowArgs<T> a = row_args();
   a.scal = scal;
   if (method == kCG) {
+    // With deferred x steps the direction alternates between p (even j) and
+    // p2 (odd j): the direction pass reads the previous p from the other
+    // buffer, and the odd iteration's update settles both x steps.
+    const bool odd = defer_x_ && (j & 1);
+    T* const* pcur = odd ? p2 : p;
+    T* const* pprev = odd ? p : p2;
     RowArgs<T> f = a, i = a;
     for (int l = 0; l < nloads; ++l) {
       f.in[l] = r[l];
-      f.out[l] = p[l];
-      i.in[l] = p[l];
+      f.out[l] = pcur[l];
+      f.aux[l] = defer_x_ ? pprev[l] : nullptr;
+      i.in[l] = pcur[l];
       i.out[l] = ap[l];
     }
     FH_CK(passes(kProDir, kEpiDir, f, i, scal));
@@ -487,16 +494,19 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
     for (int l = 0; l < nloads; ++l) {
       v.x[l] = x[l];
       v.r[l] = r[l];
-      v.p[l] = p[l];
+      v.p[l] = pcur[l];
+      v.p2[l] = pprev[l];
       v.ap[l] = ap[l];
     }
     v.scal = scal;
     v.part = part;
     v.want_pp = hist_eta_r != nullptr && items == 1;
+    v.xmode = !defer_x_ ? 1 : (odd ? 2 : 0);
     ++launches;
     FH_CK(lt.cg_update(vec, v, st));
     ++launches;
-    k_scal_beta<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, vec.grid, ncell, nloads, 0);
+    k_scal_beta<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, vec.grid, ncell, nloads, 0,
+                                                            !defer_x_ ? -1 : (odd ? 1 : 0));
     FH_CK(cudaGetLastError());
     return hist_eta_e != nullptr && items == 1 ? enqueue_eta_record() : cudaSuccess;
   }
@@ -540,7 +550,7 @@ cudaError_t Pipeline<T>::enqueue_iter(int method) {
     ++launches;
     FH_CK(lt.bicg_update(vec, v, st));
     ++launches;
-    k_scal_beta<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, vec.grid, ncell, nloads, 1);
+    k_scal_beta<<<item_blocks(items), kRedThreads, 0, st>>>(scal, part, vec.grid, ncell, nloads, 1, -1);
     FH_CK(cudaGetLastError());
     return hist_eta_e != nullptr && items == 1 ? enqueue_eta_record() : cudaSuccess;
   }
@@ -714,12 +724,31 @@ int Pipeline<T>::solve(int method, const double (*E)[kMaxD], bool rhs_field, int
 }
 
 template <typename T>
+cudaError_t Pipeline<T>::enqueue_x_flush() {
+  VecArgs<T> v;
+  std::memset(&v, 0, sizeof(v));
+  v.b.len = vlen;
+  v.b.nloads = nloads;
+  v.b.ncell = ncell;
+  v.b.d = g.d;
+  v.b.nodes = g.nodes;
+  v.b.cell_nodes = g.cell_nodes;
+  for (int l = 0; l < nloads; ++l) {
+    v.x[l] = x[l];
+    v.p[l] = p[l];
+  }
+  v.scal = scal;
+  ++launches;
+  return lt.cg_flush(vec, v, st);
+}
+
+template <typename T>
 cudaError_t Pipeline<T>::capture_loop_body(cudaGraph_t body, cudaGraphConditionalHandle h, int method, int K,
                                            long long* kernels) {
   const long long before = launches;
   FH_CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < K && e == cudaSuccess; ++k) e = enqueue_iter(method);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) e = enqueue_iter(method, k);
   if (e == cudaSuccess) {
     ++launches;
     k_loop_cond<<<1, 128, 0, st>>>(h, scal, items, d_loop);
@@ -745,7 +774,7 @@ int run_loops(Pipeline<T>* const* ps, int np, cudaStream_t launch, LoopCache& ca
   if (it == cache.exec.end()) {
     cudaGraph_t g = nullptr;
     FH_CKS(cudaGraphCreate(&g, 0));
-    std::vector<long long> kern(np, 0);
+    std::vector<long long> kern(2 * np, 0);  // per pipeline: kernels per loop round, then after the loop
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < np && e == cudaSuccess; ++i) {
       cudaGraphConditionalHandle h;
@@ -759,6 +788,19 @@ int run_loops(Pipeline<T>* const* ps, int np, cudaStream_t launch, LoopCache& ca
       e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
       if (e != cudaSuccess) break;
       e = ps[i]->capture_loop_body(cp.conditional.phGraph_out[0], h, ps[i]->run_method_, ps[i]->run_K_, &kern[i]);
+      if (e == cudaSuccess && ps[i]->defer_x_) {
+        // after the loop: the x step owed by items that stopped on an even iteration
+        Pipeline<T>& P = *ps[i];
+        e = cudaStreamBeginCaptureToGraph(P.st, g, &node, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        const long long before = P.launches;
+        e = P.enqueue_x_flush();
+        P.launches = before;
+        cudaGraph_t out = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(P.st, &out);
+        if (e == cudaSuccess) e = e2;
+        kern[np + i] = 1;
+      }
     }
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
@@ -803,7 +845,7 @@ int run_loops(Pipeline<T>* const* ps, int np, cudaStream_t launch, LoopCache& ca
   }
   const std::vector<long long>& kern = cache.kernels[key];
   for (int i = 0; i < np; ++i) {
-    ps[i]->launches += (long long)ps[i]->h_loop[0] * kern[i];
+    ps[i]->launches += (long long)ps[i]->h_loop[0] * kern[i] + kern[np + i];
     if (ps[i]->device_error()) {
       err = "a bounded device wait expired";
       return 8;
@@ -840,6 +882,11 @@ int Pipeline<T>::solve_begin(int method, const double (*E)[kMaxD], bool rhs_fiel
       if ((rc = dev_alloc(allocs, &ps[l], vlen, err))) return rc;
       if ((rc = dev_alloc(allocs, &atps[l], vlen, err))) return rc;
     }
+  }
+  defer_x_ = method == kCG && !(hist_eta_e != nullptr && items == 1);
+  if (defer_x_ && p2[0] == nullptr) {
+    for (int l = 0; l < nloads; ++l)
+      if ((rc = dev_alloc(allocs, &p2[l], vlen, err))) return rc;
   }
   rhs_active_ = rhs_field;
   // a wait that expired in an earlier solve has been reported; start clean
@@ -921,6 +968,7 @@ int Pipeline<T>::solve_begin(int method, const double (*E)[kMaxD], bool rhs_fiel
     FH_CKS(cudaGetLastError());
     for (int l = 0; l < nloads; ++l) {
       FH_CKS(cudaMemsetAsync(p[l], 0, vbytes, st));
+      if (defer_x_) FH_CKS(cudaMemsetAsync(p2[l], 0, vbytes, st));  // the first iteration's previous p
       if (method == kBiCG) {
         FH_CKS(cudaMemcpyAsync(rs[l], r[l], vbytes, cudaMemcpyDeviceToDevice, st));
         FH_CKS(cudaMemsetAsync(ps[l], 0, vbytes, st));
@@ -1064,6 +1112,7 @@ int Pipeline<T>::profile(int what, int reps, double* ms, std::string& err) {
   }
   v.scal = scal;
   v.part = part;
+  v.xmode = 1;
   auto one = [&]() -> cudaError_t {
     switch (what) {
       case 0: return launch_row_fwd(kProDir, f);

@@ -406,3 +406,29 @@ def test_even_grids_match_oracle(N):
     assert _rel_l2(x.cpu().numpy(), xo) < 1e-6
     eta = oracle.eta_e(xo, phase, L)
     assert eta < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cg_deferred_x_steps_are_exact(precision):
+    """CG settles the x step of every second iteration together with the next
+    one (x += alpha_k p_k, then += alpha_{k+1} p_{k+1}, in one pass) and owes
+    the last step when it stops after an even iteration.  With the per-iteration
+    norms requested x moves every iteration instead.  Both orders of work give
+    the same float sums, so the fields and iteration counts must agree exactly,
+    whichever parity the stopping iteration has."""
+    torch = cuda_or_skip()
+    from paper_1004_1122_gb300 import fh
+
+    phase, L, _ = _c1()
+    E = [1.0, 0.0]
+    parities = set()
+    with fh.Solver(phase, L, precision=precision) as s:
+        for tol in (1e-3, 5e-4, 2e-4, 1e-4, 3e-5, 1e-5):
+            x1, c1, i1 = s.solve(E, tol=tol, method="cg", max_iter=5000)
+            x2, c2, i2 = s.solve(E, tol=tol, method="cg", max_iter=5000, history=4096, norms=True)
+            assert i1["status"] == "FH_OK" and i2["status"] == "FH_OK", (i1, i2)
+            assert i1["iters"] == i2["iters"], (tol, i1["iters"], i2["iters"])
+            assert torch.equal(x1, x2), (tol, float((x1 - x2).abs().max()))
+            assert np.array_equal(c1, c2), (tol, c1, c2)
+            parities.add(i1["iters"] % 2)
+    assert parities == {0, 1}, parities
