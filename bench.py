@@ -447,8 +447,11 @@ def spectrum_bytes(n0, n1, d, s):
 def pass_bytes(n, d, s):
     """Algorithmic bytes per launch of the four CG-iteration pass kernels on an
     n x n grid, d components of s bytes: (profile index, bytes).  One CG
-    iteration of the 2-D solver reads and writes exactly these (Section 3's CG
-    with the operator of Eq. mtrx_B split into the row, Green and row passes)."""
+    iteration of the 2-D solver reads and writes these (Section 3's CG with the
+    operator of Eq. mtrx_B split into the row, Green and row passes).  The
+    update is timed (fh_profile) in its every-iteration form, x += alpha p; the
+    solver settles x every second iteration, so its updates move 3ds and 7ds
+    bytes per node on alternate iterations instead of 6ds each time."""
     nodes = n * n
     spec = spectrum_bytes(n, n, d, s)
     return {
