@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the cuFFT float64 CG baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--serial", action="store_true",
+                    help="run the step's solves one after another on one host thread (same contexts and "
+                         "kernels; for profilers, which serialise kernels anyway)")
     ap.add_argument("--c5-n", type=int, default=135, help="grid of the warm-start workload (a multiple of 27)")
     ap.add_argument("--c5-train", type=int, default=200, help="training cells of the warm-start workload")
     ap.add_argument("--c5-eval", type=int, default=32, help="held-out cells of the warm-start workload")
@@ -538,7 +541,7 @@ def run_fh(args):
             raise RuntimeError(f"solve failed: {info}")
         return col, info
 
-    def step(concurrent=True):
+    def step(concurrent=not args.serial):
         t, res = run_units(solve_unit, concurrent)
         leff = [np.stack([res[2 * i + j][0] for j in range(len(LOADS))], axis=1) for i in range(len(tables))]
         return t, leff, [r[1] for r in res]
@@ -594,7 +597,7 @@ def run_fh(args):
 
     e2e_ms = 0.0
     for _ in range(args.steps):
-        e2e_ms += run_units(e2e_unit, True)[0]
+        e2e_ms += run_units(e2e_unit, not args.serial)[0]
     e2e_ms = max_over_ranks(e2e_ms, world)
     e2e_value = replica_value(e2e_ms, args.steps, nsolve, world)
     h2d, d2h = bytes_moved["h2d"], bytes_moved["d2h"]
@@ -692,9 +695,11 @@ def run_fh(args):
             "dtype": "f32 (f64 refinement)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "solves_per_step": nsolve,
-                       "schedule": "the 8 independent solves of a step on 8 contexts and streams, one host "
-                                   "thread each (value = step time / 8: throughput); latency_sequential "
-                                   "holds the same step run one solve after another",
+                       "schedule": ("the 8 solves of a step one after another on one host thread (--serial)"
+                                    if args.serial else
+                                    "the 8 independent solves of a step on 8 contexts and streams, one host "
+                                    "thread each (value = step time / 8: throughput); latency_sequential "
+                                    "holds the same step run one solve after another"),
                        "l2": "no flush: working set (8 contexts, ~3 GB) > L2"},
             "latency_sequential": latency,
             "clocks": clk,
