@@ -422,14 +422,16 @@ def csrc_digest() -> str:
 
 
 TRAFFIC_SUMMARY = os.path.join("profiles", "traffic_c2_2187_fp32.md")
+TRAFFIC_SUMMARY_3D = os.path.join("profiles", "traffic_c3_243cube_fp32.md")
 
 
-def recorded_traffic(kernel: str):
+def recorded_traffic(kernel: str, summary: str = TRAFFIC_SUMMARY):
     """DRAM bytes per launch (read + write) of `kernel` as recorded by an ncu
-    capture (a cold-L2 launch of `bench.py --probe`) in the committed summary,
-    or None when the summary was taken on other kernel sources.  This is a
-    recorded figure, not a measurement of this run."""
-    path = os.path.join(ROOT, TRAFFIC_SUMMARY)
+    capture (a cold-L2 launch of `bench.py --probe`, or `--probe-3d` for the
+    3-D summary) in the committed summary, or None when the summary was taken
+    on other kernel sources.  This is a recorded figure, not a measurement of
+    this run."""
+    path = os.path.join(ROOT, summary)
     if not os.path.exists(path):
         return None
     digest = csrc_digest()
@@ -901,6 +903,7 @@ def run_c3(args):
     peak, peak_src = load_peaks()
     dom3 = max(times3, key=lambda k: times3[k])
     ach3 = kern3[dom3][1] / (times3[dom3] * 1e-3) / 1e9
+    traffic3 = recorded_traffic(dom3, TRAFFIC_SUMMARY_3D)
     s.close()
     line = {
         "metric": "3-D full effective tensor: time per load solve to true rel.res 1e-6 (3 loads per launch)",
@@ -916,7 +919,10 @@ def run_c3(args):
                    "rel_res_true": [i["rel_res_true"] for i in infos], "status": [i["status"] for i in infos],
                    "L_eff": Le.tolist(), "ct_plans": infos[0]["ct_plans"]},
         "roofline": {"bound": "hbm", "achieved": ach3, "peak": peak, "unit": "GB/s", "frac": ach3 / peak,
-                     "traffic": None, "kernel": dom3, "peak_source": peak_src,
+                     "traffic": traffic3, "kernel": dom3, "peak_source": peak_src,
+                     "traffic_source": (f"recorded, not measured by this run: ncu dram__bytes_read.sum + "
+                                        f"dram__bytes_write.sum of cold-L2 launches ({TRAFFIC_SUMMARY_3D}, "
+                                        f"kernel sources {csrc_digest()})") if traffic3 else None,
                      "algorithmic_bytes_per_launch": kern3[dom3][1], "ms_per_launch": times3[dom3],
                      "note": "one-load float32 pipeline of the same context (fh_profile)"},
         "kernels_ms": times3,

@@ -173,6 +173,12 @@ fh_status fh_apply(fh_ctx* ctx, const void* e_in, void* e_out, int transpose, in
  *  e_out      device float64 [d][N...] for the solution, or NULL.
  *  Leff_col   host, d float64 for <L e> (column of L_eff for unit E), or NULL.
  *  info       host, or NULL.
+ * The iterations of an inner solve run on the device in one graph launch
+ * (a while node over chunks of iterations).  With the environment variable
+ * FH_HOST_LOOP set (not "0") the same iterations are issued as ordinary
+ * stream launches, one chunk at a time with the host testing the stop
+ * conditions in between: slower, but visible launch by launch to profilers
+ * that cannot look inside graphs with conditional nodes.
  * Returns FH_OK, FH_ERR_NOT_CONVERGED (the iteration cap, or the host's
  * iteration guard ran out without a device status; e_out still holds the
  * last iterate), FH_ERR_BREAKDOWN, FH_ERR_ARG, FH_ERR_CUDA, or FH_ERR_TIMEOUT

@@ -761,8 +761,67 @@ cudaError_t Pipeline<T>::capture_loop_body(cudaGraph_t body, cudaGraphConditiona
   return e != cudaSuccess ? e : e2;
 }
 
+// FH_HOST_LOOP set (and not "0"): run_loops drives the iterations from the
+// host instead (run_loops_host).
+static bool host_loop_mode() {
+  static const bool on = [] {
+    const char* v = std::getenv("FH_HOST_LOOP");
+    return v != nullptr && v[0] != '\0' && !(v[0] == '0' && v[1] == '\0');
+  }();
+  return on;
+}
+
+// The same iterations as ordinary stream launches, K at a time per pipeline
+// on its own stream, with the host reading the scalars after every chunk and
+// stopping at the same conditions as the graph's while node (all items
+// stopped, or the round guard).  For profilers, which cannot profile the
+// kernel nodes of a graph that holds conditional nodes; the kernels and their
+// arguments are those of the graph.
+template <typename T>
+static int run_loops_host(Pipeline<T>* const* ps, int np, std::string& err) {
+  std::vector<long long> rounds(np, 0);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < np && e == cudaSuccess; ++i) {
+    Pipeline<T>& P = *ps[i];
+    e = cudaMemcpyAsync(P.h_scal, P.scal, P.items * sizeof(Scal), cudaMemcpyDeviceToHost, P.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P.st);
+  }
+  while (e == cudaSuccess) {
+    bool any = false;
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+      Pipeline<T>& P = *ps[i];
+      if (P.solve_done() || rounds[i] >= P.run_guard_max_) continue;
+      for (int k = 0; k < P.run_K_ && e == cudaSuccess; ++k) e = P.enqueue_iter(P.run_method_, k);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P.h_scal, P.scal, P.items * sizeof(Scal), cudaMemcpyDeviceToHost, P.st);
+      ++rounds[i];
+      any = true;
+    }
+    if (!any) break;
+    for (int i = 0; i < np && e == cudaSuccess; ++i) e = cudaStreamSynchronize(ps[i]->st);
+  }
+  for (int i = 0; i < np && e == cudaSuccess; ++i) {
+    Pipeline<T>& P = *ps[i];
+    if (P.defer_x_) e = P.enqueue_x_flush();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.h_err, P.dev_err, sizeof(int), cudaMemcpyDeviceToHost, P.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P.st);
+  }
+  if (e != cudaSuccess) {
+    err = std::string("host-driven iteration loop: ") + cudaGetErrorString(e);
+    return 5;
+  }
+  for (int i = 0; i < np; ++i) {
+    if (ps[i]->device_error()) {
+      err = "a bounded device wait expired";
+      return 8;
+    }
+  }
+  return 0;
+}
+
 template <typename T>
 int run_loops(Pipeline<T>* const* ps, int np, cudaStream_t launch, LoopCache& cache, std::string& err) {
+  if (host_loop_mode()) return run_loops_host(ps, np, err);
   std::string key;
   for (int i = 0; i < np; ++i) {
     const Pipeline<T>& P = *ps[i];
