@@ -557,13 +557,13 @@ struct GreenPoint2 {
 // forward FFT along axis 0): y^(k) = xi (xi . tau^(k)) / (xi . L0 . xi) / |N|,
 // zero at k = 0 and on padded frequencies (kColGreen), or the equilibrium-norm
 // sums of Eq. (errE_def) (kColEta, into acc).
-template <typename T, int D, int CM_>
+template <typename T, int D, int CM_, int QC = 0, int NC = 0>
 __device__ __forceinline__ void green_tile(const ColArgs<T>& a, cplx<T>* sm, int t, int blk_inner, int cell_idx,
                                            double (&acc)[2]) {
   using C = cplx<T>;
   const ColArgsBase& b = a.b;
   const Geom& g = b.g;
-  const int n = b.plan.n, Q = b.Q;
+  const int n = NC ? NC : b.plan.n, Q = QC ? QC : b.Q;
   const int M = g.M;
   const int ngrp = Q / D;  // groups of D components sharing one frequency
   T invY[D], L0[D * D];
@@ -721,13 +721,13 @@ __global__ void __launch_bounds__(ColBounds<PS>::threads, ColBounds<PS>::blocks)
 
   if (CM_ == kColGreen || CM_ == kColEta) {
     double acc[2] = {0.0, 0.0};
-    green_tile<T, D, CM_>(a, sm, blk_outer, blk_inner, cell, acc);
+    green_tile<T, D, CM_, QC, PlanLen<PS>::value>(a, sm, blk_outer, blk_inner, cell, acc);
     if (CM_ == kColEta) {
       block_reduce_store<2>(acc, 2, a.part, gridDim.x, blockIdx.x);
       return;
     }
     __syncthreads();
-    fft_plan<true, T, PS>(sm + q, Q, b.plan, u, b.tpc, a.tw);
+    fft_plan<true, T, PS>(sm + q, Q, b.plan, u, tpc, a.tw);
   }
   }
 

@@ -52,6 +52,12 @@ constexpr bool kHasDf = std::is_same<T, double>::value && D == 2;
 // 2187-point column FFT.
 constexpr int kGreenQ = 4;
 constexpr int kGreenT = 81;
+// The 3-D column passes (axis-1 forward and inverse, Green pass along axis 0)
+// also exist with the tuned 243^3 three-load tile shape compiled in: tiles of
+// 2 frequencies x 9 channels (Q = 18 columns), 9 threads per 243-point column
+// FFT.
+constexpr int kCol3Q = 18;
+constexpr int kCol3T = 9;
 // Likewise the 2187^2 A p pass: one line per 96-thread CTA, spectrum tiles of
 // 2 frequencies; the threads per line FFT stay a launch argument (compiled in,
 // they cost registers and the pass spilled: 44.0 against 41.7 us; the
@@ -79,6 +85,11 @@ struct Launchers {
       if constexpr (D == 3) {
         if ((e = opt_in_smem(k_col<T, D, kColFwd, P>, c1)) != cudaSuccess) return e;
         if ((e = opt_in_smem(k_col<T, D, kColInv, P>, c1)) != cudaSuccess) return e;
+        if constexpr (NL == 3) {
+          if ((e = opt_in_smem(k_col<T, D, kColFwd, P, kCol3Q, kCol3T>, c1)) != cudaSuccess) return e;
+          if ((e = opt_in_smem(k_col<T, D, kColInv, P, kCol3Q, kCol3T>, c1)) != cudaSuccess) return e;
+          if ((e = opt_in_smem(k_col<T, D, kColGreen, P, kCol3Q, kCol3T>, c0)) != cudaSuccess) return e;
+        }
       }
     }
 #define FH_SM(K, B) \
@@ -211,6 +222,17 @@ struct Launchers {
     if constexpr (kHasCt<T, D, NL>) {
       using P = CtPlan<D, NL>;
       if (L.block <= ColBounds<P>::threads && cplan_is<P>(a.b.plan)) {
+        if constexpr (D == 3 && NL == 3) {
+          if (a.b.Q == kCol3Q && a.b.tpc == kCol3T) {  // the tuned 243^3 three-load tile shape
+            switch (mode) {
+              case kColFwd: k_col<T, D, kColFwd, P, kCol3Q, kCol3T><<<L.grid, L.block, L.smem, st>>>(a); break;
+              case kColInv: k_col<T, D, kColInv, P, kCol3Q, kCol3T><<<L.grid, L.block, L.smem, st>>>(a); break;
+              case kColGreen: k_col<T, D, kColGreen, P, kCol3Q, kCol3T><<<L.grid, L.block, L.smem, st>>>(a); break;
+              default: return cudaErrorInvalidValue;
+            }
+            return cudaGetLastError();
+          }
+        }
         if (mode == kColGreen) {
           if constexpr (D == 2 && NL == 1) {
             if (a.b.Q == kGreenQ && a.b.tpc == kGreenT && a.b.stride_i == kGreenQ) {  // the tuned 2187^2 tile shape
