@@ -58,15 +58,26 @@ constexpr int kGreenT = 81;
 // FFT.
 constexpr int kCol3Q = 18;
 constexpr int kCol3T = 9;
+// The 3-D three-load direction and A p passes with their tuned launch shape:
+// one line per 64-thread CTA (five packed sequences of nine channels), tiles
+// of 2 frequencies.
+using RowShape243x3 = RowShape<64, 0, 2>;
+// The two-load 729^2 Green pass (the batched sweep's largest cells) with
+// tiles of 1 or 2 frequencies x 4 channels and 27 threads per column FFT.
+constexpr int kGreen729T = 27;
 // Likewise the 2187^2 A p pass: one line per 96-thread CTA, spectrum tiles of
 // 2 frequencies; the threads per line FFT stay a launch argument (compiled in,
 // they cost registers and the pass spilled: 44.0 against 41.7 us; the
 // direction pass measured no gain from either form: 47.3 / 48.8 against 47.1).
 using RowShape2187 = RowShape<96, 0, 2>;
+template <typename RS, int M, typename T>
+inline bool row_shape_is(const Launch& L, const RowArgs<T>& a) {
+  return L.block == RS::nt && a.lpc == 1 && (RS::tpl == 0 || a.tpl == RS::tpl) && a.g.C == RS::cc &&
+         a.nseq == (M + 1) / 2;
+}
 template <typename T>
 inline bool row_shape_is_2187(const Launch& L, const RowArgs<T>& a) {
-  return L.block == RowShape2187::nt && a.lpc == 1 && (RowShape2187::tpl == 0 || a.tpl == RowShape2187::tpl) &&
-         a.g.C == RowShape2187::cc && a.nseq == 1;
+  return row_shape_is<RowShape2187, 2>(L, a);
 }
 
 template <typename T, int D, int NL>
@@ -79,6 +90,14 @@ struct Launchers {
       if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, P>, rs)) != cudaSuccess) return e;
       if constexpr (D == 2 && NL == 1)
         if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, P, false, RowShape2187>, rs)) != cudaSuccess) return e;
+      if constexpr (D == 3 && NL == 3) {
+        if ((e = opt_in_smem(k_row_fwd<T, D, NL, kProDir, P, false, RowShape243x3>, rs)) != cudaSuccess) return e;
+        if ((e = opt_in_smem(k_row_inv<T, D, NL, kEpiDir, P, false, RowShape243x3>, rs)) != cudaSuccess) return e;
+      }
+      if constexpr (D == 2 && NL == 2) {
+        if ((e = opt_in_smem(k_col<T, D, kColGreen, P, 4, kGreen729T>, c0)) != cudaSuccess) return e;
+        if ((e = opt_in_smem(k_col<T, D, kColGreen, P, 8, kGreen729T>, c0)) != cudaSuccess) return e;
+      }
       if ((e = opt_in_smem(k_col<T, D, kColGreen, P>, c0)) != cudaSuccess) return e;
       if constexpr (D == 2 && NL == 1)
         if ((e = opt_in_smem(k_col<T, D, kColGreen, P, kGreenQ, kGreenT>, c0)) != cudaSuccess) return e;
@@ -143,6 +162,12 @@ struct Launchers {
     if constexpr (kHasCt<T, D, NL>) {
       using P = CtPlan<D, NL>;
       if (pro == kProDir && L.block <= RowBounds<P>::threads && cplan_is<P>(a.plan)) {
+        if constexpr (D == 3 && NL == 3) {
+          if (row_shape_is<RowShape243x3, D * NL>(L, a)) {
+            k_row_fwd<T, D, NL, kProDir, P, false, RowShape243x3><<<L.grid, L.block, L.smem, st>>>(a);
+            return cudaGetLastError();
+          }
+        }
         k_row_fwd<T, D, NL, kProDir, P><<<L.grid, L.block, L.smem, st>>>(a);
         return cudaGetLastError();
       }
@@ -180,6 +205,12 @@ struct Launchers {
     if constexpr (kHasCt<T, D, NL>) {
       using P = CtPlan<D, NL>;
       if (epi == kEpiDir && L.block <= RowBounds<P>::threads && cplan_is<P>(a.plan)) {
+        if constexpr (D == 3 && NL == 3) {
+          if (row_shape_is<RowShape243x3, D * NL>(L, a)) {
+            k_row_inv<T, D, NL, kEpiDir, P, false, RowShape243x3><<<L.grid, L.block, L.smem, st>>>(a);
+            return cudaGetLastError();
+          }
+        }
         if constexpr (D == 2 && NL == 1) {
           if (row_shape_is_2187(L, a)) {
             k_row_inv<T, D, NL, kEpiDir, P, false, RowShape2187><<<L.grid, L.block, L.smem, st>>>(a);
@@ -234,6 +265,18 @@ struct Launchers {
           }
         }
         if (mode == kColGreen) {
+          if constexpr (D == 2 && NL == 2) {
+            if (a.b.tpc == kGreen729T && a.b.stride_i == a.b.Q) {  // the 729^2 two-load tiles
+              if (a.b.Q == 4) {
+                k_col<T, D, kColGreen, P, 4, kGreen729T><<<L.grid, L.block, L.smem, st>>>(a);
+                return cudaGetLastError();
+              }
+              if (a.b.Q == 8) {
+                k_col<T, D, kColGreen, P, 8, kGreen729T><<<L.grid, L.block, L.smem, st>>>(a);
+                return cudaGetLastError();
+              }
+            }
+          }
           if constexpr (D == 2 && NL == 1) {
             if (a.b.Q == kGreenQ && a.b.tpc == kGreenT && a.b.stride_i == kGreenQ) {  // the tuned 2187^2 tile shape
               k_col<T, D, kColGreen, P, kGreenQ, kGreenT><<<L.grid, L.block, L.smem, st>>>(a);

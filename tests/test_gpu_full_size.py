@@ -11,7 +11,8 @@ tests/golden/make_full_size_parity.py, which calls only the oracle):
 * 2187^2 RSA disks (the benchmark microstructure) at contrast 10, both loads:
   effective-tensor columns, and the oracle's own true residual of the
   returned field;
-* a batch with cells of 135, 243, 375 and 729 per axis, two loads each;
+* a batch with cells of 135, 243, 375 and 729 per axis, two loads each, with
+  the default and with the autotuned launch shapes;
 * 243^3 Boolean spheres at contrast 10: the full tensor (three loads per
   launch) and one single-load solve.
 
@@ -80,13 +81,18 @@ def test_uneven_batch_with_729_cells_matches_oracle():
     gold = _gold()
     cells = [case_input("batch", k) for k in range(len(BATCH_CELLS))]
     with fh.Batch([c[0] for c in cells], [c[1] for c in cells], nloads=2, precision="fp32_refined") as bt:
-        Leff, st, it, info = bt.solve(np.eye(2), tol=TOL, method="cg", max_iter=20000)
-    assert np.all(st == 0), st
-    assert 729 in info["ct_plans"], info
-    for k in range(len(BATCH_CELLS)):
-        for b in range(2):
-            ref = gold[("batch", k, b)]["L_eff_col"]
-            assert _rel(Leff[k, :, b], ref) <= LEFF_BAR, (BATCH_CELLS[k], b, Leff[k, :, b], ref)
+        runs = [bt.solve(np.eye(2), tol=TOL, method="cg", max_iter=20000)]
+        # the tuned launch shapes (for the 729^2 cells, tile widths with their
+        # own compiled Green-pass instances) must give the oracle's solutions too
+        bt.autotune()
+        runs.append(bt.solve(np.eye(2), tol=TOL, method="cg", max_iter=20000))
+    for Leff, st, it, info in runs:
+        assert np.all(st == 0), st
+        assert 729 in info["ct_plans"], info
+        for k in range(len(BATCH_CELLS)):
+            for b in range(2):
+                ref = gold[("batch", k, b)]["L_eff_col"]
+                assert _rel(Leff[k, :, b], ref) <= LEFF_BAR, (BATCH_CELLS[k], b, Leff[k, :, b], ref)
 
 
 def test_243_cube_full_tensor_and_single_load_match_oracle():
